@@ -1,0 +1,168 @@
+"""Oracle greedy decoders OMP, SP and OMPR in FP64 (test infrastructure only).
+
+Each decoder alternates support detection (a correlation A^T r and a selection over |.|) with
+the least-squares sub-problem on the current support (Sec. II).  The oracle solves every LS
+sub-problem in closed form (QR of A_S) or, when A_S would not fit, by FP64 CG to 1e-13
+relative -- the value the paper's CG approximates (Theorems 1-2).
+
+  * OMP: Sec. II steps 1-4 and the outer loop of Algorithm 1 (exactly K iterations).
+  * SP: Subspace Pursuit (Dai & Milenkovic 2009), which the paper only cites.  Reading used:
+      S <- topK|A^T y|; s <- LS(S); r <- y - A s; then repeat: S~ = S u topK_{j not in S}|A^T r|,
+      u <- LS(S~), S' <- topK_{j in S~}|u_j|, s' <- LS(S'), r' <- y - A s'; stop and keep
+      (s, S) if S' = S or ||r'|| >= ||r||, else accept (S', s', r').  At most L_max rounds.
+  * OMPR: OMP with Replacement (Jain, Tewari & Dhillon 2011), also only cited.  Reading used
+      (step eta = 1, one replacement per iteration): S <- topK|A^T y|; s <- LS(S); then for at
+      most T_max rounds: z = s + A^T r, j = argmax_{not in S}|z_j|, i = argmin_{in S}|z_i|;
+      stop if |z_j| <= |z_i|; else S <- S - {i} + {j}, s <- LS(S), r <- y - A s.
+
+Ties are broken towards the lowest index everywhere.  Every selection records its margin
+mu = (a_(1) - a_(2)) / a_(1) (argmax, argmin) or (a_(K) - a_(K+1)) / a_(K) (top-K); mu <= 1e-3
+marks a near-tie, at which an FP32 decoder may legitimately choose differently.
+"""
+import numpy as np
+
+from . import ls as _ls
+
+NEAR_TIE = 1e-3
+
+
+def _argmax_lowest(a, allowed):
+    """Index of the largest a over `allowed` (lowest index on ties) and the selection margin."""
+    idx = np.flatnonzero(allowed)
+    vals = a[idx]
+    order = np.lexsort((idx, -vals))
+    t = int(idx[order[0]])
+    a1 = float(vals[order[0]])
+    a2 = float(vals[order[1]]) if len(order) > 1 else 0.0
+    return t, (a1 - a2) / a1 if a1 > 0 else 0.0
+
+
+def _argmin_lowest(a, allowed):
+    idx = np.flatnonzero(allowed)
+    vals = a[idx]
+    order = np.lexsort((idx, vals))
+    t = int(idx[order[0]])
+    a1 = float(vals[order[0]])
+    a2 = float(vals[order[1]]) if len(order) > 1 else np.inf
+    return t, (a2 - a1) / a2 if np.isfinite(a2) and a2 > 0 else (1.0 if a2 > a1 else 0.0)
+
+
+def topk_lowest(a, allowed, K):
+    """The K indices with the largest a among `allowed` (ties -> lowest index), sorted ascending,
+    and the boundary margin (a_(K) - a_(K+1)) / a_(K)."""
+    idx = np.flatnonzero(allowed)
+    vals = a[idx]
+    order = np.lexsort((idx, -vals))
+    pick = idx[order[:K]]
+    aK = float(vals[order[K - 1]])
+    aK1 = float(vals[order[K]]) if len(order) > K else 0.0
+    mu = (aK - aK1) / aK if aK > 0 else 0.0
+    return np.sort(pick), mu
+
+
+class Result(dict):
+    """s (dense N), S (sorted support), iters, trace [(kind, margin)], near_ties, min_margin,
+    resid (final ||y - A s||)."""
+
+
+def _finish(op, y, S, sS, iters, trace):
+    s = np.zeros(op.N)
+    s[S] = sS
+    margins = [m for _, m in trace]
+    return Result(s=s, S=np.asarray(S, dtype=np.int64), iters=iters, trace=trace,
+                  near_ties=int(sum(m <= NEAR_TIE for m in margins)),
+                  min_margin=float(min(margins)) if margins else 1.0,
+                  resid=float(np.linalg.norm(y - op.apply(s))))
+
+
+def omp(op, y, K, ls_method="auto", replay=None, on_step=None):
+    """OMP (Sec. II, Algorithm 1 outer loop).  `replay[i]` forces the i-th selected index.
+    `on_step(i, S, sS, r)` is called after each iteration (used by invariant tests)."""
+    y = np.asarray(y, dtype=np.float64)
+    r = y.copy()
+    S = np.zeros(0, dtype=np.int64)
+    sS = np.zeros(0)
+    trace = []
+    for i in range(K):
+        a = np.abs(op.apply_t(r))
+        allowed = np.ones(op.N, dtype=bool)
+        allowed[S] = False
+        t, mu = _argmax_lowest(a, allowed)
+        if replay is not None:
+            t = int(replay[i])
+        trace.append(("argmax", mu))
+        S = np.sort(np.append(S, t))
+        sS = _ls.ls(op, S, y, ls_method)
+        r = y - op.apply_support(S, sS)
+        if on_step is not None:
+            on_step(i, S, sS, r)
+    return _finish(op, y, S, sS, K, trace)
+
+
+def sp(op, y, K, ls_method="auto", L_max=50):
+    """Subspace Pursuit with the stopping rule stated in the module docstring."""
+    y = np.asarray(y, dtype=np.float64)
+    trace = []
+    everything = np.ones(op.N, dtype=bool)
+    S, mu = topk_lowest(np.abs(op.apply_t(y)), everything, K)
+    trace.append(("topk", mu))
+    sS = _ls.ls(op, S, y, ls_method)
+    r = y - op.apply_support(S, sS)
+    rn = float(np.linalg.norm(r))
+    it = 0
+    while it < L_max:
+        it += 1
+        allowed = np.ones(op.N, dtype=bool)
+        allowed[S] = False
+        T, mu = topk_lowest(np.abs(op.apply_t(r)), allowed, K)
+        trace.append(("topk", mu))
+        St = np.sort(np.concatenate([S, T]))
+        u = _ls.ls(op, St, y, ls_method)
+        ua = np.zeros(op.N)
+        ua[St] = np.abs(u)
+        inside = np.zeros(op.N, dtype=bool)
+        inside[St] = True
+        Sp, mu = topk_lowest(ua, inside, K)
+        trace.append(("topk", mu))
+        sp_ = _ls.ls(op, Sp, y, ls_method)
+        rp = y - op.apply_support(Sp, sp_)
+        rpn = float(np.linalg.norm(rp))
+        if np.array_equal(Sp, S) or rpn >= rn:
+            break
+        S, sS, r, rn = Sp, sp_, rp, rpn
+    return _finish(op, y, S, sS, it, trace)
+
+
+def ompr(op, y, K, ls_method="auto", T_max=100):
+    """OMP with Replacement (eta = 1, one swap per iteration) as stated in the module docstring."""
+    y = np.asarray(y, dtype=np.float64)
+    trace = []
+    S, mu = topk_lowest(np.abs(op.apply_t(y)), np.ones(op.N, dtype=bool), K)
+    trace.append(("topk", mu))
+    sS = _ls.ls(op, S, y, ls_method)
+    r = y - op.apply_support(S, sS)
+    it = 0
+    while it < T_max:
+        z = op.apply_t(r)
+        z[S] += sS
+        a = np.abs(z)
+        inside = np.zeros(op.N, dtype=bool)
+        inside[S] = True
+        j, mu_j = _argmax_lowest(a, ~inside)
+        i, mu_i = _argmin_lowest(a, inside)
+        big = max(a[j], a[i])
+        mu_swap = abs(a[j] - a[i]) / big if big > 0 else 0.0
+        trace.append(("argmax", mu_j))
+        trace.append(("argmin", mu_i))
+        trace.append(("swap", mu_swap))
+        if a[j] <= a[i]:
+            break
+        it += 1
+        S = np.sort(np.append(S[S != i], j))
+        sS = _ls.ls(op, S, y, ls_method)
+        r = y - op.apply_support(S, sS)
+    return _finish(op, y, S, sS, it, trace)
+
+
+def recover(op, y, K, algo, **kw):
+    return {"omp": omp, "sp": sp, "ompr": ompr}[algo](op, y, K, **kw)

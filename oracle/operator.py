@@ -1,0 +1,63 @@
+"""Oracle sensing operator A = P_Omega . C_N . diag(d) (test infrastructure only).
+
+Sec. III-A, Eq. 7: the structurally random matrix Phi = D F R with D a row sampler, F an
+orthonormal fast transform (the DCT) and R a randomiser.  Here R is the Rademacher sign flip
+diag(d), F = C_N the orthonormal DCT-II, D = P_Omega keeps the rows in Omega.  The sparsifying
+basis is the identity, so A = Phi and y = A s (Eq. 1-2).  No sqrt(N/M) rescaling is applied,
+hence A A^T = I_M.
+
+Sec. III-D lists the operator realisations this follows: "W x" zeroes entries outside the
+support, "D x" picks M entries, "F x" is the DCT computed by FFT, "R x" is the randomiser.
+"""
+import numpy as np
+
+from . import dct as _dct
+from . import rng as _rng
+
+
+class Operator:
+    """A in R^{M x N}; `fast=True` applies C_N via FFT (O-fast), else by the O(N^2) sum."""
+
+    def __init__(self, N, M, seed, fast=True):
+        if N < 2 or (N & (N - 1)):
+            raise ValueError("N must be a power of two >= 2")
+        self.N, self.M, self.seed = int(N), int(M), int(seed)
+        self.omega = _rng.omega(N, M, seed)
+        self.d = _rng.signs(N, seed)
+        self.fast = fast
+
+    # --- transforms -------------------------------------------------------------------
+    def _c(self, x):
+        return _dct.dct2_fast(x) if self.fast else _dct.dct2_naive(x)
+
+    def _ct(self, X):
+        return _dct.dct3_fast(X) if self.fast else _dct.dct3_naive(X)
+
+    # --- A and A^T (Sec. III-D operator list) --------------------------------------------
+    def apply(self, x):
+        """A x = (C_N (d * x))[Omega]."""
+        return self._c(self.d * np.asarray(x, dtype=np.float64))[..., self.omega]
+
+    def apply_t(self, u):
+        """A^T u = d * C_N^T (P_Omega^T u)."""
+        u = np.asarray(u, dtype=np.float64)
+        full = np.zeros(u.shape[:-1] + (self.N,))
+        full[..., self.omega] = u
+        return self.d * self._ct(full)
+
+    def columns(self, S):
+        """Dense A_S (M x |S|) from the closed form A[m, j] = d_j w_{Omega_m} cos(pi (2j+1) Omega_m / (2N))."""
+        S = np.asarray(S, dtype=np.int64)
+        k = self.omega[:, None].astype(np.float64)
+        j = S[None, :].astype(np.float64)
+        w = _dct.weights(self.N)[self.omega][:, None]
+        return self.d[S][None, :] * w * np.cos(np.pi * (2.0 * j + 1.0) * k / (2.0 * self.N))
+
+    def dense(self):
+        return self.columns(np.arange(self.N))
+
+    def apply_support(self, S, v):
+        """A W_S theta for theta supported on S with values v (Eq. 8's weighting)."""
+        x = np.zeros(self.N)
+        x[np.asarray(S, dtype=np.int64)] = v
+        return self.apply(x)
