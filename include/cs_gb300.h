@@ -1,0 +1,145 @@
+/*
+ * cs_gb300.h -- C ABI of the GB300 (sm_103a) greedy compressive-sensing decoders.
+ *
+ * The library recovers a K-sparse s from y = A s (+ noise) with the greedy decoders OMP, SP
+ * (Subspace Pursuit) and OMPR (OMP with Replacement), each using the paper's CG-based weighted
+ * least-squares step (Hsieh, Lu & Pei, "Fast Greedy Approaches for Compressive Sensing of
+ * Large-Scale Signals", arXiv:1509.03979).
+ *
+ * Operator (Sec. III-A, Eq. 7):  A = P_Omega . C_N . diag(d)  in R^{M x N}
+ *   d      Rademacher signs (the randomiser), regenerated from the seed (SplitMix64 hash)
+ *   C_N    orthonormal DCT-II, C_N[k,n] = w_k cos(pi (2n+1) k / (2N)), w_0 = sqrt(1/N),
+ *          w_k = sqrt(2/N); no sqrt(N/M) rescaling, so A A^T = I_M
+ *   Omega  M distinct rows, partial Fisher-Yates from a SplitMix64 stream, sorted ascending
+ * Random-draw definitions (both must match exactly for the oracle cross-check):
+ *   gamma = 0x9E3779B97F4A7C15, mix = SplitMix64 finaliser, h(x) = mix(x + gamma)
+ *   d_n = -1 iff the top bit of h((seed ^ 0xD1B54A32D192ED03) + n) is set
+ *   Omega: for i = 0..M-1: j = i + (mix((seed ^ gamma) + (i+1) gamma) mod (N-i)); swap
+ *
+ * Conventions for every entry point below:
+ *   - Array arguments are caller-owned DEVICE pointers (e.g. torch tensor data_ptr()),
+ *     FP32 values and int32 indices, contiguous, unless a comment says "host".
+ *   - Calls are asynchronous on the operator's stream (cs_op_set_stream); they return after
+ *     the launch.  Argument errors are returned synchronously and nothing is launched.
+ *   - N must be a power of two with 16 <= N <= 2^18 (else CS_ERR_UNSUPPORTED_N);
+ *     1 <= M <= N; 0 <= K <= M; for SP also 2K <= M (else CS_ERR_INVALID_ARG).
+ *   - cg_tol is RELATIVE: CG stops when ||r_j|| <= cg_tol * ||W A^T y|| (or after cg_maxit
+ *     steps; reaching cg_maxit is not an error, it is counted in cs_stats.cg_maxit_hits).
+ *   - cs_last_error() returns a thread-local message describing the last failure.
+ *   - Operators are not thread-safe: one host thread at a time per cs_op_t.
+ */
+#ifndef CS_GB300_H
+#define CS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_op* cs_op_t;
+
+typedef enum { CS_OMP = 0, CS_SP = 1, CS_OMPR = 2 } cs_algo;
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_INVALID_ARG = 1,
+  CS_ERR_UNSUPPORTED_N = 2,
+  CS_ERR_OOM = 3,
+  CS_ERR_CUDA = 4,
+  CS_ERR_TIMEOUT = 5
+} cs_status;
+
+/* Per-recovery statistics (written on the device, read back by cs_get_stats). */
+typedef struct {
+  int32_t outer_iters;     /* greedy iterations (OMP: K; SP/OMPR: rounds run) */
+  int32_t cg_iters_total;  /* CG steps over all LS solves (each = one H d product) */
+  int32_t cg_maxit_hits;   /* LS solves that stopped on cg_maxit */
+  int32_t near_ties;       /* reserved (not computed on the device): 0 */
+  float final_resid;       /* ||y - A s_hat||_2 of the returned solution */
+  float min_margin;        /* reserved: -1 */
+  int32_t status;          /* cs_status of the device-side run */
+} cs_stats;
+
+/* Create the operator A = P_Omega C_N diag(d) for (N, M, seed) (Sec. III-A, Eq. 7).
+ * Builds Omega on the host, uploads its bitmask/rank tables and the twiddle tables.
+ * Returns NULL on failure (see cs_last_error()).  Owns all its device memory. */
+cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed);
+
+/* Free the operator and every buffer it owns.  Waits for its stream first. */
+void cs_op_destroy(cs_op_t op);
+
+/* Launch all further work of `op` on `cuda_stream` (a cudaStream_t; NULL = legacy default). */
+cs_status cs_op_set_stream(cs_op_t op, void* cuda_stream);
+
+/* y_M = A x_N: sign flip, orthonormal DCT-II, keep rows Omega (Sec. III-D operator list).
+ * x_N: [N] device, y_M: [M] device (written).  Buffers must not overlap. */
+cs_status cs_op_apply(cs_op_t op, const float* x_N, float* y_M);
+
+/* x_N = A^T y_M: scatter onto Omega, orthonormal DCT-III, sign flip (the correlation A^T r of
+ * Eq. 6).  y_M: [M] device; x_N: [N] device (written).  Buffers must not overlap. */
+cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N);
+
+/* Copy the operator's random draws to HOST memory for cross-checking: omega_M_host [M]
+ * (sorted row indices) and d_N_host [N] (+1/-1).  Either pointer may be NULL. */
+cs_status cs_op_export(cs_op_t op, int32_t* omega_M_host, int8_t* d_N_host);
+
+/* Host-only: the same random draws cs_op_create(N, M, seed) uses, without touching a GPU.
+ * omega_M_host [M] HOST (sorted), d_N_host [N] HOST (+1/-1); either may be NULL.
+ * Returns CS_ERR_UNSUPPORTED_N / CS_ERR_INVALID_ARG under the same rules as cs_op_create. */
+cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_M_host, int8_t* d_N_host);
+
+/* Greedy recovery (Sec. II steps 1-4; Algorithm 1 for OMP; SP and OMPR as cited in
+ * Sec. IV) with the CG weighted LS step (Eq. 8-10, the CG function of Algorithm 1).
+ *   y           [M] device measurements
+ *   K           sparsity (number of support entries returned)
+ *   algo        CS_OMP, CS_SP or CS_OMPR
+ *   cg_tol      relative CG tolerance (see conventions); cg_maxit >= 1
+ *   s_out       [N] device, dense estimate, zeros off the support
+ *   support_out [K] device, selected indices sorted ascending
+ * One kernel launch on the op's stream; the whole greedy + CG loop runs on the device
+ * without host synchronisation.  K = 0 writes zeros. */
+cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float cg_tol,
+                     int32_t cg_maxit, float* s_out, int32_t* support_out);
+
+/* Batched recovery of B independent signals in one persistent launch per cluster size.
+ * ops[b], y[b], K[b], algo[b], s_out[b], support_out[b] describe signal b (HOST arrays of
+ * handles/device pointers).  All ops must share one stream (taken from ops[0]).
+ * stats_host [B] HOST (may be NULL): filled after the work completes -- a non-NULL
+ * stats_host makes the call wait for the stream. */
+cs_status cs_recover_batched(int32_t B, const cs_op_t* ops, const float* const* y,
+                             const int32_t* K, const int32_t* algo, float cg_tol,
+                             int32_t cg_maxit, float* const* s_out,
+                             int32_t* const* support_out, cs_stats* stats_host);
+
+/* LS on a FIXED support (Sec. II step 3 solved as Algorithm 1's CG on
+ * H = W A^T A W, b = W A^T y; Theorems 1-2 make the on-support entries equal).
+ *   support [k] device, sorted ascending, distinct; y [M] device; s_S_out [k] device,
+ *   s_S_out[i] is the coefficient of column support[i]. */
+cs_status cs_ls_solve(cs_op_t op, const int32_t* support, int32_t k, const float* y,
+                      float cg_tol, int32_t cg_maxit, float* s_S_out);
+
+/* Adjoint of cs_ls_solve on a fixed support: dy = A_S (A_S^T A_S)^{-1} g, i.e. a CG solve
+ * with the normal-equation matrix of Eq. 10 followed by one application of A_S.
+ *   support [k] device sorted; g [k] device (dL/ds_S); dy_out [M] device. */
+cs_status cs_ls_backward(cs_op_t op, const int32_t* support, int32_t k, const float* g,
+                         float cg_tol, int32_t cg_maxit, float* dy_out);
+
+/* Batched fixed-support LS solve / adjoint: B right-hand sides sharing one operator and one
+ * support length k.  support, y/g, out are device arrays laid out [B][k], [B][M] or
+ * [B][k], [B][k] -> [B][M] respectively (row-major, contiguous). */
+cs_status cs_ls_solve_batched(cs_op_t op, int32_t B, const int32_t* support, int32_t k,
+                              const float* y, float cg_tol, int32_t cg_maxit, float* s_S_out);
+cs_status cs_ls_backward_batched(cs_op_t op, int32_t B, const int32_t* support, int32_t k,
+                                 const float* g, float cg_tol, int32_t cg_maxit, float* dy_out);
+
+/* Statistics of the last single-signal call on this op (synchronises the op's stream). */
+cs_status cs_get_stats(cs_op_t op, cs_stats* out);
+
+/* Thread-local description of the last error (never NULL). */
+const char* cs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CS_GB300_H */

@@ -1,0 +1,219 @@
+"""Thin ctypes binding over the C ABI in include/cs_gb300.h (argument marshalling only).
+
+Every computation runs in the CUDA library libcs_gb300.so built from csrc/; this module only
+checks tensor shapes, dtypes and devices, passes raw pointers, and attaches the calls to
+PyTorch's current CUDA stream.  If the library is missing, every call raises: there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcs_gb300.so")
+
+OMP, SP, OMPR = 0, 1, 2
+ALGOS = {"omp": OMP, "sp": SP, "ompr": OMPR}
+
+
+class CsStats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("cg_iters_total", ctypes.c_int32),
+                ("cg_maxit_hits", ctypes.c_int32), ("near_ties", ctypes.c_int32),
+                ("final_resid", ctypes.c_float), ("min_margin", ctypes.c_float),
+                ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64, _U64, _I32, _F32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_float
+SIGNATURES = {
+    "cs_op_create": (_P, [_I64, _I64, _U64]),
+    "cs_op_destroy": (None, [_P]),
+    "cs_op_set_stream": (_I32, [_P, _P]),
+    "cs_op_apply": (_I32, [_P, _P, _P]),
+    "cs_op_apply_t": (_I32, [_P, _P, _P]),
+    "cs_op_export": (_I32, [_P, _P, _P]),
+    "cs_operator_draws": (_I32, [_I64, _I64, _U64, _P, _P]),
+    "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
+    "cs_recover_batched": (_I32, [_I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P]),
+    "cs_ls_solve": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
+    "cs_ls_backward": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
+    "cs_ls_solve_batched": (_I32, [_P, _I32, _P, _I32, _P, _F32, _I32, _P]),
+    "cs_ls_backward_batched": (_I32, [_P, _I32, _P, _I32, _P, _F32, _I32, _P]),
+    "cs_get_stats": (_I32, [_P, _P]),
+    "cs_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libcs_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise RuntimeError(f"cs_gb300 error {status}: {lib().cs_last_error().decode()}")
+
+
+def _dev(t, dtype, n=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def operator_draws(N, M, seed):
+    """The operator's Omega (sorted int32 [M]) and d (+-1 int8 [N]), computed on the host."""
+    import numpy as np
+    om = np.zeros(M, dtype=np.int32)
+    d = np.zeros(N, dtype=np.int8)
+    _check(lib().cs_operator_draws(N, M, seed, om.ctypes.data_as(_P), d.ctypes.data_as(_P)))
+    return om, d
+
+
+class Operator:
+    """A = P_Omega C_N diag(d) on the current CUDA device (Sec. III-A, Eq. 7)."""
+
+    def __init__(self, N, M, seed):
+        self.N, self.M, self.seed = int(N), int(M), int(seed)
+        h = lib().cs_op_create(self.N, self.M, self.seed)
+        if not h:
+            raise RuntimeError(f"cs_op_create failed: {lib().cs_last_error().decode()}")
+        self._h = ctypes.c_void_p(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cs_op_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _stream(self):
+        _check(lib().cs_op_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def apply(self, x, out=None):
+        out = torch.empty(self.M, dtype=torch.float32, device=x.device) if out is None else out
+        self._stream()
+        _check(lib().cs_op_apply(self._h, _dev(x, torch.float32, self.N, "x"), _dev(out, torch.float32, self.M, "y")))
+        return out
+
+    def apply_t(self, u, out=None):
+        out = torch.empty(self.N, dtype=torch.float32, device=u.device) if out is None else out
+        self._stream()
+        _check(lib().cs_op_apply_t(self._h, _dev(u, torch.float32, self.M, "u"), _dev(out, torch.float32, self.N, "x")))
+        return out
+
+    def export(self):
+        import numpy as np
+        om = np.zeros(self.M, dtype=np.int32)
+        d = np.zeros(self.N, dtype=np.int8)
+        _check(lib().cs_op_export(self._h, om.ctypes.data_as(_P), d.ctypes.data_as(_P)))
+        return om, d
+
+    def recover(self, y, K, algo="omp", cg_tol=1e-6, cg_maxit=100, s_out=None, support_out=None):
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        s_out = torch.empty(self.N, dtype=torch.float32, device=y.device) if s_out is None else s_out
+        support_out = (torch.empty(max(K, 1), dtype=torch.int32, device=y.device)
+                       if support_out is None else support_out)
+        self._stream()
+        _check(lib().cs_recover(self._h, _dev(y, torch.float32, self.M, "y"), int(K), a, float(cg_tol),
+                                int(cg_maxit), _dev(s_out, torch.float32, self.N, "s_out"),
+                                _dev(support_out, torch.int32, None, "support_out")))
+        return s_out, support_out[:K]
+
+    def ls_solve(self, support, y, cg_tol=1e-6, cg_maxit=100, out=None):
+        """Batched when y is [B, M] and support is [B, k]."""
+        batched = y.dim() == 2
+        B = y.shape[0] if batched else 1
+        k = support.shape[-1]
+        out = torch.empty((B, k) if batched else (k,), dtype=torch.float32, device=y.device) if out is None else out
+        self._stream()
+        _check(lib().cs_ls_solve_batched(self._h, B, _dev(support, torch.int32, B * k, "support"), k,
+                                         _dev(y, torch.float32, B * self.M, "y"), float(cg_tol), int(cg_maxit),
+                                         _dev(out, torch.float32, B * k, "out")))
+        return out
+
+    def ls_backward(self, support, g, cg_tol=1e-6, cg_maxit=100, out=None):
+        batched = g.dim() == 2
+        B = g.shape[0] if batched else 1
+        k = support.shape[-1]
+        out = (torch.empty((B, self.M) if batched else (self.M,), dtype=torch.float32, device=g.device)
+               if out is None else out)
+        self._stream()
+        _check(lib().cs_ls_backward_batched(self._h, B, _dev(support, torch.int32, B * k, "support"), k,
+                                            _dev(g, torch.float32, B * k, "g"), float(cg_tol), int(cg_maxit),
+                                            _dev(out, torch.float32, B * self.M, "dy")))
+        return out
+
+    def stats(self):
+        st = CsStats()
+        _check(lib().cs_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+
+def recover_batched(ops, ys, Ks, algos, cg_tol=1e-6, cg_maxit=100, s_outs=None, supports=None, want_stats=False):
+    """Recover B independent signals (each with its own operator) in one persistent launch
+    per cluster size.  Returns (s_outs, supports[, stats])."""
+    B = len(ops)
+    s_outs = s_outs or [torch.empty(op.N, dtype=torch.float32, device=y.device) for op, y in zip(ops, ys)]
+    supports = supports or [torch.empty(max(k, 1), dtype=torch.int32, device=y.device) for k, y in zip(Ks, ys)]
+    for op in ops:
+        op._stream()
+    arr = lambda ctype, vals: (ctype * B)(*vals)
+    h = arr(_P, [op.handle.value for op in ops])
+    yp = arr(_P, [_dev(y, torch.float32, op.M, "y").value for op, y in zip(ops, ys)])
+    sp = arr(_P, [_dev(s, torch.float32, op.N, "s_out").value for op, s in zip(ops, s_outs)])
+    kp = arr(_P, [_dev(t, torch.int32, None, "support").value for t in supports])
+    Karr = arr(_I32, [int(k) for k in Ks])
+    Aarr = arr(_I32, [ALGOS[a] if isinstance(a, str) else int(a) for a in algos])
+    st = (CsStats * B)() if want_stats else None
+    _check(lib().cs_recover_batched(B, h, yp, Karr, Aarr, float(cg_tol), int(cg_maxit), sp, kp,
+                                    st if want_stats else None))
+    out = (s_outs, [t[:k] for t, k in zip(supports, Ks)])
+    if want_stats:
+        return out + ([s.as_dict() for s in st],)
+    return out
+
+
+class CGLeastSquares(torch.autograd.Function):
+    """s_S = LS(y; S) on a fixed support through the CUDA CG solver; backward applies the
+    hand-written adjoint dy = A_S (A_S^T A_S)^{-1} g (the support gets no gradient)."""
+
+    @staticmethod
+    def forward(ctx, y, support, op, cg_tol=1e-6, cg_maxit=100):
+        ctx.op, ctx.cg_tol, ctx.cg_maxit = op, cg_tol, cg_maxit
+        ctx.save_for_backward(support)
+        return op.ls_solve(support, y.contiguous(), cg_tol, cg_maxit)
+
+    @staticmethod
+    def backward(ctx, g):
+        (support,) = ctx.saved_tensors
+        dy = ctx.op.ls_backward(support, g.contiguous(), ctx.cg_tol, ctx.cg_maxit)
+        return dy, None, None, None, None

@@ -1,0 +1,452 @@
+// cs_api.cu -- host side of the C ABI declared in include/cs_gb300.h.
+//
+// Builds the operator's random draws and tables (Sec. III-A, Eq. 7), validates arguments,
+// packs tasks and launches the cluster engine of cs_engine.cu.  No compute happens here.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "cs_internal.h"
+
+using namespace csg;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+cs_status fail(cs_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+cs_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(CS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr uint64_t GAMMA = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t SIGN_SALT = 0xD1B54A32D192ED03ull;
+
+uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Omega: partial Fisher-Yates driven by the SplitMix64 stream seeded with seed ^ gamma,
+// j = i + (u_{i+1} mod (N - i)); the first M entries, sorted.
+std::vector<int32_t> draw_omega(int64_t N, int64_t M, uint64_t seed) {
+  std::vector<int32_t> perm((size_t)N);
+  std::iota(perm.begin(), perm.end(), 0);
+  uint64_t st = seed ^ GAMMA;
+  for (int64_t i = 0; i < M; ++i) {
+    st += GAMMA;
+    const uint64_t u = mix64(st);
+    const int64_t j = i + (int64_t)(u % (uint64_t)(N - i));
+    std::swap(perm[(size_t)i], perm[(size_t)j]);
+  }
+  std::vector<int32_t> om(perm.begin(), perm.begin() + M);
+  std::sort(om.begin(), om.end());
+  return om;
+}
+
+// d_n = -1 iff the top bit of mix((seed ^ salt) + n + gamma) is set.
+int8_t draw_sign(uint64_t sign_key, int64_t n) {
+  return (mix64(sign_key + (uint64_t)n + GAMMA) >> 63) ? (int8_t)-1 : (int8_t)1;
+}
+
+cs_status check_nm(int64_t N, int64_t M) {
+  if (!is_pow2(N) || N < N_MIN || N > N_MAX)
+    return fail(CS_ERR_UNSUPPORTED_N, "N must be a power of two in [16, 2^18], got " + std::to_string(N));
+  if (M < 1 || M > N) return fail(CS_ERR_INVALID_ARG, "M must satisfy 1 <= M <= N");
+  return CS_OK;
+}
+int log2i(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+
+}  // namespace
+
+struct cs_op {
+  int64_t N = 0, M = 0;
+  uint64_t seed = 0;
+  OpDev dev{};
+  int32_t* d_omega = nullptr;
+  uint32_t* d_omask = nullptr;
+  int32_t* d_orank = nullptr;
+  float2* d_tw = nullptr;
+  std::vector<int32_t> h_omega;
+  cudaStream_t stream = nullptr;
+  float* d_scratch = nullptr;   // one cluster's scratch
+  uint32_t* d_bits = nullptr;
+  cs_stats* d_stats = nullptr;
+};
+
+namespace {
+
+void free_op(cs_op* op) {
+  if (!op) return;
+  cudaFree(op->d_omega);
+  cudaFree(op->d_omask);
+  cudaFree(op->d_orank);
+  cudaFree(op->d_tw);
+  cudaFree(op->d_scratch);
+  cudaFree(op->d_bits);
+  cudaFree(op->d_stats);
+  delete op;
+}
+
+Task base_task(const cs_op* op, int mode) {
+  Task t{};
+  t.op = op->dev;
+  t.mode = mode;
+  t.algo = 0;
+  t.K = 0;
+  t.k_in = 0;
+  t.cg_tol = 1e-6f;
+  t.cg_maxit = 100;
+  t.outer_max = 0;
+  t.stats = op->d_stats;
+  return t;
+}
+
+Launch single_launch(const cs_op* op, const Task& t) {
+  Launch L{};
+  L.tasks = nullptr;
+  L.single = t;
+  L.ntasks = 1;
+  L.F_alloc = op->dev.F;
+  L.scratch = op->d_scratch;
+  L.scratch_per_cluster = (size_t)op->dev.P * scratch_floats_per_cta(op->dev.F);
+  L.bits = op->d_bits;
+  L.bits_per_cluster = (size_t)(op->N + 31) / 32;
+  return L;
+}
+
+cs_status run_single(cs_op* op, const Task& t) {
+  const Launch L = single_launch(op, t);
+  cudaError_t e = launch_engine(L, op->dev.P, 1, op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "engine launch");
+  return CS_OK;
+}
+
+cs_status check_cg(float cg_tol, int32_t cg_maxit) {
+  if (!(cg_tol >= 0.f) || cg_maxit < 1) return fail(CS_ERR_INVALID_ARG, "cg_tol must be >= 0 and cg_maxit >= 1");
+  return CS_OK;
+}
+
+constexpr int SP_ROUNDS = 50;     // SP outer-iteration cap
+constexpr int OMPR_SWAPS = 100;   // OMPR replacement cap
+
+}  // namespace
+
+extern "C" {
+
+const char* cs_last_error(void) { return g_err.c_str(); }
+
+cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_M_host, int8_t* d_N_host) {
+  const cs_status st = check_nm(N, M);
+  if (st != CS_OK) return st;
+  if (omega_M_host) {
+    const std::vector<int32_t> om = draw_omega(N, M, seed);
+    std::memcpy(omega_M_host, om.data(), sizeof(int32_t) * (size_t)M);
+  }
+  if (d_N_host)
+    for (int64_t n = 0; n < N; ++n) d_N_host[n] = draw_sign(seed ^ SIGN_SALT, n);
+  return CS_OK;
+}
+
+cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) {
+  if (check_nm(N, M) != CS_OK) return nullptr;
+  cs_op* op = new cs_op();
+  op->N = N;
+  op->M = M;
+  op->seed = seed;
+  op->h_omega = draw_omega(N, M, seed);
+  const int64_t W = (N + 31) / 32;
+  std::vector<uint32_t> omask((size_t)W, 0u);
+  std::vector<int32_t> orank((size_t)W, 0);
+  for (int32_t v : op->h_omega) omask[(size_t)(v >> 5)] |= 1u << (v & 31);
+  for (int64_t w = 1; w < W; ++w) orank[(size_t)w] = orank[(size_t)w - 1] + __builtin_popcount(omask[(size_t)w - 1]);
+  // twiddles omega_{4N}^j = exp(-2 pi i j / 4N), two-level split
+  const int T = log2i(4 * N);
+  const int lo_bits = (T + 1) / 2, hi_bits = T - lo_bits;
+  const int nlo = 1 << lo_bits, nhi = 1 << hi_bits;
+  std::vector<float2> tw((size_t)(nlo + nhi));
+  const double four_n = 4.0 * (double)N;
+  for (int i = 0; i < nlo; ++i) {
+    const double a = 2.0 * M_PI * (double)i / four_n;
+    tw[(size_t)i] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  for (int j = 0; j < nhi; ++j) {
+    const double a = 2.0 * M_PI * (double)((int64_t)j << lo_bits) / four_n;
+    tw[(size_t)(nlo + j)] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  const int64_t L = N / 2;
+  int P = 1, F = (int)L;
+  if (L > F_MAX) { P = (int)(L / F_MAX); F = F_MAX; }
+  OpDev& d = op->dev;
+  d.N = (int)N;
+  d.M = (int)M;
+  d.P = P;
+  d.F = F;
+  d.lo_bits = lo_bits;
+  d.hi_bits = hi_bits;
+  d.sign_key = seed ^ SIGN_SALT;
+  cudaError_t e;
+  const size_t scratch = (size_t)P * scratch_floats_per_cta(F) * sizeof(float);
+#define CSG_TRY(call)                                   \
+  if ((e = (call)) != cudaSuccess) {                    \
+    cuda_fail(e, #call);                                \
+    free_op(op);                                        \
+    return nullptr;                                     \
+  }
+  CSG_TRY(cudaMalloc(&op->d_omega, sizeof(int32_t) * (size_t)M));
+  CSG_TRY(cudaMalloc(&op->d_omask, sizeof(uint32_t) * (size_t)W));
+  CSG_TRY(cudaMalloc(&op->d_orank, sizeof(int32_t) * (size_t)W));
+  CSG_TRY(cudaMalloc(&op->d_tw, sizeof(float2) * tw.size()));
+  CSG_TRY(cudaMalloc(&op->d_scratch, scratch));
+  CSG_TRY(cudaMalloc(&op->d_bits, sizeof(uint32_t) * (size_t)W));
+  CSG_TRY(cudaMalloc(&op->d_stats, sizeof(cs_stats)));
+  CSG_TRY(cudaMemcpy(op->d_omega, op->h_omega.data(), sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice));
+  CSG_TRY(cudaMemcpy(op->d_omask, omask.data(), sizeof(uint32_t) * (size_t)W, cudaMemcpyHostToDevice));
+  CSG_TRY(cudaMemcpy(op->d_orank, orank.data(), sizeof(int32_t) * (size_t)W, cudaMemcpyHostToDevice));
+  CSG_TRY(cudaMemcpy(op->d_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+  CSG_TRY(cudaMemset(op->d_scratch, 0, scratch));
+  CSG_TRY(cudaMemset(op->d_stats, 0, sizeof(cs_stats)));
+#undef CSG_TRY
+  d.omask = op->d_omask;
+  d.orank = op->d_orank;
+  d.tw = op->d_tw;
+  if (max_active_clusters(P, F) < 1) {
+    fail(CS_ERR_UNSUPPORTED_N, "a cluster of " + std::to_string(P) + " CTAs cannot be scheduled on this device");
+    free_op(op);
+    return nullptr;
+  }
+  return op;
+}
+
+void cs_op_destroy(cs_op_t op) {
+  if (!op) return;
+  if (op->stream) cudaStreamSynchronize(op->stream);
+  else cudaDeviceSynchronize();
+  free_op(op);
+}
+
+cs_status cs_op_set_stream(cs_op_t op, void* cuda_stream) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  op->stream = (cudaStream_t)cuda_stream;
+  return CS_OK;
+}
+
+cs_status cs_op_apply(cs_op_t op, const float* x_N, float* y_M) {
+  if (!op || !x_N || !y_M) return fail(CS_ERR_INVALID_ARG, "null argument");
+  Task t = base_task(op, MODE_APPLY);
+  t.in = x_N;
+  t.out = y_M;
+  return run_single(op, t);
+}
+
+cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N) {
+  if (!op || !y_M || !x_N) return fail(CS_ERR_INVALID_ARG, "null argument");
+  Task t = base_task(op, MODE_APPLY_T);
+  t.in = y_M;
+  t.out = x_N;
+  return run_single(op, t);
+}
+
+cs_status cs_op_export(cs_op_t op, int32_t* omega_M_host, int8_t* d_N_host) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  if (omega_M_host) std::memcpy(omega_M_host, op->h_omega.data(), sizeof(int32_t) * (size_t)op->M);
+  if (d_N_host)
+    for (int64_t n = 0; n < op->N; ++n) d_N_host[n] = draw_sign(op->dev.sign_key, n);
+  return CS_OK;
+}
+
+static cs_status check_recover(const cs_op* op, const float* y, int32_t K, int algo, float* s_out,
+                               int32_t* support_out) {
+  if (!op || !y || !s_out || (K > 0 && !support_out)) return fail(CS_ERR_INVALID_ARG, "null argument");
+  if (algo < CS_OMP || algo > CS_OMPR) return fail(CS_ERR_INVALID_ARG, "unknown algo");
+  if (K < 0 || K > op->M) return fail(CS_ERR_INVALID_ARG, "K must satisfy 0 <= K <= M");
+  if (algo == CS_SP && 2 * (int64_t)K > op->M) return fail(CS_ERR_INVALID_ARG, "SP needs 2K <= M");
+  return CS_OK;
+}
+
+cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float cg_tol, int32_t cg_maxit,
+                     float* s_out, int32_t* support_out) {
+  cs_status st = check_recover(op, y, K, (int)algo, s_out, support_out);
+  if (st != CS_OK) return st;
+  if ((st = check_cg(cg_tol, cg_maxit)) != CS_OK) return st;
+  if (K == 0) {
+    cudaError_t e = cudaMemsetAsync(s_out, 0, sizeof(float) * (size_t)op->N, op->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    return CS_OK;
+  }
+  Task t = base_task(op, MODE_RECOVER);
+  t.algo = (int)algo;
+  t.K = K;
+  t.cg_tol = cg_tol;
+  t.cg_maxit = cg_maxit;
+  t.outer_max = algo == CS_SP ? SP_ROUNDS : OMPR_SWAPS;
+  t.in = y;
+  t.out = s_out;
+  t.supp_out = support_out;
+  return run_single(op, t);
+}
+
+// Launch a list of tasks grouped by cluster size; scratch and task arrays come from the
+// stream-ordered allocator and are released on the same stream.
+static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
+  std::map<int, std::vector<Task>> groups;
+  for (const Task& t : tasks) groups[t.op.P].push_back(t);
+  for (auto& kv : groups) {
+    const int P = kv.first;
+    std::vector<Task>& g = kv.second;
+    // largest work first (a static round-robin over clusters then balances reasonably)
+    std::stable_sort(g.begin(), g.end(), [](const Task& a, const Task& b) {
+      return (int64_t)a.op.N * std::max(a.K, a.k_in) > (int64_t)b.op.N * std::max(b.K, b.k_in);
+    });
+    int F_alloc = 0, Nmax = 0;
+    for (const Task& t : g) { F_alloc = std::max(F_alloc, t.op.F); Nmax = std::max(Nmax, t.op.N); }
+    const int maxc = max_active_clusters(P, F_alloc);
+    if (maxc < 1) return fail(CS_ERR_UNSUPPORTED_N, "cluster configuration cannot be scheduled");
+    const int G = std::min<int>((int)g.size(), maxc);
+    Launch L{};
+    L.ntasks = (int)g.size();
+    L.F_alloc = F_alloc;
+    L.scratch_per_cluster = (size_t)P * scratch_floats_per_cta(F_alloc);
+    L.bits_per_cluster = (size_t)(Nmax + 31) / 32;
+    Task* d_tasks = nullptr;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&d_tasks, sizeof(Task) * g.size(), stream)) != cudaSuccess) return cuda_fail(e, "alloc tasks");
+    if ((e = cudaMallocAsync(&L.scratch, sizeof(float) * L.scratch_per_cluster * G, stream)) != cudaSuccess)
+      return cuda_fail(e, "alloc scratch");
+    if ((e = cudaMallocAsync(&L.bits, sizeof(uint32_t) * L.bits_per_cluster * G, stream)) != cudaSuccess)
+      return cuda_fail(e, "alloc bits");
+    if ((e = cudaMemcpyAsync(d_tasks, g.data(), sizeof(Task) * g.size(), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload tasks");
+    L.tasks = d_tasks;
+    if ((e = launch_engine(L, P, G, stream)) != cudaSuccess) return cuda_fail(e, "engine launch");
+    cudaFreeAsync(d_tasks, stream);
+    cudaFreeAsync(L.scratch, stream);
+    cudaFreeAsync(L.bits, stream);
+  }
+  return CS_OK;
+}
+
+cs_status cs_recover_batched(int32_t B, const cs_op_t* ops, const float* const* y, const int32_t* K,
+                             const int32_t* algo, float cg_tol, int32_t cg_maxit, float* const* s_out,
+                             int32_t* const* support_out, cs_stats* stats_host) {
+  if (B < 0 || (B > 0 && (!ops || !y || !K || !algo || !s_out || !support_out)))
+    return fail(CS_ERR_INVALID_ARG, "null argument");
+  if (B == 0) return CS_OK;
+  cs_status st = check_cg(cg_tol, cg_maxit);
+  if (st != CS_OK) return st;
+  cudaStream_t stream = ops[0] ? ops[0]->stream : nullptr;
+  cs_stats* d_stats = nullptr;
+  cudaError_t e;
+  if ((e = cudaMallocAsync(&d_stats, sizeof(cs_stats) * (size_t)B, stream)) != cudaSuccess) return cuda_fail(e, "alloc stats");
+  if ((e = cudaMemsetAsync(d_stats, 0, sizeof(cs_stats) * (size_t)B, stream)) != cudaSuccess) return cuda_fail(e, "memset");
+  std::vector<Task> tasks;
+  tasks.reserve((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    if ((st = check_recover(ops[b], y[b], K[b], algo[b], s_out[b], support_out[b])) != CS_OK) {
+      cudaFreeAsync(d_stats, stream);
+      return fail(st, "signal " + std::to_string(b) + ": " + g_err);
+    }
+    if (K[b] == 0) {
+      cudaMemsetAsync(s_out[b], 0, sizeof(float) * (size_t)ops[b]->N, stream);
+      continue;
+    }
+    Task t = base_task(ops[b], MODE_RECOVER);
+    t.algo = algo[b];
+    t.K = K[b];
+    t.cg_tol = cg_tol;
+    t.cg_maxit = cg_maxit;
+    t.outer_max = algo[b] == CS_SP ? SP_ROUNDS : OMPR_SWAPS;
+    t.in = y[b];
+    t.out = s_out[b];
+    t.supp_out = support_out[b];
+    t.stats = d_stats + b;
+    tasks.push_back(t);
+  }
+  st = launch_tasks(tasks, stream);
+  if (st == CS_OK && stats_host) {
+    if ((e = cudaMemcpyAsync(stats_host, d_stats, sizeof(cs_stats) * (size_t)B, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      st = cuda_fail(e, "stats copy");
+    else if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
+      st = cuda_fail(e, "stats sync");
+  }
+  cudaFreeAsync(d_stats, stream);
+  return st;
+}
+
+static cs_status ls_batched(cs_op_t op, int mode, int32_t B, const int32_t* support, int32_t k, const float* in,
+                            float cg_tol, int32_t cg_maxit, float* out) {
+  if (!op || (B > 0 && (!support || !in || !out))) return fail(CS_ERR_INVALID_ARG, "null argument");
+  if (B < 0 || k < 0 || k > op->M) return fail(CS_ERR_INVALID_ARG, "need B >= 0 and 0 <= k <= M");
+  cs_status st = check_cg(cg_tol, cg_maxit);
+  if (st != CS_OK) return st;
+  if (B == 0) return CS_OK;
+  if (k == 0) {
+    const size_t n = mode == MODE_LS_BACKWARD ? (size_t)op->M * B : 0;
+    if (n) cudaMemsetAsync(out, 0, sizeof(float) * n, op->stream);
+    return CS_OK;
+  }
+  std::vector<Task> tasks;
+  for (int b = 0; b < B; ++b) {
+    Task t = base_task(op, mode);
+    t.k_in = k;
+    t.cg_tol = cg_tol;
+    t.cg_maxit = cg_maxit;
+    t.supp_in = support + (size_t)b * k;
+    if (mode == MODE_LS_SOLVE) {
+      t.in = in + (size_t)b * op->M;
+      t.out = out + (size_t)b * k;
+    } else {
+      t.in = in + (size_t)b * k;
+      t.out = out + (size_t)b * op->M;
+    }
+    tasks.push_back(t);
+  }
+  if (B == 1) return run_single(op, tasks[0]);
+  for (Task& t : tasks) t.stats = nullptr;
+  return launch_tasks(tasks, op->stream);
+}
+
+cs_status cs_ls_solve(cs_op_t op, const int32_t* support, int32_t k, const float* y, float cg_tol, int32_t cg_maxit,
+                      float* s_S_out) {
+  return ls_batched(op, MODE_LS_SOLVE, 1, support, k, y, cg_tol, cg_maxit, s_S_out);
+}
+
+cs_status cs_ls_backward(cs_op_t op, const int32_t* support, int32_t k, const float* g, float cg_tol,
+                         int32_t cg_maxit, float* dy_out) {
+  return ls_batched(op, MODE_LS_BACKWARD, 1, support, k, g, cg_tol, cg_maxit, dy_out);
+}
+
+cs_status cs_ls_solve_batched(cs_op_t op, int32_t B, const int32_t* support, int32_t k, const float* y,
+                              float cg_tol, int32_t cg_maxit, float* s_S_out) {
+  return ls_batched(op, MODE_LS_SOLVE, B, support, k, y, cg_tol, cg_maxit, s_S_out);
+}
+
+cs_status cs_ls_backward_batched(cs_op_t op, int32_t B, const int32_t* support, int32_t k, const float* g,
+                                 float cg_tol, int32_t cg_maxit, float* dy_out) {
+  return ls_batched(op, MODE_LS_BACKWARD, B, support, k, g, cg_tol, cg_maxit, dy_out);
+}
+
+cs_status cs_get_stats(cs_op_t op, cs_stats* out) {
+  if (!op || !out) return fail(CS_ERR_INVALID_ARG, "null argument");
+  cudaError_t e = cudaStreamSynchronize(op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  e = cudaMemcpy(out, op->d_stats, sizeof(cs_stats), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "stats copy");
+  return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1191 @@
+// cs_engine.cu -- cluster-resident device engine for the greedy CS decoders (sm_103a).
+//
+// One thread-block cluster of P CTAs (P = 1..16) owns one signal.  The N-point orthonormal
+// DCT-II / DCT-III behind A = P_Omega C_N diag(d) (Sec. III-A, Eq. 7) is computed through an
+// L = N/2 point complex FFT (Makhoul's reordering, J. Makhoul, IEEE TASSP 1980) that lives
+// entirely in the cluster's shared memory:
+//
+//   * CTA p holds z[q P + p] (q < Q = L/P, "stride-P" layout) and runs a Q-point Stockham FFT
+//     in shared memory (radix 16/8/4/2 butterflies in registers);
+//   * a twiddle omega_L^{p k_q}, an all-to-all pull over distributed shared memory, and
+//     P-point DFTs across CTAs finish the four-step FFT; CTA c then holds the frequency slots
+//     k_q in [c h, c h + h) and their mirrors Q - k_q (h = Q / 2P), so each DCT output pair
+//     (k, L - k) is CTA-local;
+//   * the DCT post-processing, the Omega mask / residual / output step, and the DCT-III
+//     pre-processing all happen in that frequency layout, and the inverse path mirrors the
+//     forward one.
+//
+// Signal-domain values stay in the FFT buffer in "slot" order: real slot sigma = 2 q + b of
+// CTA p is signal index n(p, sigma) (see n_of_slot).  The support W_S of Eq. 8 is a per-CTA
+// bitmask over slots; CG vectors are compressed to the support entries a CTA owns, so the
+// scatter W x and the gather W^T of Algorithm 1 are CTA-local.
+//
+// Every barrier is a hardware barrier (__syncthreads or barrier.cluster); every branch around
+// a barrier depends only on task parameters or on cluster-reduced values that all CTAs compute
+// in the same order, so control flow is uniform across the cluster and no wait can spin.
+#include <cooperative_groups.h>
+
+#include "cs_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace csg {
+
+// ------------------------------------------------------------------------------- helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmuli(float2 a) { return make_float2(-a.y, a.x); }   // a * i
+
+// cos(2 pi j / 16): exact mathematical constants.
+__device__ __forceinline__ float cos16(int j) {
+  switch (j & 15) {
+    case 0: return 1.0f;
+    case 1: case 15: return 0.92387953251128674f;
+    case 2: case 14: return 0.70710678118654752f;
+    case 3: case 13: return 0.38268343236508977f;
+    case 4: case 12: return 0.0f;
+    case 5: case 11: return -0.38268343236508977f;
+    case 6: case 10: return -0.70710678118654752f;
+    case 7: case 9: return -0.92387953251128674f;
+    default: return -1.0f;
+  }
+}
+__device__ __forceinline__ float sin16(int j) { return cos16(j - 4); }
+
+// b * omega_16^t with omega = exp(DIR * 2 pi i / 16); t is a compile-time constant after unrolling.
+template <int DIR>
+__device__ __forceinline__ float2 mul_w16(float2 b, int t) {
+  t &= 15;
+  if (t == 0) return b;
+  if (t == 8) return make_float2(-b.x, -b.y);
+  if (t == 4) return DIR > 0 ? cmuli(b) : make_float2(b.y, -b.x);
+  if (t == 12) return DIR > 0 ? make_float2(b.y, -b.x) : cmuli(b);
+  return cmul(b, make_float2(cos16(t), DIR * sin16(t)));
+}
+
+__host__ __device__ constexpr int brev_bits(int x, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+template <int R> struct Lg { static constexpr int v = R <= 1 ? 0 : 1 + Lg<R / 2>::v; };
+template <> struct Lg<1> { static constexpr int v = 0; };
+
+// In-register R-point DFT, natural order in and out (iterative radix-2 decimation in time).
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2* v) {
+  if constexpr (R > 1) {
+    constexpr int LG = Lg<R>::v;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int j = brev_bits(i, LG);
+      if (j > i) { float2 t = v[i]; v[i] = v[j]; v[j] = t; }
+    }
+#pragma unroll
+    for (int len = 2; len <= R; len <<= 1) {
+      const int half = len >> 1;
+#pragma unroll
+      for (int i = 0; i < R; i += len) {
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+          const float2 a = v[i + j];
+          const float2 b = mul_w16<DIR>(v[i + j + half], j * (16 / len));
+          v[i + j] = cadd(a, b);
+          v[i + j + half] = csub(a, b);
+        }
+      }
+    }
+  }
+}
+
+// Padded index into the local FFT buffer (one spare element every 16 keeps the strided
+// Stockham stores of the early passes free of shared-memory bank conflicts).
+__device__ __forceinline__ int aidx(int q) { return q + (q >> 4); }
+__host__ __device__ inline int apad(int F) { return F + F / 16; }
+
+// Two-level twiddle table: omega_{4N}^j = exp(-2 pi i j / 4N) = lo[j & m] * hi[j >> lo_bits].
+struct Tw {
+  const float2* lo;
+  const float2* hi;
+  int lo_bits;
+  int lo_mask;
+  int mask4n;   // 4N - 1
+  template <int DIR>
+  __device__ __forceinline__ float2 get(int j) const {
+    j &= mask4n;
+    const float2 w = cmul(lo[j & lo_mask], hi[j >> lo_bits]);
+    return DIR > 0 ? cconj(w) : w;
+  }
+};
+
+// v[r] *= w^r with w = omega_{4N}^t (DIR < 0) or its conjugate; powers built from w, w^2,
+// w^4, w^8 read from the table, so every factor carries at most three rounded products.
+template <int R, int DIR>
+__device__ __forceinline__ void twiddle_powers(float2* v, const Tw& tw, int t) {
+  const float2 w1 = tw.get<DIR>(t);
+  v[1] = cmul(v[1], w1);
+  if constexpr (R >= 4) {
+    const float2 w2 = tw.get<DIR>(2 * t);
+    const float2 w3 = cmul(w1, w2);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    if constexpr (R >= 8) {
+      const float2 w4 = tw.get<DIR>(4 * t);
+      v[4] = cmul(v[4], w4);
+      v[5] = cmul(v[5], cmul(w1, w4));
+      v[6] = cmul(v[6], cmul(w2, w4));
+      v[7] = cmul(v[7], cmul(w3, w4));
+      if constexpr (R >= 16) {
+        const float2 w8 = tw.get<DIR>(8 * t);
+        v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], cmul(w1, w8));
+        v[10] = cmul(v[10], cmul(w2, w8));
+        v[11] = cmul(v[11], cmul(w3, w8));
+        v[12] = cmul(v[12], cmul(w4, w8));
+        v[13] = cmul(v[13], cmul(cmul(w1, w4), w8));
+        v[14] = cmul(v[14], cmul(cmul(w2, w4), w8));
+        v[15] = cmul(v[15], cmul(cmul(w3, w4), w8));
+      }
+    }
+  }
+}
+
+// One in-place Stockham pass of radix R over the F-point buffer X (padded indexing).
+// All R-point groups are loaded into registers before any store (F <= 16 * NT).
+template <int R, int DIR>
+__device__ __noinline__ void fft_pass(float2* X, int F, int Ns, const Tw& tw, int four_n) {
+  constexpr int BPT = 16 / R;
+  const int nb = F / R;
+  float2 v[BPT][R];
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int j = threadIdx.x + b * NT;
+    if (j < nb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = X[aidx(j + r * nb)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int j = threadIdx.x + b * NT;
+    if (j < nb) {
+      const int k = j & (Ns - 1);
+      if (Ns > 1) twiddle_powers<R, DIR>(v[b], tw, k * (four_n / (Ns * R)));
+      dft<R, DIR>(v[b]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) X[aidx(base + r * Ns)] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Q-point FFT of the local buffer, natural order in and out.
+template <int DIR>
+__device__ __noinline__ void local_fft(float2* X, int F, const Tw& tw, int four_n) {
+  int Ns = 1;
+  while (Ns < F) {
+    const int rem = F / Ns;
+    if (rem >= 16) { fft_pass<16, DIR>(X, F, Ns, tw, four_n); Ns *= 16; }
+    else if (rem == 8) { fft_pass<8, DIR>(X, F, Ns, tw, four_n); Ns *= 8; }
+    else if (rem == 4) { fft_pass<4, DIR>(X, F, Ns, tw, four_n); Ns *= 4; }
+    else { fft_pass<2, DIR>(X, F, Ns, tw, four_n); Ns *= 2; }
+  }
+}
+
+// P-point DFT across CTAs, one frequency slot column per thread; B is laid out [p][s].
+template <int R, int DIR>
+__device__ __forceinline__ void pcol(float2* B, int s, int S2) {
+  float2 v[R];
+#pragma unroll
+  for (int p = 0; p < R; ++p) v[p] = B[p * S2 + s];
+  dft<R, DIR>(v);
+#pragma unroll
+  for (int p = 0; p < R; ++p) B[p * S2 + s] = v[p];
+}
+template <int DIR>
+__device__ __noinline__ void pstep(float2* B, int P, int S2) {
+  if (P > 1) {
+    for (int s = threadIdx.x; s < S2; s += NT) {
+      switch (P) {
+        case 2: pcol<2, DIR>(B, s, S2); break;
+        case 4: pcol<4, DIR>(B, s, S2); break;
+        case 8: pcol<8, DIR>(B, s, S2); break;
+        default: pcol<16, DIR>(B, s, S2); break;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------ reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// ------------------------------------------------------------------------- shared layout
+struct Smem {
+  float2* A;          // local FFT buffer (padded), signal-domain slots between transforms
+  float2* B;          // exchange / frequency buffer [P][2h]
+  float2* twlo;
+  float2* twhi;
+  uint32_t* signw;    // d_n bits per local slot (1 = -1)
+  uint32_t* mask[2];  // support bitmasks over local slots
+  uint32_t* hist;     // [2][256]
+  uint32_t* htot;     // [256]
+  float* ring;        // [4][4] cluster-reduction partials
+  unsigned long long* ring64;   // [4][2]
+  float* wsum;        // [4][16] warp partials
+  unsigned long long* wmax;     // [2][16]
+  int* iscr;          // [64] integer scratch / broadcast
+  float* fscr;        // [8]
+};
+
+__device__ Smem carve(unsigned char* base, int F_alloc) {
+  Smem s;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { unsigned char* p = base + off; off += (bytes + 15) & ~size_t(15); return p; };
+  s.A = (float2*)take(sizeof(float2) * apad(F_alloc));
+  s.B = (float2*)take(sizeof(float2) * F_alloc);
+  s.twlo = (float2*)take(sizeof(float2) * 1024);
+  s.twhi = (float2*)take(sizeof(float2) * 1024);
+  const int nw = (2 * F_alloc + 31) / 32;
+  s.signw = (uint32_t*)take(4 * nw);
+  s.mask[0] = (uint32_t*)take(4 * nw);
+  s.mask[1] = (uint32_t*)take(4 * nw);
+  s.hist = (uint32_t*)take(4 * 512);
+  s.htot = (uint32_t*)take(4 * 256);
+  s.ring = (float*)take(4 * 16);
+  s.ring64 = (unsigned long long*)take(8 * 8);
+  s.wsum = (float*)take(4 * 64);
+  s.wmax = (unsigned long long*)take(8 * 32);
+  s.iscr = (int*)take(4 * 64);
+  s.fscr = (float*)take(4 * 8);
+  return s;
+}
+
+size_t smem_bytes(int F_alloc) {
+  auto r = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const int nw = (2 * F_alloc + 31) / 32;
+  return r(sizeof(float2) * apad(F_alloc)) + r(sizeof(float2) * F_alloc) + 2 * r(sizeof(float2) * 1024) +
+         3 * r(4 * nw) + r(4 * 512) + r(4 * 256) + r(4 * 16) + r(8 * 8) + r(4 * 64) + r(8 * 32) + r(4 * 64) +
+         r(4 * 8);
+}
+
+// ---------------------------------------------------------------------- per-signal context
+enum MidKind : int { MID_MASK = 0, MID_RESID = 1, MID_OUT = 2, MID_IN = 3 };
+enum SrcKind : int { SRC_NONE = 0, SRC_CG = 1, SRC_DENSE_SLOTS = 2, SRC_GLOBAL_N = 3 };
+
+struct Ctx {
+  cg::cluster_group cl;
+  Smem sm;
+  Tw tw;
+  int N, M, L, P, F, h, S2, c, nwords, four_n;
+  const uint32_t* omask;
+  const int32_t* orank;
+  // global per-CTA scratch
+  float* xd[2];
+  float* cy;
+  int* list;
+  float* cgx;
+  float* cgr;
+  float* cgp;
+  float* cgq;
+  uint32_t* bits;     // per-cluster N-bit output bitmask
+  int ring_slot;
+  int hist_slot;
+  int cg_total;
+  int cg_hits;
+};
+
+__device__ __forceinline__ float& slot_ref(float2* A, int sigma) {
+  return reinterpret_cast<float*>(A)[2 * aidx(sigma >> 1) + (sigma & 1)];
+}
+// Signal index of local real slot sigma of CTA c: complex point m = q P + c of z, real index
+// v = 2 m + b of Makhoul's reordered sequence, v < N/2 -> n = 2 v, else n = 2 (N - 1 - v) + 1.
+__device__ __forceinline__ int n_of_slot(const Ctx& x, int sigma) {
+  const int m = (sigma >> 1) * x.P + x.c;
+  const int v = 2 * m + (sigma & 1);
+  return v < (x.N >> 1) ? 2 * v : 2 * (x.N - 1 - v) + 1;
+}
+__device__ __forceinline__ void slot_of_n(const Ctx& x, int n, int& owner, int& sigma) {
+  const int v = (n & 1) ? x.N - 1 - (n >> 1) : (n >> 1);
+  const int m = v >> 1;
+  owner = m % x.P;
+  sigma = 2 * (m / x.P) + (v & 1);
+}
+__device__ __forceinline__ float sgn(const Ctx& x, int sigma) {
+  return (x.sm.signw[sigma >> 5] >> (sigma & 31)) & 1u ? -1.0f : 1.0f;
+}
+__device__ __forceinline__ bool mask_bit(const uint32_t* m, int sigma) { return (m[sigma >> 5] >> (sigma & 31)) & 1u; }
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+// Frequency slot k_q held by slot s of CTA c (mirror-paired assignment).
+__device__ __forceinline__ int kq_of(const Ctx& x, int s) {
+  const int Q = x.F;
+  if (s < x.h) return x.c * x.h + s;
+  const int j = x.c * x.h + s - x.h;
+  return j == 0 ? (Q >> 1) : Q - j;
+}
+__device__ __forceinline__ void owner_of_kq(const Ctx& x, int k, int& c, int& s) {
+  const int Q = x.F;
+  if (k < (Q >> 1)) { c = k / x.h; s = k - c * x.h; }
+  else if (k == (Q >> 1)) { c = 0; s = x.h; }
+  else { const int j = Q - k; c = j / x.h; s = x.h + (j - c * x.h); }
+}
+
+// ---------------------------------------------------------------- cluster-wide reductions
+// Sum n (<= 4) per-thread values over the whole cluster; every thread gets the totals, and
+// every CTA adds the partials in rank order, so all CTAs hold bit-identical results.
+__device__ __noinline__ void cluster_sum(Ctx& x, float* v, int n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < n; ++i) {
+    const float s = warp_sum(v[i]);
+    if (lane == 0) x.sm.wsum[i * 16 + warp] = s;
+  }
+  __syncthreads();
+  float* ring = x.sm.ring + 4 * x.ring_slot;
+  if (threadIdx.x < n) {
+    float t = 0.f;
+    for (int w = 0; w < NT / 32; ++w) t += x.sm.wsum[threadIdx.x * 16 + w];
+    ring[threadIdx.x] = t;
+  }
+  x.cl.sync();
+  if (warp == 0) {
+    for (int i = 0; i < n; ++i) {
+      float t = 0.f;
+      if (lane < x.P) t = *x.cl.map_shared_rank(ring + i, lane);
+      // fixed-shape tree over 32 lanes: identical order in every CTA
+      t = warp_sum(t);
+      if (lane == 0) x.sm.fscr[i] = t;
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < n; ++i) v[i] = x.sm.fscr[i];
+  x.ring_slot = (x.ring_slot + 1) & 3;
+}
+
+// Max of up to two 64-bit keys over the cluster.
+__device__ __noinline__ void cluster_max64(Ctx& x, unsigned long long* v, int n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < n; ++i) {
+    const unsigned long long s = warp_max64(v[i]);
+    if (lane == 0) x.sm.wmax[i * 16 + warp] = s;
+  }
+  __syncthreads();
+  unsigned long long* ring = x.sm.ring64 + 2 * x.ring_slot;
+  if (threadIdx.x < n) {
+    unsigned long long t = 0;
+    for (int w = 0; w < NT / 32; ++w) t = max(t, x.sm.wmax[threadIdx.x * 16 + w]);
+    ring[threadIdx.x] = t;
+  }
+  x.cl.sync();
+  if (warp == 0) {
+    for (int i = 0; i < n; ++i) {
+      unsigned long long t = 0;
+      if (lane < x.P) t = *x.cl.map_shared_rank(ring + i, lane);
+      t = warp_max64(t);
+      if (lane == 0) x.sm.iscr[2 * i] = (int)(t & 0xffffffffu), x.sm.iscr[2 * i + 1] = (int)(t >> 32);
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < n; ++i)
+    v[i] = ((unsigned long long)(uint32_t)x.sm.iscr[2 * i + 1] << 32) | (uint32_t)x.sm.iscr[2 * i];
+  __syncthreads();
+  x.ring_slot = (x.ring_slot + 1) & 3;
+}
+
+// Exclusive block scan of one int per thread; returns the exclusive prefix, total via *tot.
+__device__ __noinline__ int block_scan(Ctx& x, int v, int* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) x.sm.iscr[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < NT / 32 ? x.sm.iscr[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < NT / 32) x.sm.iscr[32 + lane] = wi - w;
+    if (lane == 31) x.sm.iscr[63] = wi;
+  }
+  __syncthreads();
+  const int ex = x.sm.iscr[32 + warp] + inc - v;
+  *tot = x.sm.iscr[63];
+  __syncthreads();
+  return ex;
+}
+
+// Rebuild this CTA's sorted support list (local slots) from a bitmask; returns its length.
+__device__ __noinline__ int build_list(Ctx& x, const uint32_t* m) {
+  const int w = threadIdx.x;
+  const uint32_t word = w < x.nwords ? m[w] : 0u;
+  int total;
+  int off = block_scan(x, __popc(word), &total);
+  uint32_t bitsleft = word;
+  while (bitsleft) {
+    const int b = __ffs(bitsleft) - 1;
+    bitsleft &= bitsleft - 1;
+    x.list[off++] = w * 32 + b;
+  }
+  __syncthreads();
+  return total;
+}
+
+// ------------------------------------------------------------------- the transform pair
+// Frequency-domain stage: DCT-II post-processing of the pair (Z_k, Z_{L-k}), the Omega step,
+// and DCT-III pre-processing back into the pair.  Returns this thread's sum of squares of the
+// residual (MID_RESID).
+__device__ __noinline__ float freq_stage(Ctx& x, int kind, bool fwd_done, bool inv_next, const float* vin, float* vout) {
+  const int P = x.P, h = x.h, S2 = x.S2, Q = x.F, L = x.L, N = x.N;
+  const float wk = sqrtf(2.0f / (float)N), w0 = sqrtf(1.0f / (float)N);
+  const int ntask = h * P + (x.c == 0 ? 1 : 0);
+  const int ncol0 = P > 1 ? P / 2 + 1 : 1;
+  const int ncolh = P > 1 ? P / 2 : 1;
+  float acc = 0.f;
+  for (int t = threadIdx.x; t < ntask; t += NT) {
+    int sa, kpa, sb, kpb;
+    if (x.c == 0 && t < ncol0) { sa = 0; kpa = t; sb = 0; kpb = (P - t) & (P - 1); }
+    else if (x.c == 0 && t < ncol0 + ncolh) { const int u = t - ncol0; sa = h; kpa = u; sb = h; kpb = P - 1 - u; }
+    else if (x.c == 0) {
+      const int u = t - ncol0 - ncolh;
+      sa = 1 + u % (h - 1); kpa = u / (h - 1); sb = sa + h; kpb = P - 1 - kpa;
+    } else { sa = t % h; kpa = t / h; sb = sa + h; kpb = P - 1 - kpa; }
+    const bool self = (sa == sb) && (kpa == kpb);
+    const int k = kq_of(x, sa) + Q * kpa;
+    int f[4];
+    float X[4] = {0.f, 0.f, 0.f, 0.f};
+    int nf;
+    if (k == 0) { f[0] = 0; f[1] = L; nf = 2; }
+    else if (self) { f[0] = k; f[1] = N - k; nf = 2; }
+    else { f[0] = k; f[1] = N - k; f[2] = L + k; f[3] = L - k; nf = 4; }
+    if (fwd_done) {
+      const float2 Za = x.sm.B[kpa * S2 + sa];
+      const float2 Zb = x.sm.B[kpb * S2 + sb];
+      const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
+      const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
+      const float2 tO = cmul(x.tw.get<-1>(4 * k), O);
+      const float2 u1 = cmul(x.tw.get<-1>(k), cadd(E, tO));
+      const float2 u2 = cmul(x.tw.get<-1>(k + L), csub(E, tO));
+      if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
+      else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i < nf) {
+        const int fi = f[i];
+        const uint32_t word = x.omask[fi >> 5];
+        const bool in = (word >> (fi & 31)) & 1u;
+        if (kind == MID_MASK) {
+          if (!in) X[i] = 0.f;
+        } else {
+          int rk = 0;
+          if (in) rk = x.orank[fi >> 5] + __popc(word & ((1u << (fi & 31)) - 1u));
+          if (kind == MID_RESID) {
+            X[i] = in ? vin[rk] - X[i] : 0.f;
+            acc = fmaf(X[i], X[i], acc);
+          } else if (kind == MID_OUT) {
+            if (in) vout[rk] = X[i];
+          } else {   // MID_IN
+            X[i] = in ? vin[rk] : 0.f;
+          }
+        }
+      }
+    }
+    if (inv_next) {
+      float X4[4];
+      if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
+      else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
+      else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
+      // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
+      const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
+      const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
+      const float2 V1 = cmul(x.tw.get<1>(k), u1);
+      const float2 V2 = cmul(x.tw.get<1>(k + L), u2);
+      const float2 E = cscale(cadd(V1, V2), 0.5f);
+      const float2 O = cmul(cscale(csub(V1, V2), 0.5f), x.tw.get<1>(4 * k));
+      x.sm.B[kpa * S2 + sa] = cadd(E, cmuli(O));
+      if (!self) x.sm.B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
+    }
+  }
+  return acc;
+}
+
+// One application of A (forward), A^T (inverse) or A^T mask A, driven by src / kind.
+//   src   SRC_NONE: the forward input is zero (skip the forward transform)
+//         SRC_CG: compressed CG vector cgp on the local list (nloc entries)
+//         SRC_DENSE_SLOTS: dense-by-slot array `dense` read on the local list
+//         SRC_GLOBAL_N: dense signal vector `gin` of length N in global memory
+//   kind  frequency step (mask Omega / residual with y / write y_M / read u_M)
+//   inv   run the DCT-III back to the signal domain (result left in the A buffer)
+// Returns this thread's MID_RESID partial.
+__device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* dense, const float* gin, int kind, bool inv,
+                           const float* vin, float* vout) {
+  const int F = x.F;
+  float2* A = x.sm.A;
+  if (src != SRC_NONE) {
+    if (src == SRC_GLOBAL_N) {
+      for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(x, sg)] * sgn(x, sg);
+    } else {
+      for (int q = threadIdx.x; q < apad(F); q += NT) A[q] = make_float2(0.f, 0.f);
+      __syncthreads();
+      if (src == SRC_CG) {
+        for (int i = threadIdx.x; i < nloc; i += NT) {
+          const int sg = x.list[i];
+          slot_ref(A, sg) = x.cgp[i] * sgn(x, sg);
+        }
+      } else {
+        for (int i = threadIdx.x; i < nloc; i += NT) {
+          const int sg = x.list[i];
+          slot_ref(A, sg) = dense[sg] * sgn(x, sg);
+        }
+      }
+    }
+    __syncthreads();
+    local_fft<-1>(A, F, x.tw, x.four_n);
+    x.cl.sync();                                    // every CTA's A is final
+    {
+      const int S2 = x.S2;
+      for (int idx = threadIdx.x; idx < x.P * S2; idx += NT) {
+        const int p = idx / S2, s = idx - p * S2;
+        const int k = kq_of(x, s);
+        const float2* Ap = x.cl.map_shared_rank(A, p);
+        x.sm.B[idx] = cmul(Ap[aidx(k)], x.tw.get<-1>(8 * p * k));
+      }
+    }
+    __syncthreads();
+    pstep<-1>(x.sm.B, x.P, x.S2);
+  } else {
+    x.cl.sync();                                    // nobody still reads this CTA's B
+  }
+  const float acc = freq_stage(x, kind, src != SRC_NONE, inv, vin, vout);
+  __syncthreads();
+  if (inv) {
+    pstep<1>(x.sm.B, x.P, x.S2);
+    x.cl.sync();                                    // every CTA's B is final
+    for (int k = threadIdx.x; k < F; k += NT) {
+      int cc, s;
+      owner_of_kq(x, k, cc, s);
+      const float2* Bc = x.cl.map_shared_rank(x.sm.B, cc);
+      A[aidx(k)] = cmul(Bc[x.c * x.S2 + s], x.tw.get<1>(8 * x.c * k));
+    }
+    __syncthreads();
+    local_fft<1>(A, F, x.tw, x.four_n);
+  } else {
+    x.cl.sync();                                    // nobody still reads this CTA's A
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------------------ selection
+// Radix select (8-bit digits, most significant first) of the K largest nonzero keys over the
+// cluster.  On return: keys > *tau are selected and *need more are to be taken among the keys
+// equal to *tau; *eq is the cluster-wide count of keys equal to *tau.
+template <class KeyFn>
+__device__ void radix_select(Ctx& x, int count, int K, KeyFn key, uint32_t* tau, int* need, int* eq) {
+  uint32_t prefix = 0, pmask = 0;
+  int nd = K;
+  int last_eq = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    uint32_t* hist = x.sm.hist + 256 * x.hist_slot;
+    if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += NT) {
+      const uint32_t kk = key(i);
+      if (kk != 0u && (kk & pmask) == prefix) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
+    }
+    x.cl.sync();
+    if (threadIdx.x < 256) {
+      uint32_t t = 0;
+      for (int r = 0; r < x.P; ++r) t += *x.cl.map_shared_rank(hist + threadIdx.x, r);
+      x.sm.htot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // lane l owns digits [8 l, 8 l + 8); suffix sums from the top digit down
+      const int lane = threadIdx.x;
+      uint32_t mine = 0;
+      for (int d = 0; d < 8; ++d) mine += x.sm.htot[8 * lane + d];
+      uint32_t suf = mine;   // inclusive suffix over lanes >= lane
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(0xffffffffu, suf, o);
+        if (lane + o < 32) suf += t;
+      }
+      const uint32_t above = suf - mine;   // keys with digit in higher lanes
+      // the threshold digit is in the lane with above < nd <= suf
+      if (above < (uint32_t)nd && (uint32_t)nd <= suf) {
+        uint32_t acc = above;
+        int d = 7;
+        for (; d > 0; --d) {
+          const uint32_t cnt = x.sm.htot[8 * lane + d];
+          if (acc + cnt >= (uint32_t)nd) break;
+          acc += cnt;
+        }
+        x.sm.iscr[0] = 8 * lane + d;
+        x.sm.iscr[1] = (int)acc;                      // keys strictly above the digit
+        x.sm.iscr[2] = (int)x.sm.htot[8 * lane + d];  // keys equal to the digit (so far)
+      }
+      if (lane == 0 && suf < (uint32_t)nd) {          // fewer candidates than requested
+        x.sm.iscr[0] = -1;
+        x.sm.iscr[1] = (int)suf;
+        x.sm.iscr[2] = 0;
+      }
+    }
+    __syncthreads();
+    const int dig = x.sm.iscr[0];
+    const int above = x.sm.iscr[1];
+    last_eq = x.sm.iscr[2];
+    __syncthreads();
+    x.hist_slot ^= 1;
+    if (dig < 0) {   // take every candidate (uniform decision)
+      *tau = 0u; *need = 0; *eq = 0;
+      return;
+    }
+    nd -= above;
+    prefix |= (uint32_t)dig << shift;
+    pmask |= 255u << shift;
+  }
+  *tau = prefix;
+  *need = nd;
+  *eq = last_eq;
+}
+
+// Select the K largest keys (ties towards the lowest signal index) and call mark(i) for each
+// selected index; the second radix pass on the index only runs when the threshold is tied.
+template <class KeyFn, class IdxFn, class MarkFn>
+__device__ void select_topk(Ctx& x, int count, int K, KeyFn key, IdxFn nidx, MarkFn mark) {
+  uint32_t tau;
+  int need, eq;
+  radix_select(x, count, K, key, &tau, &need, &eq);
+  if (need > 0 && eq > need) {
+    const uint32_t N = (uint32_t)x.N;
+    uint32_t tau2;
+    int need2, eq2;
+    radix_select(
+        x, count, need, [&](int i) { return key(i) == tau ? N - (uint32_t)nidx(i) : 0u; }, &tau2, &need2, &eq2);
+    for (int i = threadIdx.x; i < count; i += NT) {
+      const uint32_t kk = key(i);
+      if (kk > tau || (kk == tau && N - (uint32_t)nidx(i) >= tau2)) mark(i);
+    }
+  } else {
+    for (int i = threadIdx.x; i < count; i += NT) {
+      const uint32_t kk = key(i);
+      if (kk != 0u && kk >= tau) mark(i);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t abs_key(float v) { return (__float_as_uint(v) & 0x7fffffffu) + 1u; }
+
+// ------------------------------------------------------------------------------------ CG
+enum R0Src : int { R0_FROM_A = 0, R0_FROM_CY = 1 };
+
+// Algorithm 1's CG on H = W A^T A W restricted to the support in the local list (Theorem 5's
+// |S|-compressed form), b = W A^T y whose by-slot values are in cy.  Start from x0 = xd[wi]
+// on the list (warm) or 0, with r0 = b - H x0 taken from the A buffer (R0_FROM_A: the caller
+// has just computed A^T (y - A x0)) or from cy (R0_FROM_CY, x0 = 0).  Loop while
+// ||r_j|| > tol ||b|| (the printed loop test is read as its negation) and j < maxit.
+__device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r0src, float tol, int maxit) {
+  float* xd = x.xd[wi];
+  float v[2] = {0.f, 0.f};
+  for (int i = threadIdx.x; i < nloc; i += NT) {
+    const int sg = x.list[i];
+    const float x0 = warm ? xd[sg] : 0.f;
+    const float r0 = r0src == R0_FROM_A ? slot_ref(x.sm.A, sg) * sgn(x, sg) : x.cy[sg];
+    const float b = x.cy[sg];
+    x.cgx[i] = x0;
+    x.cgr[i] = r0;
+    x.cgp[i] = r0;
+    v[0] = fmaf(r0, r0, v[0]);
+    v[1] = fmaf(b, b, v[1]);
+  }
+  cluster_sum(x, v, 2);
+  float rr = v[0];
+  const float stop2 = tol * tol * v[1];
+  int it = 0;
+  while (it < maxit && rr > stop2) {
+    transform(x, SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
+    float pq = 0.f;
+    for (int i = threadIdx.x; i < nloc; i += NT) {
+      const int sg = x.list[i];
+      const float q = slot_ref(x.sm.A, sg) * sgn(x, sg);
+      x.cgq[i] = q;
+      pq = fmaf(x.cgp[i], q, pq);
+    }
+    cluster_sum(x, &pq, 1);
+    const float alpha = rr / pq;
+    float rn = 0.f;
+    for (int i = threadIdx.x; i < nloc; i += NT) {
+      x.cgx[i] = fmaf(alpha, x.cgp[i], x.cgx[i]);
+      const float r = fmaf(-alpha, x.cgq[i], x.cgr[i]);
+      x.cgr[i] = r;
+      rn = fmaf(r, r, rn);
+    }
+    cluster_sum(x, &rn, 1);
+    const float beta = rn / rr;
+    rr = rn;
+    for (int i = threadIdx.x; i < nloc; i += NT) x.cgp[i] = fmaf(beta, x.cgp[i], x.cgr[i]);
+    ++it;
+  }
+  x.cg_total += it;
+  if (it >= maxit && rr > stop2) x.cg_hits += 1;
+  for (int i = threadIdx.x; i < nloc; i += NT) xd[x.list[i]] = x.cgx[i];
+  __syncthreads();
+}
+
+// Residual-correlation: A buffer <- C^T P^T (y - A xd) (unsigned slots), returns ||y - A xd||^2.
+__device__ __noinline__ float resid_corr(Ctx& x, int wi, int nloc, const float* y) {
+  float v = transform(x, SRC_DENSE_SLOTS, nloc, x.xd[wi], nullptr, MID_RESID, true, y, nullptr);
+  cluster_sum(x, &v, 1);
+  return v;
+}
+
+// Correlation of the slot c(sigma) = d_n (C^T ...)_n held in the A buffer.
+__device__ __forceinline__ float corr(const Ctx& x, int sg) { return slot_ref(x.sm.A, sg) * sgn(x, sg); }
+
+// ------------------------------------------------------------------------ task execution
+__device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int nloc, float rn2, int outer) {
+  const int N = x.N, P = x.P;
+  // zero s_out and the output bitmask (contiguous share per CTA)
+  const int per = N / P;
+  for (int i = threadIdx.x; i < per; i += NT) t.out[x.c * per + i] = 0.f;
+  const int W = (N + 31) / 32;
+  const int wper = (W + P - 1) / P;
+  for (int i = threadIdx.x; i < wper; i += NT) {
+    const int w = x.c * wper + i;
+    if (w < W) x.bits[w] = 0u;
+  }
+  x.cl.sync();
+  for (int i = threadIdx.x; i < nloc; i += NT) {
+    const int sg = x.list[i];
+    const int n = n_of_slot(x, sg);
+    t.out[n] = x.xd[wi][sg];
+    atomicOr(&x.bits[n >> 5], 1u << (n & 31));
+  }
+  x.cl.sync();
+  // sorted support: CTA c compacts words [c wper, (c+1) wper)
+  int cnt = 0;
+  for (int i = threadIdx.x; i < wper; i += NT) {
+    const int w = x.c * wper + i;
+    if (w < W) cnt += __popc(x.bits[w]);
+  }
+  float fc = (float)cnt;   // counts < 2^24: exact in FP32
+  // per-CTA total into ring, then exclusive prefix over ranks
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float s = warp_sum(fc);
+    if (lane == 0) x.sm.wsum[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float tt = 0.f;
+      for (int w = 0; w < NT / 32; ++w) tt += x.sm.wsum[w];
+      x.sm.ring[4 * x.ring_slot] = tt;
+    }
+    x.cl.sync();
+    if (threadIdx.x == 0) {
+      float off = 0.f;
+      for (int r = 0; r < x.c; ++r) off += *x.cl.map_shared_rank(x.sm.ring + 4 * x.ring_slot, r);
+      x.sm.iscr[40] = (int)off;
+    }
+    __syncthreads();
+    x.ring_slot = (x.ring_slot + 1) & 3;
+  }
+  int base = x.sm.iscr[40];
+  __syncthreads();
+  // block-ordered compaction: wper words per CTA, processed NT at a time
+  for (int w0 = 0; w0 < wper; w0 += NT) {
+    const int w = x.c * wper + w0 + threadIdx.x;
+    const uint32_t word = (w0 + threadIdx.x < wper && w < W) ? x.bits[w] : 0u;
+    int tot;
+    int off = base + block_scan(x, __popc(word), &tot);
+    uint32_t b = word;
+    while (b) {
+      const int j = __ffs(b) - 1;
+      b &= b - 1;
+      if (off < t.K) t.supp_out[off] = w * 32 + j;
+      ++off;
+    }
+    base += tot;
+  }
+  if (x.c == 0 && threadIdx.x == 0 && t.stats) {
+    cs_stats st;
+    st.outer_iters = outer;
+    st.cg_iters_total = x.cg_total;
+    st.cg_maxit_hits = x.cg_hits;
+    st.near_ties = 0;
+    st.final_resid = sqrtf(rn2);
+    st.min_margin = -1.f;
+    st.status = CS_OK;
+    *t.stats = st;
+  }
+}
+
+// A^T y into cy (dense by slot, signed) and the A buffer; returns ||y||^2.
+__device__ __noinline__ float init_correlation(Ctx& x, const float* y) {
+  float v = transform(x, SRC_NONE, 0, nullptr, nullptr, MID_RESID, true, y, nullptr);
+  for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) x.cy[sg] = corr(x, sg);
+  cluster_sum(x, &v, 1);
+  return v;
+}
+
+__device__ void zero_mask(Ctx& x, uint32_t* m) {
+  for (int w = threadIdx.x; w < x.nwords; w += NT) m[w] = 0u;
+  __syncthreads();
+}
+
+// Top-K of |c| over the local slots not in `excl` (may be null); marks into `dst`.
+__device__ __noinline__ void topk_corr(Ctx& x, int K, const uint32_t* excl, uint32_t* dst) {
+  select_topk(
+      x, 2 * x.F, K,
+      [&](int sg) -> uint32_t {
+        if (excl && mask_bit(excl, sg)) return 0u;
+        return abs_key(slot_ref(x.sm.A, sg));
+      },
+      [&](int sg) { return n_of_slot(x, sg); },
+      [&](int sg) { atomicOr(&dst[sg >> 5], 1u << (sg & 31)); });
+}
+
+__device__ __noinline__ void run_omp(Ctx& x, const Task& t) {
+  const float* y = t.in;
+  init_correlation(x, y);
+  uint32_t* mA = x.sm.mask[0];
+  zero_mask(x, mA);
+  int nloc = 0;
+  float rn2 = 0.f;
+  for (int it = 0; it < t.K; ++it) {
+    unsigned long long key = 0;
+    for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) {
+      if (mask_bit(mA, sg)) continue;
+      const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(x.sm.A, sg)) << 32) |
+                                    (0xffffffffu - (uint32_t)n_of_slot(x, sg));
+      key = kk > key ? kk : key;
+    }
+    cluster_max64(x, &key, 1);
+    if (key == 0ull) break;   // no candidate left (uniform: key is cluster-reduced)
+    const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
+    int owner, sg;
+    slot_of_n(x, n, owner, sg);
+    if (owner == x.c && threadIdx.x == 0) {
+      mA[sg >> 5] |= 1u << (sg & 31);
+      x.xd[0][sg] = 0.f;
+    }
+    __syncthreads();
+    nloc = build_list(x, mA);
+    cg_solve(x, 0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    rn2 = resid_corr(x, 0, nloc, y);
+  }
+  write_recovery(x, t, 0, nloc, rn2, t.K);
+}
+
+__device__ __noinline__ void run_sp(Ctx& x, const Task& t) {
+  const float* y = t.in;
+  init_correlation(x, y);
+  int acc = 0;   // index of the accepted (support, solution) pair
+  uint32_t* mA = x.sm.mask[acc];
+  zero_mask(x, mA);
+  topk_corr(x, t.K, nullptr, mA);
+  int nloc = build_list(x, mA);
+  cg_solve(x, acc, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  float rn2 = resid_corr(x, acc, nloc, y);
+  int rounds = 0;
+  while (rounds < t.outer_max) {
+    ++rounds;
+    const int wi = acc ^ 1;
+    uint32_t* mW = x.sm.mask[wi];
+    mA = x.sm.mask[acc];
+    // S~ = S u topK_{not in S} |A^T r|
+    for (int w = threadIdx.x; w < x.nwords; w += NT) mW[w] = mA[w];
+    __syncthreads();
+    topk_corr(x, t.K, mA, mW);
+    int nW = build_list(x, mW);
+    // warm start: x0 = s on S, 0 on the new entries; r0 = c on S~
+    for (int i = threadIdx.x; i < nW; i += NT) {
+      const int sg = x.list[i];
+      x.xd[wi][sg] = mask_bit(mA, sg) ? x.xd[acc][sg] : 0.f;
+    }
+    __syncthreads();
+    cg_solve(x, wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    // S' = topK_{j in S~} |u_j|
+    zero_mask(x, mW);
+    select_topk(
+        x, nW, t.K, [&](int i) -> uint32_t { return abs_key(x.xd[wi][x.list[i]]); },
+        [&](int i) { return n_of_slot(x, x.list[i]); },
+        [&](int i) { const int sg = x.list[i]; atomicOr(&mW[sg >> 5], 1u << (sg & 31)); });
+    nW = build_list(x, mW);
+    // r0 for the warm start on S' (x0 = u restricted to S')
+    resid_corr(x, wi, nW, y);
+    cg_solve(x, wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    const float rn2_new = resid_corr(x, wi, nW, y);
+    float diff = 0.f;
+    for (int w = threadIdx.x; w < x.nwords; w += NT) diff += (float)__popc(mW[w] ^ mA[w]);
+    cluster_sum(x, &diff, 1);
+    if (diff == 0.f || rn2_new >= rn2) break;
+    acc = wi;
+    rn2 = rn2_new;
+    nloc = nW;
+  }
+  // the returned pair is `acc`; rebuild its list (the working list may differ)
+  nloc = build_list(x, x.sm.mask[acc]);
+  write_recovery(x, t, acc, nloc, rn2, rounds);
+}
+
+__device__ __noinline__ void run_ompr(Ctx& x, const Task& t) {
+  const float* y = t.in;
+  init_correlation(x, y);
+  uint32_t* mA = x.sm.mask[0];
+  zero_mask(x, mA);
+  topk_corr(x, t.K, nullptr, mA);
+  int nloc = build_list(x, mA);
+  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  float rn2 = resid_corr(x, 0, nloc, y);
+  int swaps = 0;
+  while (swaps < t.outer_max) {
+    // z = s + A^T r: j = argmax_{not in S} |z|, i = argmin_{in S} |z| (lowest index on ties)
+    unsigned long long key[2] = {0ull, 0ull};
+    for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) {
+      const uint32_t lo = 0xffffffffu - (uint32_t)n_of_slot(x, sg);
+      if (mask_bit(mA, sg)) {
+        const float z = x.xd[0][sg] + corr(x, sg);
+        const unsigned long long kk =
+            ((unsigned long long)(0xffffffffu - (__float_as_uint(z) & 0x7fffffffu)) << 32) | lo;
+        key[1] = kk > key[1] ? kk : key[1];
+      } else {
+        const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(x.sm.A, sg)) << 32) | lo;
+        key[0] = kk > key[0] ? kk : key[0];
+      }
+    }
+    cluster_max64(x, key, 2);
+    const uint32_t zj = (uint32_t)(key[0] >> 32) - 1u;                  // |z_j| bits
+    const uint32_t zi = 0xffffffffu - (uint32_t)(key[1] >> 32);         // |z_i| bits
+    if (key[0] == 0ull || key[1] == 0ull || zj <= zi) break;            // no improving swap
+    const int nj = (int)(0xffffffffu - (uint32_t)(key[0] & 0xffffffffu));
+    const int ni = (int)(0xffffffffu - (uint32_t)(key[1] & 0xffffffffu));
+    int oj, sj, oi, si;
+    slot_of_n(x, nj, oj, sj);
+    slot_of_n(x, ni, oi, si);
+    if (threadIdx.x == 0) {
+      if (oi == x.c) { mA[si >> 5] &= ~(1u << (si & 31)); x.xd[0][si] = 0.f; }
+      if (oj == x.c) { mA[sj >> 5] |= 1u << (sj & 31); x.xd[0][sj] = 0.f; }
+    }
+    __syncthreads();
+    ++swaps;
+    nloc = build_list(x, mA);
+    resid_corr(x, 0, nloc, y);   // r0 for x0 = s without i, 0 at j
+    cg_solve(x, 0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    rn2 = resid_corr(x, 0, nloc, y);
+  }
+  write_recovery(x, t, 0, nloc, rn2, swaps);
+}
+
+// Fixed support from a sorted global index list: set the bits this CTA owns.
+__device__ __noinline__ void mask_from_support(Ctx& x, const int32_t* supp, int k, uint32_t* m) {
+  zero_mask(x, m);
+  for (int i = threadIdx.x; i < k; i += NT) {
+    const int n = supp[i];
+    if (n < 0 || n >= x.N) continue;
+    int owner, sg;
+    slot_of_n(x, n, owner, sg);
+    if (owner == x.c) atomicOr(&m[sg >> 5], 1u << (sg & 31));
+  }
+  __syncthreads();
+}
+
+__device__ __noinline__ void run_ls_solve(Ctx& x, const Task& t) {
+  init_correlation(x, t.in);
+  uint32_t* m = x.sm.mask[0];
+  mask_from_support(x, t.supp_in, t.k_in, m);
+  const int nloc = build_list(x, m);
+  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  for (int i = threadIdx.x; i < t.k_in; i += NT) {
+    const int n = t.supp_in[i];
+    if (n < 0 || n >= x.N) continue;
+    int owner, sg;
+    slot_of_n(x, n, owner, sg);
+    if (owner == x.c) t.out[i] = x.xd[0][sg];
+  }
+  if (x.c == 0 && threadIdx.x == 0 && t.stats) {
+    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK};
+    *t.stats = st;
+  }
+}
+
+__device__ __noinline__ void run_ls_backward(Ctx& x, const Task& t) {
+  uint32_t* m = x.sm.mask[0];
+  mask_from_support(x, t.supp_in, t.k_in, m);
+  // b = g placed by slot (cy doubles as the right-hand side)
+  for (int i = threadIdx.x; i < t.k_in; i += NT) {
+    const int n = t.supp_in[i];
+    if (n < 0 || n >= x.N) continue;
+    int owner, sg;
+    slot_of_n(x, n, owner, sg);
+    if (owner == x.c) x.cy[sg] = t.in[i];
+  }
+  __syncthreads();
+  const int nloc = build_list(x, m);
+  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  // dy = A_S z
+  transform(x, SRC_DENSE_SLOTS, nloc, x.xd[0], nullptr, MID_OUT, false, nullptr, t.out);
+  if (x.c == 0 && threadIdx.x == 0 && t.stats) {
+    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK};
+    *t.stats = st;
+  }
+}
+
+extern __shared__ __align__(16) unsigned char smem_raw[];
+
+__global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int P = (int)cl.num_blocks();
+  const int c = (int)cl.block_rank();
+  const int cid = blockIdx.x / P;
+  const int ncl = gridDim.x / P;
+  Ctx x{cl, carve(smem_raw, lp.F_alloc)};
+  x.c = c;
+  x.ring_slot = 0;
+  x.hist_slot = 0;
+  float* base = lp.scratch + (size_t)cid * lp.scratch_per_cluster + (size_t)c * scratch_floats_per_cta(lp.F_alloc);
+  const size_t a = 2 * (size_t)lp.F_alloc;
+  x.xd[0] = base;
+  x.xd[1] = base + a;
+  x.cy = base + 2 * a;
+  x.list = reinterpret_cast<int*>(base + 3 * a);
+  x.cgx = base + 4 * a;
+  x.cgr = base + 5 * a;
+  x.cgp = base + 6 * a;
+  x.cgq = base + 7 * a;
+  x.bits = lp.bits + (size_t)cid * lp.bits_per_cluster;
+
+  for (int ti = cid; ti < lp.ntasks; ti += ncl) {
+    const Task t = lp.tasks ? lp.tasks[ti] : lp.single;
+    const OpDev& op = t.op;
+    if (op.P != P || op.F > lp.F_alloc) {   // host grouping error: skip uniformly
+      if (c == 0 && threadIdx.x == 0 && t.stats) t.stats->status = CS_ERR_INVALID_ARG;
+      continue;
+    }
+    x.N = op.N; x.M = op.M; x.L = op.N >> 1; x.P = P; x.F = op.F;
+    x.h = op.F / (2 * P); x.S2 = 2 * x.h; x.four_n = 4 * op.N;
+    x.nwords = (2 * op.F + 31) / 32;
+    x.omask = op.omask; x.orank = op.orank;
+    x.cg_total = 0; x.cg_hits = 0;
+    // twiddle tables and sign bits
+    const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
+    for (int i = threadIdx.x; i < nlo; i += NT) x.sm.twlo[i] = op.tw[i];
+    for (int i = threadIdx.x; i < nhi; i += NT) x.sm.twhi[i] = op.tw[nlo + i];
+    x.tw.lo = x.sm.twlo; x.tw.hi = x.sm.twhi; x.tw.lo_bits = op.lo_bits; x.tw.lo_mask = nlo - 1;
+    x.tw.mask4n = x.four_n - 1;
+    for (int w = threadIdx.x; w < x.nwords; w += NT) {
+      uint32_t bitsw = 0u;
+      for (int b = 0; b < 32; ++b) {
+        const int sg = 32 * w + b;
+        if (sg < 2 * op.F) {
+          const uint64_t hsh = mix64(op.sign_key + (uint64_t)n_of_slot(x, sg) + 0x9E3779B97F4A7C15ull);
+          bitsw |= (uint32_t)(hsh >> 63) << b;
+        }
+      }
+      x.sm.signw[w] = bitsw;
+    }
+    __syncthreads();
+    switch (t.mode) {
+      case MODE_APPLY:
+        transform(x, SRC_GLOBAL_N, 0, nullptr, t.in, MID_OUT, false, nullptr, t.out);
+        break;
+      case MODE_APPLY_T:
+        transform(x, SRC_NONE, 0, nullptr, nullptr, MID_IN, true, t.in, nullptr);
+        for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) t.out[n_of_slot(x, sg)] = corr(x, sg);
+        break;
+      case MODE_RECOVER:
+        if (t.algo == CS_OMP) run_omp(x, t);
+        else if (t.algo == CS_SP) run_sp(x, t);
+        else run_ompr(x, t);
+        break;
+      case MODE_LS_SOLVE: run_ls_solve(x, t); break;
+      case MODE_LS_BACKWARD: run_ls_backward(x, t); break;
+      default: break;
+    }
+    cl.sync();
+  }
+}
+
+cudaError_t launch_engine(const Launch& L, int P, int num_clusters, cudaStream_t stream) {
+  const size_t smem = smem_bytes(L.F_alloc);
+  cudaError_t e = cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (P > 8) {
+    e = cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P * num_clusters);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, engine_kernel, L);
+}
+
+int max_active_clusters(int P, int F_alloc) {
+  const size_t smem = smem_bytes(F_alloc);
+  if (cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  if (P > 8 && cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, engine_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+}  // namespace csg

@@ -1,0 +1,54 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every declared entry point, and its
+host-side random draws equal the oracle's independent implementation bit for bit."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import rng
+from paper_1509_03979_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(cs_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1509_03979_gb300 import build
+    build.build()
+    return binding.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in binding.SIGNATURES, n
+
+
+@pytest.mark.parametrize("N,M,seed", [(16, 8, 1), (4096, 1024, 0x0C5001), (1 << 14, 1 << 12, 99),
+                                      (1 << 18, 1 << 16, 0x0C5002)])
+def test_operator_draws_match_oracle(lib, N, M, seed):
+    om, d = binding.operator_draws(N, M, seed)
+    assert np.array_equal(om.astype(np.int64), rng.omega(N, M, seed))
+    assert np.array_equal(d.astype(np.float64), rng.signs(N, seed))
+
+
+@pytest.mark.parametrize("N,M,code", [(24, 8, 2), (8, 4, 2), (1 << 19, 8, 2), (64, 0, 1), (64, 65, 1)])
+def test_invalid_sizes_rejected_without_gpu(lib, N, M, code):
+    om = np.zeros(max(M, 1), dtype=np.int32)
+    st = lib.cs_operator_draws(N, M, 1, om.ctypes.data_as(ctypes.c_void_p), None)
+    assert st == code
+    assert len(lib.cs_last_error()) > 0
