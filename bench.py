@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the greedy CS hot path on GB300: Subspace Pursuit with the CG weighted
+least-squares step on signals of N = 2^18 (a 512x512 image flattened), M = N/4, K = 6554,
+Gaussian nonzeros, additive noise sigma = 1e-3 ||y|| / sqrt(M).
+
+One step = one batched recovery launch over B synthetic signals per GPU (B = the number of
+signals the GPU runs at once, one per resident thread-block cluster).  Prints ONE JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1509_03979_gb300 import synth  # noqa: E402
+
+WORKLOAD = synth.workload(2)
+CG_TOL, CG_MAXIT = 1e-6, 100
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 SMSPs x 32)
+METRIC = "recoveries/s (SP + CG-LS, N=2^18)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batch", type=int, default=0, help="signals per GPU per step (0 = fill the GPU)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-batch", type=int, default=256)
+    return ap.parse_args()
+
+
+def signal_seeds(i):
+    """Seeds of the i-th signal of the workload (all share one operator)."""
+    return WORKLOAD.signal_seed + 7919 * i, WORKLOAD.noise_seed + 7919 * i
+
+
+def flops_per_dct(N):
+    """Algorithmic FP32 flops of one N-point DCT via an N/2-point complex FFT: 2.5 N log2 N."""
+    return 2.5 * N * np.log2(N)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    """The FP64 CPU oracle timed on the host cores: each timed step recovers one signal of the
+    same workload (the oracle holds no warm state, so warm-up steps recover a 1/64-size signal)."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import greedy
+    p = WORKLOAD
+
+    def one(N, M, K, i):
+        op = oracle.Operator(N, M, p.op_seed)
+        ss, ns = signal_seeds(i)
+        prob = synth.Problem(N, M, K, "sp", p.op_seed, ss, ns, p.noise_rel)
+        y = prob.add_noise(op.apply(prob.signal())).astype(np.float32).astype(np.float64)
+        t = time.perf_counter()
+        greedy.sp(op, y, K)
+        return time.perf_counter() - t
+
+    for w in range(args.warmup):
+        one(p.N // 64, p.M // 64, p.K // 64, w)
+    times = [one(p.N, p.M, p.K, i) for i in range(args.steps)]
+    value = 1.0 / statistics.mean(times)
+    sample = f"{args.steps} full SP recoveries of the N=2^18 workload, FP64 numpy (pocketfft, 1 thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "recoveries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "SP+CG-LS N=2^18 M=65536 K=6554 noise 1e-3", "batch_per_gpu": 1},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": "recoveries/s"},
+        "e2e": {"value": value, "unit": "recoveries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------ GB300 arm
+def run_gb300(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1509_03979_gb300 import binding
+
+    torch.cuda.set_device(local_rank)
+    devc = torch.device("cuda", local_rank)
+    p = WORKLOAD
+    op = binding.Operator(p.N, p.M, p.op_seed)
+    B = args.batch or op.concurrency()
+
+    # ---- inputs (seeded, synthetic, resident in HBM before timing)
+    idx = [rank * B + b for b in range(B)]
+    S = np.zeros((B, p.N), dtype=np.float32)
+    noise = np.zeros((B, p.M), dtype=np.float32)
+    for b, i in enumerate(idx):
+        ss, ns = signal_seeds(i)
+        S[b] = synth.sparse_gaussian(p.N, p.K, ss)
+        noise[b] = synth.normals(ns, p.M)
+    S_d = torch.from_numpy(S).to(devc)
+    Yc = op.apply_batched(S_d)                                  # y_clean = A s on the device
+    sigma = p.noise_rel * torch.linalg.vector_norm(Yc, dim=1, keepdim=True) / np.sqrt(p.M)
+    Y = (Yc + sigma * torch.from_numpy(noise).to(devc)).contiguous()
+    s_out = torch.empty((B, p.N), dtype=torch.float32, device=devc)
+    supp = torch.empty((B, p.K), dtype=torch.int32, device=devc)
+    ops = [op] * B
+    ys = [Y[b] for b in range(B)]
+    souts = [s_out[b] for b in range(B)]
+    supps = [supp[b] for b in range(B)]
+
+    def step():
+        binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, CG_TOL, CG_MAXIT, souts, supps)
+
+    # one untimed run with statistics (transform counts for the roofline, quality)
+    _, _, stats = binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, CG_TOL, CG_MAXIT, souts, supps,
+                                          want_stats=True)
+    torch.cuda.synchronize()
+    transforms = sum(s["transforms"] for s in stats)
+    rounds = [s["outer_iters"] for s in stats]
+    cg_iters = [s["cg_iters_total"] for s in stats]
+    status = [s["status"] for s in stats]
+    supp_h = supp.cpu().numpy()
+    recall = float(np.mean([np.isin(np.flatnonzero(S[b]), supp_h[b]).mean() for b in range(B)]))
+    err_truth = float(np.mean([np.linalg.norm(s_out[b].cpu().numpy() - S[b]) / np.linalg.norm(S[b])
+                               for b in range(B)]))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=devc)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t0 = time.perf_counter()
+    for e0, e1 in evs:
+        l2_flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=devc)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * B * args.steps / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # ---- roofline of the (only) kernel: one engine launch per step
+    n_sm = torch.cuda.get_device_properties(devc).multi_processor_count
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_alu = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s
+    achieved = transforms * flops_per_dct(p.N) / (ms_per_step / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": achieved / peak_alu, "traffic": None,
+                "kernel": "engine_kernel (SP recovery, one launch per step)",
+                "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
+
+    # ---- A / A^T apply bandwidth over a batch larger than L2
+    hbm_peak, peak_kind = peaks()
+    Xa = torch.randn((args.apply_batch, p.N), device=devc)
+    Ya = torch.empty((args.apply_batch, p.M), device=devc)
+    Xt = torch.empty((args.apply_batch, p.N), device=devc)
+    for _ in range(3):
+        op.apply_batched(Xa, Ya)
+        op.apply_t_batched(Ya, Xt)
+    torch.cuda.synchronize()
+    reps = 5
+    ta = []
+    tt = []
+    for _ in range(reps):
+        l2_flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream); op.apply_batched(Xa, Ya); a1.record(stream)
+        l2_flush.zero_()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream); op.apply_t_batched(Ya, Xt); b1.record(stream)
+        torch.cuda.synchronize()
+        ta.append(a0.elapsed_time(a1))
+        tt.append(b0.elapsed_time(b1))
+    bytes_apply = args.apply_batch * 4.0 * (p.N + p.M)          # read x, write y
+    gbs_a = bytes_apply / (statistics.median(ta) / 1e3) / 1e9
+    gbs_t = bytes_apply / (statistics.median(tt) / 1e3) / 1e9
+    apply = {"bound": "hbm", "batch": args.apply_batch, "A_GBs": gbs_a, "AT_GBs": gbs_t, "peak": hbm_peak,
+             "frac_A": gbs_a / hbm_peak, "frac_AT": gbs_t / hbm_peak, "peak_kind": peak_kind,
+             "bytes_per_vector": 4 * (p.N + p.M)}
+
+    # ---- end to end through the public API with host buffers (pinned), copies inside
+    Yh = Y.cpu().pin_memory()
+    Sh = torch.empty((B, p.N), dtype=torch.float32).pin_memory()
+    Kh = torch.empty((B, p.K), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        l2_flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Y.copy_(Yh, non_blocking=True)
+        step()
+        Sh.copy_(s_out, non_blocking=True)
+        Kh.copy_(supp, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_s = sum(e2e_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device=devc)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * B * args.steps / e2e_s, "unit": "recoveries/s",
+           "h2d_bytes_per_step": B * p.M * 4, "d2h_bytes_per_step": B * (p.N + p.K) * 4}
+
+    # ---- CPU baseline: the FP64 oracle on signal 0 (also a full-size parity check)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        from oracle import greedy
+        ref_op = oracle.Operator(p.N, p.M, p.op_seed)
+        y0 = Y[0].cpu().numpy().astype(np.float64)
+        t = time.perf_counter()
+        ref = greedy.sp(ref_op, y0, p.K)
+        dt = time.perf_counter() - t
+        s0 = s_out[0].cpu().numpy().astype(np.float64)
+        cpu = {"value": 1.0 / dt, "unit": "recoveries/s", "cores": 1, "kind": "oracle",
+               "sample": "one full SP recovery of signal 0 of this workload, FP64 numpy (pocketfft, 1 thread)",
+               "parity": {"rel_err_vs_oracle": float(np.linalg.norm(s0 - ref["s"]) / np.linalg.norm(ref["s"])),
+                          "support_equal": bool(np.array_equal(np.sort(supp_h[0]), ref["S"])),
+                          "oracle_near_ties": ref["near_ties"], "oracle_rounds": ref["iters"]}}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "recoveries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "SP+CG-LS N=2^18 M=65536 K=6554 noise 1e-3 (config 2)",
+                       "batch_per_gpu": B, "cg_tol": CG_TOL, "cg_maxit": CG_MAXIT,
+                       "l2": "256 MiB buffer written between timed steps",
+                       "parallelism": f"signals sharded over {world} GPU(s), no collective"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
+            "apply_roofline": apply, "cpu_baseline": cpu,
+            "quality": {"support_recall_vs_truth": recall, "rel_err_vs_truth": err_truth,
+                        "sp_rounds": rounds, "cg_iters_total": cg_iters, "status": status,
+                        "transforms_per_step": transforms},
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    op.close()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    try:
+        run_gb300(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -59,6 +59,7 @@ typedef struct {
   float final_resid;       /* ||y - A s_hat||_2 of the returned solution */
   float min_margin;        /* reserved: -1 */
   int32_t status;          /* cs_status of the device-side run */
+  int32_t transforms;      /* N-point DCT-II / DCT-III applications executed */
 } cs_stats;
 
 /* Create the operator A = P_Omega C_N diag(d) for (N, M, seed) (Sec. III-A, Eq. 7).
@@ -79,6 +80,15 @@ cs_status cs_op_apply(cs_op_t op, const float* x_N, float* y_M);
 /* x_N = A^T y_M: scatter onto Omega, orthonormal DCT-III, sign flip (the correlation A^T r of
  * Eq. 6).  y_M: [M] device; x_N: [N] device (written).  Buffers must not overlap. */
 cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N);
+
+/* Batched A / A^T: B independent vectors through the same operator, one persistent launch.
+ * X [B][N] and Y [B][M] device, row-major contiguous; U [B][M] -> X [B][N] for the transpose. */
+cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y);
+cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X);
+
+/* Number of signals of this operator's size that the device runs at the same time (one per
+ * resident thread-block cluster); a batch of this many fills the GPU.  >= 1. */
+int32_t cs_op_concurrency(cs_op_t op);
 
 /* Copy the operator's random draws to HOST memory for cross-checking: omega_M_host [M]
  * (sorted row indices) and d_N_host [N] (+1/-1).  Either pointer may be NULL. */

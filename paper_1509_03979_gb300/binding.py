@@ -21,7 +21,7 @@ class CsStats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int32), ("cg_iters_total", ctypes.c_int32),
                 ("cg_maxit_hits", ctypes.c_int32), ("near_ties", ctypes.c_int32),
                 ("final_resid", ctypes.c_float), ("min_margin", ctypes.c_float),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("transforms", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -37,6 +37,9 @@ SIGNATURES = {
     "cs_op_apply": (_I32, [_P, _P, _P]),
     "cs_op_apply_t": (_I32, [_P, _P, _P]),
     "cs_op_export": (_I32, [_P, _P, _P]),
+    "cs_op_apply_batched": (_I32, [_P, _I32, _P, _P]),
+    "cs_op_apply_t_batched": (_I32, [_P, _I32, _P, _P]),
+    "cs_op_concurrency": (_I32, [_P]),
     "cs_operator_draws": (_I32, [_I64, _I64, _U64, _P, _P]),
     "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
     "cs_recover_batched": (_I32, [_I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P]),
@@ -129,6 +132,28 @@ class Operator:
         self._stream()
         _check(lib().cs_op_apply_t(self._h, _dev(u, torch.float32, self.M, "u"), _dev(out, torch.float32, self.N, "x")))
         return out
+
+    def apply_batched(self, X, out=None):
+        """Y[b] = A X[b] for X of shape [B, N]."""
+        Bn = X.shape[0]
+        out = torch.empty((Bn, self.M), dtype=torch.float32, device=X.device) if out is None else out
+        self._stream()
+        _check(lib().cs_op_apply_batched(self._h, Bn, _dev(X, torch.float32, Bn * self.N, "X"),
+                                         _dev(out, torch.float32, Bn * self.M, "Y")))
+        return out
+
+    def apply_t_batched(self, U, out=None):
+        """X[b] = A^T U[b] for U of shape [B, M]."""
+        Bn = U.shape[0]
+        out = torch.empty((Bn, self.N), dtype=torch.float32, device=U.device) if out is None else out
+        self._stream()
+        _check(lib().cs_op_apply_t_batched(self._h, Bn, _dev(U, torch.float32, Bn * self.M, "U"),
+                                           _dev(out, torch.float32, Bn * self.N, "X")))
+        return out
+
+    def concurrency(self):
+        """Signals of this size the GPU runs at once (resident clusters)."""
+        return int(lib().cs_op_concurrency(self._h))
 
     def export(self):
         import numpy as np

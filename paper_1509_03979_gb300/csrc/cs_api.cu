@@ -261,6 +261,39 @@ cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N) {
   return run_single(op, t);
 }
 
+static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream);
+
+static cs_status apply_batched(cs_op_t op, int mode, int32_t B, const float* in, float* out) {
+  if (!op || B < 0 || (B > 0 && (!in || !out))) return fail(CS_ERR_INVALID_ARG, "null argument or B < 0");
+  if (B == 0) return CS_OK;
+  const size_t nin = mode == MODE_APPLY ? (size_t)op->N : (size_t)op->M;
+  const size_t nout = mode == MODE_APPLY ? (size_t)op->M : (size_t)op->N;
+  std::vector<Task> tasks;
+  tasks.reserve((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    Task t = base_task(op, mode);
+    t.in = in + (size_t)b * nin;
+    t.out = out + (size_t)b * nout;
+    t.stats = nullptr;
+    tasks.push_back(t);
+  }
+  if (B == 1) return run_single(op, tasks[0]);
+  return launch_tasks(tasks, op->stream);
+}
+
+cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y) {
+  return apply_batched(op, MODE_APPLY, B, X, Y);
+}
+
+cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X) {
+  return apply_batched(op, MODE_APPLY_T, B, U, X);
+}
+
+int32_t cs_op_concurrency(cs_op_t op) {
+  if (!op) return 1;
+  return std::max(1, max_active_clusters(op->dev.P, op->dev.F));
+}
+
 cs_status cs_op_export(cs_op_t op, int32_t* omega_M_host, int8_t* d_N_host) {
   if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
   if (omega_M_host) std::memcpy(omega_M_host, op->h_omega.data(), sizeof(int32_t) * (size_t)op->M);

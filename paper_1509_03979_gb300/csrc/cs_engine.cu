@@ -312,6 +312,7 @@ struct Ctx {
   int hist_slot;
   int cg_total;
   int cg_hits;
+  int ntrans;         // N-point DCT applications (forward or inverse)
 };
 
 __device__ __forceinline__ float& slot_ref(float2* A, int sigma) {
@@ -555,6 +556,7 @@ __device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* 
                            const float* vin, float* vout) {
   const int F = x.F;
   float2* A = x.sm.A;
+  x.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
   if (src != SRC_NONE) {
     if (src == SRC_GLOBAL_N) {
       for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(x, sg)] * sgn(x, sg);
@@ -850,6 +852,7 @@ __device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int n
     st.final_resid = sqrtf(rn2);
     st.min_margin = -1.f;
     st.status = CS_OK;
+    st.transforms = x.ntrans;
     *t.stats = st;
   }
 }
@@ -1038,7 +1041,7 @@ __device__ __noinline__ void run_ls_solve(Ctx& x, const Task& t) {
     if (owner == x.c) t.out[i] = x.xd[0][sg];
   }
   if (x.c == 0 && threadIdx.x == 0 && t.stats) {
-    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK};
+    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK, x.ntrans};
     *t.stats = st;
   }
 }
@@ -1060,7 +1063,7 @@ __device__ __noinline__ void run_ls_backward(Ctx& x, const Task& t) {
   // dy = A_S z
   transform(x, SRC_DENSE_SLOTS, nloc, x.xd[0], nullptr, MID_OUT, false, nullptr, t.out);
   if (x.c == 0 && threadIdx.x == 0 && t.stats) {
-    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK};
+    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK, x.ntrans};
     *t.stats = st;
   }
 }
@@ -1100,7 +1103,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
     x.h = op.F / (2 * P); x.S2 = 2 * x.h; x.four_n = 4 * op.N;
     x.nwords = (2 * op.F + 31) / 32;
     x.omask = op.omask; x.orank = op.orank;
-    x.cg_total = 0; x.cg_hits = 0;
+    x.cg_total = 0; x.cg_hits = 0; x.ntrans = 0;
     // twiddle tables and sign bits
     const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
     for (int i = threadIdx.x; i < nlo; i += NT) x.sm.twlo[i] = op.tw[i];
