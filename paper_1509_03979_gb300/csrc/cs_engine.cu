@@ -103,6 +103,16 @@ __device__ __forceinline__ void dft(float2* v) {
   }
 }
 
+extern __shared__ __align__(16) unsigned char smem_raw[];
+
+// Re-derive a pointer from the shared-memory base so the compiler knows its address space
+// (pointers travelling through non-inlined calls are generic).
+template <class T>
+__device__ __forceinline__ T* shp(T* p) {
+  const ptrdiff_t off = reinterpret_cast<const unsigned char*>(p) - smem_raw;
+  return reinterpret_cast<T*>(smem_raw + off);
+}
+
 // Padded index into the local FFT buffer (one spare element every 16 keeps the strided
 // Stockham stores of the early passes free of shared-memory bank conflicts).
 __device__ __forceinline__ int aidx(int q) { return q + (q >> 4); }
@@ -158,7 +168,7 @@ __device__ __forceinline__ void twiddle_powers(float2* v, const Tw& tw, int t) {
 // One in-place Stockham pass of radix R over the F-point buffer X (padded indexing).
 // All R-point groups are loaded into registers before any store (F <= 16 * NT).
 template <int R, int DIR>
-__device__ __noinline__ void fft_pass(float2* X, int F, int Ns, const Tw& tw, int four_n) {
+__device__ __forceinline__ void fft_pass(float2* X, int F, int Ns, const Tw& tw, int four_n) {
   constexpr int BPT = 16 / R;
   const int nb = F / R;
   float2 v[BPT][R];
@@ -186,9 +196,13 @@ __device__ __noinline__ void fft_pass(float2* X, int F, int Ns, const Tw& tw, in
   __syncthreads();
 }
 
-// Q-point FFT of the local buffer, natural order in and out.
+// Q-point FFT of the local buffer, natural order in and out (one call per FFT; the passes
+// are inlined here so registers are saved once per FFT, not once per pass).
 template <int DIR>
-__device__ __noinline__ void local_fft(float2* X, int F, const Tw& tw, int four_n) {
+__device__ __noinline__ void local_fft(float2* X, int F, Tw tw, int four_n) {
+  X = shp(X);
+  tw.lo = shp(tw.lo);
+  tw.hi = shp(tw.hi);
   int Ns = 1;
   while (Ns < F) {
     const int rem = F / Ns;
@@ -210,7 +224,7 @@ __device__ __forceinline__ void pcol(float2* B, int s, int S2) {
   for (int p = 0; p < R; ++p) B[p * S2 + s] = v[p];
 }
 template <int DIR>
-__device__ __noinline__ void pstep(float2* B, int P, int S2) {
+__device__ __forceinline__ void pstep(float2* B, int P, int S2) {
   if (P > 1) {
     for (int s = threadIdx.x; s < S2; s += NT) {
       switch (P) {
@@ -220,8 +234,8 @@ __device__ __noinline__ void pstep(float2* B, int P, int S2) {
         default: pcol<16, DIR>(B, s, S2); break;
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // ------------------------------------------------------------------------------ reductions
@@ -240,6 +254,10 @@ __device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
 }
 
 // ------------------------------------------------------------------------- shared layout
+
+constexpr int CG_CAP_MAX = 3072;   // support entries per CTA whose CG vectors live on chip
+__host__ __device__ inline int cg_cap(int F_alloc) { return 2 * F_alloc < CG_CAP_MAX ? 2 * F_alloc : CG_CAP_MAX; }
+
 struct Smem {
   float2* A;          // local FFT buffer (padded), signal-domain slots between transforms
   float2* B;          // exchange / frequency buffer [P][2h]
@@ -247,6 +265,7 @@ struct Smem {
   float2* twhi;
   uint32_t* signw;    // d_n bits per local slot (1 = -1)
   uint32_t* mask[2];  // support bitmasks over local slots
+  uint8_t* fbits;     // Omega membership of the (up to 4) DCT outputs of each frequency task
   uint32_t* hist;     // [2][256]
   uint32_t* htot;     // [256]
   float* ring;        // [4][4] cluster-reduction partials
@@ -255,53 +274,87 @@ struct Smem {
   unsigned long long* wmax;     // [2][16]
   int* iscr;          // [64] integer scratch / broadcast
   float* fscr;        // [8]
+  int* cgl;           // [cap] support list when it fits
+  float* cgv;         // [4][cap] CG x, r, p, q when they fit
 };
 
-__device__ Smem carve(unsigned char* base, int F_alloc) {
-  Smem s;
-  size_t off = 0;
-  auto take = [&](size_t bytes) { unsigned char* p = base + off; off += (bytes + 15) & ~size_t(15); return p; };
-  s.A = (float2*)take(sizeof(float2) * apad(F_alloc));
-  s.B = (float2*)take(sizeof(float2) * F_alloc);
-  s.twlo = (float2*)take(sizeof(float2) * 1024);
-  s.twhi = (float2*)take(sizeof(float2) * 1024);
+// Bump allocator over the dynamic shared-memory window (16-byte granules).
+struct Bump {
+  unsigned char* base;
+  size_t off;
+  __host__ __device__ unsigned char* operator()(size_t bytes) {
+    unsigned char* p = base ? base + off : nullptr;
+    off += (bytes + 15) & ~size_t(15);
+    return p;
+  }
+};
+
+__host__ __device__ inline void layout(int F_alloc, Bump& take, Smem* s) {
   const int nw = (2 * F_alloc + 31) / 32;
-  s.signw = (uint32_t*)take(4 * nw);
-  s.mask[0] = (uint32_t*)take(4 * nw);
-  s.mask[1] = (uint32_t*)take(4 * nw);
-  s.hist = (uint32_t*)take(4 * 512);
-  s.htot = (uint32_t*)take(4 * 256);
-  s.ring = (float*)take(4 * 16);
-  s.ring64 = (unsigned long long*)take(8 * 8);
-  s.wsum = (float*)take(4 * 64);
-  s.wmax = (unsigned long long*)take(8 * 32);
-  s.iscr = (int*)take(4 * 64);
-  s.fscr = (float*)take(4 * 8);
+  const int cap = cg_cap(F_alloc);
+  unsigned char* A = take(sizeof(float2) * apad(F_alloc));
+  unsigned char* B = take(sizeof(float2) * F_alloc);
+  unsigned char* tl = take(sizeof(float2) * 1024);
+  unsigned char* th = take(sizeof(float2) * 1024);
+  unsigned char* sw = take(4 * nw);
+  unsigned char* m0 = take(4 * nw);
+  unsigned char* m1 = take(4 * nw);
+  unsigned char* fb = take(F_alloc / 2 + 16);
+  unsigned char* hi = take(4 * 512);
+  unsigned char* ht = take(4 * 256);
+  unsigned char* rg = take(4 * 16);
+  unsigned char* r64 = take(8 * 8);
+  unsigned char* ws = take(4 * 64);
+  unsigned char* wm = take(8 * 32);
+  unsigned char* is = take(4 * 64);
+  unsigned char* fs = take(4 * 8);
+  unsigned char* cl = take(4 * (size_t)cap);
+  unsigned char* cv = take(16 * (size_t)cap);
+  if (s) {
+    s->A = (float2*)A; s->B = (float2*)B; s->twlo = (float2*)tl; s->twhi = (float2*)th;
+    s->signw = (uint32_t*)sw; s->mask[0] = (uint32_t*)m0; s->mask[1] = (uint32_t*)m1;
+    s->fbits = (uint8_t*)fb; s->hist = (uint32_t*)hi; s->htot = (uint32_t*)ht; s->ring = (float*)rg;
+    s->ring64 = (unsigned long long*)r64; s->wsum = (float*)ws; s->wmax = (unsigned long long*)wm;
+    s->iscr = (int*)is; s->fscr = (float*)fs; s->cgl = (int*)cl; s->cgv = (float*)cv;
+  }
+}
+
+__device__ Smem carve(int F_alloc) {
+  Smem s;
+  Bump b{smem_raw, 0};
+  layout(F_alloc, b, &s);
   return s;
 }
 
 size_t smem_bytes(int F_alloc) {
-  auto r = [](size_t b) { return (b + 15) & ~size_t(15); };
-  const int nw = (2 * F_alloc + 31) / 32;
-  return r(sizeof(float2) * apad(F_alloc)) + r(sizeof(float2) * F_alloc) + 2 * r(sizeof(float2) * 1024) +
-         3 * r(4 * nw) + r(4 * 512) + r(4 * 256) + r(4 * 16) + r(8 * 8) + r(4 * 64) + r(8 * 32) + r(4 * 64) +
-         r(4 * 8);
+  Bump b{nullptr, 0};
+  layout(F_alloc, b, nullptr);
+  return b.off;
 }
 
 // ---------------------------------------------------------------------- per-signal context
 enum MidKind : int { MID_MASK = 0, MID_RESID = 1, MID_OUT = 2, MID_IN = 3 };
 enum SrcKind : int { SRC_NONE = 0, SRC_CG = 1, SRC_DENSE_SLOTS = 2, SRC_GLOBAL_N = 3 };
 
+// Geometry of one signal as seen by one CTA (all sizes powers of two); kept in registers.
+struct Geo {
+  int N, L, P, F, h, lh, S2, c, four_n;
+};
+
 struct Ctx {
   cg::cluster_group cl;
   Smem sm;
   Tw tw;
-  int N, M, L, P, F, h, S2, c, nwords, four_n;
+  Geo g;
+  int M, nwords, cap;
   const uint32_t* omask;
   const int32_t* orank;
   // global per-CTA scratch
   float* xd[2];
   float* cy;
+  int* glist;          // global list (fallback when the support share exceeds cap)
+  float* gcg;          // global CG vectors (fallback), 4 arrays of 2F
+  // current support list and CG vectors (shared memory when they fit)
   int* list;
   float* cgx;
   float* cgr;
@@ -320,19 +373,19 @@ __device__ __forceinline__ float& slot_ref(float2* A, int sigma) {
 }
 // Signal index of local real slot sigma of CTA c: complex point m = q P + c of z, real index
 // v = 2 m + b of Makhoul's reordered sequence, v < N/2 -> n = 2 v, else n = 2 (N - 1 - v) + 1.
-__device__ __forceinline__ int n_of_slot(const Ctx& x, int sigma) {
-  const int m = (sigma >> 1) * x.P + x.c;
+__device__ __forceinline__ int n_of_slot(const Geo& g, int sigma) {
+  const int m = (sigma >> 1) * g.P + g.c;
   const int v = 2 * m + (sigma & 1);
-  return v < (x.N >> 1) ? 2 * v : 2 * (x.N - 1 - v) + 1;
+  return v < (g.N >> 1) ? 2 * v : 2 * (g.N - 1 - v) + 1;
 }
-__device__ __forceinline__ void slot_of_n(const Ctx& x, int n, int& owner, int& sigma) {
-  const int v = (n & 1) ? x.N - 1 - (n >> 1) : (n >> 1);
+__device__ __forceinline__ void slot_of_n(const Geo& g, int n, int& owner, int& sigma) {
+  const int v = (n & 1) ? g.N - 1 - (n >> 1) : (n >> 1);
   const int m = v >> 1;
-  owner = m % x.P;
-  sigma = 2 * (m / x.P) + (v & 1);
+  owner = m & (g.P - 1);
+  sigma = 2 * (m / g.P) + (v & 1);
 }
-__device__ __forceinline__ float sgn(const Ctx& x, int sigma) {
-  return (x.sm.signw[sigma >> 5] >> (sigma & 31)) & 1u ? -1.0f : 1.0f;
+__device__ __forceinline__ float sgn_bits(const uint32_t* signw, int sigma) {
+  return (signw[sigma >> 5] >> (sigma & 31)) & 1u ? -1.0f : 1.0f;
 }
 __device__ __forceinline__ bool mask_bit(const uint32_t* m, int sigma) { return (m[sigma >> 5] >> (sigma & 31)) & 1u; }
 
@@ -346,17 +399,45 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // Frequency slot k_q held by slot s of CTA c (mirror-paired assignment).
-__device__ __forceinline__ int kq_of(const Ctx& x, int s) {
-  const int Q = x.F;
-  if (s < x.h) return x.c * x.h + s;
-  const int j = x.c * x.h + s - x.h;
-  return j == 0 ? (Q >> 1) : Q - j;
+__device__ __forceinline__ int kq_of(const Geo& g, int s) {
+  if (s < g.h) return g.c * g.h + s;
+  const int j = g.c * g.h + s - g.h;
+  return j == 0 ? (g.F >> 1) : g.F - j;
 }
-__device__ __forceinline__ void owner_of_kq(const Ctx& x, int k, int& c, int& s) {
-  const int Q = x.F;
-  if (k < (Q >> 1)) { c = k / x.h; s = k - c * x.h; }
-  else if (k == (Q >> 1)) { c = 0; s = x.h; }
-  else { const int j = Q - k; c = j / x.h; s = x.h + (j - c * x.h); }
+__device__ __forceinline__ void owner_of_kq(const Geo& g, int k, int& c, int& s) {
+  const int Q = g.F;
+  if (k < (Q >> 1)) { c = k >> g.lh; s = k - (c << g.lh); }
+  else if (k == (Q >> 1)) { c = 0; s = g.h; }
+  else { const int j = Q - k; c = j >> g.lh; s = g.h + (j - (c << g.lh)); }
+}
+
+// Frequency task t of this CTA -> the slot pair holding (Z_k, Z_{L-k}).  Tasks [0, h P) walk
+// the (slot, k_p) grid of the lower half; CTA 0 skips its slot 0 there and instead runs P + 1
+// tasks for its two self-mirrored columns (k_q = 0 and k_q = Q/2).  Returns false for a skip.
+__device__ __forceinline__ int ntasks(const Geo& g) { return g.h * g.P + (g.c == 0 ? g.P + 1 : 0); }
+__device__ __forceinline__ bool task_pair(const Geo& g, int t, int& sa, int& kpa, int& sb, int& kpb) {
+  const int P = g.P, h = g.h;
+  const int reg = h * P;
+  if (t < reg) {
+    sa = t & (h - 1);
+    kpa = t >> g.lh;
+    if (g.c == 0 && sa == 0) return false;
+    sb = sa + h;
+    kpb = P - 1 - kpa;
+    return true;
+  }
+  const int u = t - reg;
+  const int ncol0 = P > 1 ? P / 2 + 1 : 1;
+  if (u < ncol0) { sa = 0; kpa = u; sb = 0; kpb = (P - u) & (P - 1); }
+  else { const int v = u - ncol0; sa = h; kpa = v; sb = h; kpb = P - 1 - v; }
+  return true;
+}
+// The DCT output indices produced by the pair whose first FFT bin is k.
+__device__ __forceinline__ int pair_outputs(const Geo& g, int k, bool self, int* f) {
+  if (k == 0) { f[0] = 0; f[1] = g.L; return 2; }
+  if (self) { f[0] = k; f[1] = g.N - k; return 2; }
+  f[0] = k; f[1] = g.N - k; f[2] = g.L + k; f[3] = g.L - k;
+  return 4;
 }
 
 // ---------------------------------------------------------------- cluster-wide reductions
@@ -364,58 +445,62 @@ __device__ __forceinline__ void owner_of_kq(const Ctx& x, int k, int& c, int& s)
 // every CTA adds the partials in rank order, so all CTAs hold bit-identical results.
 __device__ __noinline__ void cluster_sum(Ctx& x, float* v, int n) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* wsum = shp(x.sm.wsum);
   for (int i = 0; i < n; ++i) {
     const float s = warp_sum(v[i]);
-    if (lane == 0) x.sm.wsum[i * 16 + warp] = s;
+    if (lane == 0) wsum[i * 16 + warp] = s;
   }
   __syncthreads();
-  float* ring = x.sm.ring + 4 * x.ring_slot;
+  float* ring = shp(x.sm.ring) + 4 * x.ring_slot;
   if (threadIdx.x < n) {
     float t = 0.f;
-    for (int w = 0; w < NT / 32; ++w) t += x.sm.wsum[threadIdx.x * 16 + w];
+    for (int w = 0; w < NT / 32; ++w) t += wsum[threadIdx.x * 16 + w];
     ring[threadIdx.x] = t;
   }
   x.cl.sync();
+  float* fscr = shp(x.sm.fscr);
   if (warp == 0) {
     for (int i = 0; i < n; ++i) {
       float t = 0.f;
-      if (lane < x.P) t = *x.cl.map_shared_rank(ring + i, lane);
+      if (lane < x.g.P) t = *x.cl.map_shared_rank(ring + i, lane);
       // fixed-shape tree over 32 lanes: identical order in every CTA
       t = warp_sum(t);
-      if (lane == 0) x.sm.fscr[i] = t;
+      if (lane == 0) fscr[i] = t;
     }
   }
   __syncthreads();
-  for (int i = 0; i < n; ++i) v[i] = x.sm.fscr[i];
+  for (int i = 0; i < n; ++i) v[i] = fscr[i];
   x.ring_slot = (x.ring_slot + 1) & 3;
 }
 
 // Max of up to two 64-bit keys over the cluster.
 __device__ __noinline__ void cluster_max64(Ctx& x, unsigned long long* v, int n) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long* wmax = shp(x.sm.wmax);
   for (int i = 0; i < n; ++i) {
     const unsigned long long s = warp_max64(v[i]);
-    if (lane == 0) x.sm.wmax[i * 16 + warp] = s;
+    if (lane == 0) wmax[i * 16 + warp] = s;
   }
   __syncthreads();
-  unsigned long long* ring = x.sm.ring64 + 2 * x.ring_slot;
+  unsigned long long* ring = shp(x.sm.ring64) + 2 * x.ring_slot;
   if (threadIdx.x < n) {
     unsigned long long t = 0;
-    for (int w = 0; w < NT / 32; ++w) t = max(t, x.sm.wmax[threadIdx.x * 16 + w]);
+    for (int w = 0; w < NT / 32; ++w) t = max(t, wmax[threadIdx.x * 16 + w]);
     ring[threadIdx.x] = t;
   }
   x.cl.sync();
+  int* iscr = shp(x.sm.iscr);
   if (warp == 0) {
     for (int i = 0; i < n; ++i) {
       unsigned long long t = 0;
-      if (lane < x.P) t = *x.cl.map_shared_rank(ring + i, lane);
+      if (lane < x.g.P) t = *x.cl.map_shared_rank(ring + i, lane);
       t = warp_max64(t);
-      if (lane == 0) x.sm.iscr[2 * i] = (int)(t & 0xffffffffu), x.sm.iscr[2 * i + 1] = (int)(t >> 32);
+      if (lane == 0) iscr[2 * i] = (int)(t & 0xffffffffu), iscr[2 * i + 1] = (int)(t >> 32);
     }
   }
   __syncthreads();
   for (int i = 0; i < n; ++i)
-    v[i] = ((unsigned long long)(uint32_t)x.sm.iscr[2 * i + 1] << 32) | (uint32_t)x.sm.iscr[2 * i];
+    v[i] = ((unsigned long long)(uint32_t)iscr[2 * i + 1] << 32) | (uint32_t)iscr[2 * i];
   __syncthreads();
   x.ring_slot = (x.ring_slot + 1) & 3;
 }
@@ -423,190 +508,253 @@ __device__ __noinline__ void cluster_max64(Ctx& x, unsigned long long* v, int n)
 // Exclusive block scan of one int per thread; returns the exclusive prefix, total via *tot.
 __device__ __noinline__ int block_scan(Ctx& x, int v, int* tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* iscr = shp(x.sm.iscr);
   int inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int t = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += t;
   }
-  if (lane == 31) x.sm.iscr[warp] = inc;
+  if (lane == 31) iscr[warp] = inc;
   __syncthreads();
   if (warp == 0) {
-    int w = lane < NT / 32 ? x.sm.iscr[lane] : 0;
+    int w = lane < NT / 32 ? iscr[lane] : 0;
     int wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, wi, o);
       if (lane >= o) wi += t;
     }
-    if (lane < NT / 32) x.sm.iscr[32 + lane] = wi - w;
-    if (lane == 31) x.sm.iscr[63] = wi;
+    if (lane < NT / 32) iscr[32 + lane] = wi - w;
+    if (lane == 31) iscr[63] = wi;
   }
   __syncthreads();
-  const int ex = x.sm.iscr[32 + warp] + inc - v;
-  *tot = x.sm.iscr[63];
+  const int ex = iscr[32 + warp] + inc - v;
+  *tot = iscr[63];
   __syncthreads();
   return ex;
 }
 
 // Rebuild this CTA's sorted support list (local slots) from a bitmask; returns its length.
+// The list and the CG vectors go to shared memory when this CTA's share fits, else to the
+// global fallback arrays (a per-CTA choice; no barrier depends on it).
 __device__ __noinline__ int build_list(Ctx& x, const uint32_t* m) {
   const int w = threadIdx.x;
   const uint32_t word = w < x.nwords ? m[w] : 0u;
   int total;
   int off = block_scan(x, __popc(word), &total);
+  const bool on_chip = total <= x.cap;
+  int* list = on_chip ? shp(x.sm.cgl) : x.glist;
+  float* cg = on_chip ? shp(x.sm.cgv) : x.gcg;
+  const int stride = on_chip ? x.cap : 2 * x.g.F;
+  x.list = list;
+  x.cgx = cg;
+  x.cgr = cg + stride;
+  x.cgp = cg + 2 * stride;
+  x.cgq = cg + 3 * stride;
   uint32_t bitsleft = word;
   while (bitsleft) {
     const int b = __ffs(bitsleft) - 1;
     bitsleft &= bitsleft - 1;
-    x.list[off++] = w * 32 + b;
+    list[off++] = w * 32 + b;
   }
   __syncthreads();
   return total;
 }
 
-// ------------------------------------------------------------------- the transform pair
-// Frequency-domain stage: DCT-II post-processing of the pair (Z_k, Z_{L-k}), the Omega step,
-// and DCT-III pre-processing back into the pair.  Returns this thread's sum of squares of the
-// residual (MID_RESID).
-__device__ __noinline__ float freq_stage(Ctx& x, int kind, bool fwd_done, bool inv_next, const float* vin, float* vout) {
-  const int P = x.P, h = x.h, S2 = x.S2, Q = x.F, L = x.L, N = x.N;
-  const float wk = sqrtf(2.0f / (float)N), w0 = sqrtf(1.0f / (float)N);
-  const int ntask = h * P + (x.c == 0 ? 1 : 0);
-  const int ncol0 = P > 1 ? P / 2 + 1 : 1;
-  const int ncolh = P > 1 ? P / 2 : 1;
-  float acc = 0.f;
-  for (int t = threadIdx.x; t < ntask; t += NT) {
+// Omega membership bits of every frequency task of this CTA (bit i <-> output f[i]).
+__device__ __noinline__ void build_fbits(Ctx& x) {
+  const Geo g = x.g;
+  uint8_t* fb = shp(x.sm.fbits);
+  const int nt = ntasks(g);
+  for (int t = threadIdx.x; t < nt; t += NT) {
     int sa, kpa, sb, kpb;
-    if (x.c == 0 && t < ncol0) { sa = 0; kpa = t; sb = 0; kpb = (P - t) & (P - 1); }
-    else if (x.c == 0 && t < ncol0 + ncolh) { const int u = t - ncol0; sa = h; kpa = u; sb = h; kpb = P - 1 - u; }
-    else if (x.c == 0) {
-      const int u = t - ncol0 - ncolh;
-      sa = 1 + u % (h - 1); kpa = u / (h - 1); sb = sa + h; kpb = P - 1 - kpa;
-    } else { sa = t % h; kpa = t / h; sb = sa + h; kpb = P - 1 - kpa; }
-    const bool self = (sa == sb) && (kpa == kpb);
-    const int k = kq_of(x, sa) + Q * kpa;
-    int f[4];
-    float X[4] = {0.f, 0.f, 0.f, 0.f};
-    int nf;
-    if (k == 0) { f[0] = 0; f[1] = L; nf = 2; }
-    else if (self) { f[0] = k; f[1] = N - k; nf = 2; }
-    else { f[0] = k; f[1] = N - k; f[2] = L + k; f[3] = L - k; nf = 4; }
-    if (fwd_done) {
-      const float2 Za = x.sm.B[kpa * S2 + sa];
-      const float2 Zb = x.sm.B[kpb * S2 + sb];
-      const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
-      const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
-      const float2 tO = cmul(x.tw.get<-1>(4 * k), O);
-      const float2 u1 = cmul(x.tw.get<-1>(k), cadd(E, tO));
-      const float2 u2 = cmul(x.tw.get<-1>(k + L), csub(E, tO));
-      if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
-      else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
+    uint8_t bits = 0;
+    if (task_pair(g, t, sa, kpa, sb, kpb)) {
+      const int k = kq_of(g, sa) + g.F * kpa;
+      int f[4];
+      const int nf = pair_outputs(g, k, sa == sb && kpa == kpb, f);
+      for (int i = 0; i < nf; ++i) bits |= (uint8_t)(((x.omask[f[i] >> 5] >> (f[i] & 31)) & 1u) << i);
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (i < nf) {
-        const int fi = f[i];
-        const uint32_t word = x.omask[fi >> 5];
-        const bool in = (word >> (fi & 31)) & 1u;
-        if (kind == MID_MASK) {
-          if (!in) X[i] = 0.f;
-        } else {
-          int rk = 0;
-          if (in) rk = x.orank[fi >> 5] + __popc(word & ((1u << (fi & 31)) - 1u));
-          if (kind == MID_RESID) {
-            X[i] = in ? vin[rk] - X[i] : 0.f;
-            acc = fmaf(X[i], X[i], acc);
-          } else if (kind == MID_OUT) {
-            if (in) vout[rk] = X[i];
-          } else {   // MID_IN
-            X[i] = in ? vin[rk] : 0.f;
-          }
-        }
-      }
-    }
-    if (inv_next) {
-      float X4[4];
-      if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
-      else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
-      else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
-      // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
-      const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
-      const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
-      const float2 V1 = cmul(x.tw.get<1>(k), u1);
-      const float2 V2 = cmul(x.tw.get<1>(k + L), u2);
-      const float2 E = cscale(cadd(V1, V2), 0.5f);
-      const float2 O = cmul(cscale(csub(V1, V2), 0.5f), x.tw.get<1>(4 * k));
-      x.sm.B[kpa * S2 + sa] = cadd(E, cmuli(O));
-      if (!self) x.sm.B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
-    }
+    fb[t] = bits;
   }
-  return acc;
+  __syncthreads();
 }
 
+// ------------------------------------------------------------------- the transform pair
 // One application of A (forward), A^T (inverse) or A^T mask A, driven by src / kind.
 //   src   SRC_NONE: the forward input is zero (skip the forward transform)
 //         SRC_CG: compressed CG vector cgp on the local list (nloc entries)
 //         SRC_DENSE_SLOTS: dense-by-slot array `dense` read on the local list
 //         SRC_GLOBAL_N: dense signal vector `gin` of length N in global memory
-//   kind  frequency step (mask Omega / residual with y / write y_M / read u_M)
+//   kind  frequency step: MID_MASK keeps the Omega rows (H d), MID_RESID forms y - A x on Omega,
+//         MID_OUT writes y_M = A x, MID_IN reads u_M (A^T u)
 //   inv   run the DCT-III back to the signal domain (result left in the A buffer)
-// Returns this thread's MID_RESID partial.
-__device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* dense, const float* gin, int kind, bool inv,
-                           const float* vin, float* vout) {
-  const int F = x.F;
-  float2* A = x.sm.A;
+// Returns this thread's sum of squares of the MID_RESID residual.
+__device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* dense, const float* gin, int kind,
+                                        bool inv, const float* vin, float* vout) {
+  const Geo g = x.g;
+  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
+  float2* A = shp(x.sm.A);
+  float2* B = shp(x.sm.B);
+  const uint32_t* signw = shp(x.sm.signw);
+  const cg::cluster_group cl = x.cl;
+  const int F = g.F, P = g.P, S2 = g.S2;
   x.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
+
   if (src != SRC_NONE) {
+    // ---- scatter (W x, sign flip d, Makhoul reordering are all in the slot map)
     if (src == SRC_GLOBAL_N) {
-      for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(x, sg)] * sgn(x, sg);
+      for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(g, sg)] * sgn_bits(signw, sg);
     } else {
-      for (int q = threadIdx.x; q < apad(F); q += NT) A[q] = make_float2(0.f, 0.f);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4* A4 = reinterpret_cast<float4*>(A);
+      for (int q = threadIdx.x; q < apad(F) / 2; q += NT) A4[q] = z4;
       __syncthreads();
+      const int* list = x.list;
+      const float* vals = src == SRC_CG ? x.cgp : dense;
       if (src == SRC_CG) {
         for (int i = threadIdx.x; i < nloc; i += NT) {
-          const int sg = x.list[i];
-          slot_ref(A, sg) = x.cgp[i] * sgn(x, sg);
+          const int sg = list[i];
+          slot_ref(A, sg) = vals[i] * sgn_bits(signw, sg);
         }
       } else {
         for (int i = threadIdx.x; i < nloc; i += NT) {
-          const int sg = x.list[i];
-          slot_ref(A, sg) = dense[sg] * sgn(x, sg);
+          const int sg = list[i];
+          slot_ref(A, sg) = vals[sg] * sgn_bits(signw, sg);
         }
       }
     }
     __syncthreads();
-    local_fft<-1>(A, F, x.tw, x.four_n);
-    x.cl.sync();                                    // every CTA's A is final
+    local_fft<-1>(A, F, tw, g.four_n);
+    cl.sync();                                      // every CTA's A is final
+    // ---- all-to-all pull: B[p][s] = A_p[k_q(s)] * omega_L^{p k_q}; all loads issued first
     {
-      const int S2 = x.S2;
-      for (int idx = threadIdx.x; idx < x.P * S2; idx += NT) {
-        const int p = idx / S2, s = idx - p * S2;
-        const int k = kq_of(x, s);
-        const float2* Ap = x.cl.map_shared_rank(A, p);
-        x.sm.B[idx] = cmul(Ap[aidx(k)], x.tw.get<-1>(8 * p * k));
+      constexpr int EPT = F_MAX / NT;
+      const int lS2 = __ffs(S2) - 1;
+      float2 v[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int idx = threadIdx.x + e * NT;
+        if (idx < F) {
+          const int p = idx >> lS2, s = idx & (S2 - 1);
+          v[e] = cl.map_shared_rank(A, p)[aidx(kq_of(g, s))];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int idx = threadIdx.x + e * NT;
+        if (idx < F) {
+          const int p = idx >> lS2, s = idx & (S2 - 1);
+          B[idx] = cmul(v[e], tw.get<-1>(8 * p * kq_of(g, s)));
+        }
       }
     }
     __syncthreads();
-    pstep<-1>(x.sm.B, x.P, x.S2);
+    pstep<-1>(B, P, S2);
   } else {
-    x.cl.sync();                                    // nobody still reads this CTA's B
+    cl.sync();                                      // nobody still reads this CTA's B
   }
-  const float acc = freq_stage(x, kind, src != SRC_NONE, inv, vin, vout);
+
+  // ---- frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, DCT-III
+  // pre-processing back into the pair
+  float acc = 0.f;
+  {
+    const bool fwd_done = src != SRC_NONE;
+    const float wk = sqrtf(2.0f / (float)g.N), w0 = sqrtf(1.0f / (float)g.N);
+    const int nt = ntasks(g);
+    const uint8_t* fb = shp(x.sm.fbits);
+    const uint32_t* omask = x.omask;
+    const int32_t* orank = x.orank;
+    const int L = g.L;
+    for (int t = threadIdx.x; t < nt; t += NT) {
+      int sa, kpa, sb, kpb;
+      if (!task_pair(g, t, sa, kpa, sb, kpb)) continue;
+      const bool self = (sa == sb) && (kpa == kpb);
+      const int k = kq_of(g, sa) + F * kpa;
+      int f[4];
+      const int nf = pair_outputs(g, k, self, f);
+      const uint32_t bits = fb[t];
+      float X[4] = {0.f, 0.f, 0.f, 0.f};
+      int rk[4] = {0, 0, 0, 0};
+      if (kind != MID_MASK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (i < nf && ((bits >> i) & 1u))
+            rk[i] = orank[f[i] >> 5] + __popc(omask[f[i] >> 5] & ((1u << (f[i] & 31)) - 1u));
+      }
+      if (fwd_done) {
+        const float2 Za = B[kpa * S2 + sa];
+        const float2 Zb = B[kpb * S2 + sb];
+        const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
+        const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
+        const float2 tO = cmul(tw.get<-1>(4 * k), O);
+        const float2 u1 = cmul(tw.get<-1>(k), cadd(E, tO));
+        const float2 u2 = cmul(tw.get<-1>(k + L), csub(E, tO));
+        if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
+        else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i < nf) {
+          const bool in = (bits >> i) & 1u;
+          if (kind == MID_MASK) {
+            if (!in) X[i] = 0.f;
+          } else if (kind == MID_RESID) {
+            X[i] = in ? vin[rk[i]] - X[i] : 0.f;
+            acc = fmaf(X[i], X[i], acc);
+          } else if (kind == MID_OUT) {
+            if (in) vout[rk[i]] = X[i];
+          } else {   // MID_IN
+            X[i] = in ? vin[rk[i]] : 0.f;
+          }
+        }
+      }
+      if (inv) {
+        float X4[4];
+        if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
+        else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
+        else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
+        // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
+        const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
+        const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
+        const float2 V1 = cmul(tw.get<1>(k), u1);
+        const float2 V2 = cmul(tw.get<1>(k + L), u2);
+        const float2 E = cscale(cadd(V1, V2), 0.5f);
+        const float2 O = cmul(cscale(csub(V1, V2), 0.5f), tw.get<1>(4 * k));
+        B[kpa * S2 + sa] = cadd(E, cmuli(O));
+        if (!self) B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
+      }
+    }
+  }
   __syncthreads();
+
   if (inv) {
-    pstep<1>(x.sm.B, x.P, x.S2);
-    x.cl.sync();                                    // every CTA's B is final
-    for (int k = threadIdx.x; k < F; k += NT) {
-      int cc, s;
-      owner_of_kq(x, k, cc, s);
-      const float2* Bc = x.cl.map_shared_rank(x.sm.B, cc);
-      A[aidx(k)] = cmul(Bc[x.c * x.S2 + s], x.tw.get<1>(8 * x.c * k));
+    pstep<1>(B, P, S2);
+    cl.sync();                                      // every CTA's B is final
+    // ---- all-to-all pull back: A[k] = B_{owner(k)}[c][s(k)] * conj(omega_L^{c k})
+    {
+      constexpr int EPT = F_MAX / NT;
+      float2 v[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int k = threadIdx.x + e * NT;
+        if (k < F) {
+          int cc, s;
+          owner_of_kq(g, k, cc, s);
+          v[e] = cl.map_shared_rank(B, cc)[g.c * S2 + s];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int k = threadIdx.x + e * NT;
+        if (k < F) A[aidx(k)] = cmul(v[e], tw.get<1>(8 * g.c * k));
+      }
     }
     __syncthreads();
-    local_fft<1>(A, F, x.tw, x.four_n);
+    local_fft<1>(A, F, tw, g.four_n);
   } else {
-    x.cl.sync();                                    // nobody still reads this CTA's A
+    cl.sync();                                      // nobody still reads this CTA's A
   }
   return acc;
 }
@@ -620,8 +768,10 @@ __device__ void radix_select(Ctx& x, int count, int K, KeyFn key, uint32_t* tau,
   uint32_t prefix = 0, pmask = 0;
   int nd = K;
   int last_eq = 0;
+  uint32_t* htot = shp(x.sm.htot);
+  int* iscr = shp(x.sm.iscr);
   for (int shift = 24; shift >= 0; shift -= 8) {
-    uint32_t* hist = x.sm.hist + 256 * x.hist_slot;
+    uint32_t* hist = shp(x.sm.hist) + 256 * x.hist_slot;
     if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
     __syncthreads();
     for (int i = threadIdx.x; i < count; i += NT) {
@@ -631,15 +781,15 @@ __device__ void radix_select(Ctx& x, int count, int K, KeyFn key, uint32_t* tau,
     x.cl.sync();
     if (threadIdx.x < 256) {
       uint32_t t = 0;
-      for (int r = 0; r < x.P; ++r) t += *x.cl.map_shared_rank(hist + threadIdx.x, r);
-      x.sm.htot[threadIdx.x] = t;
+      for (int r = 0; r < x.g.P; ++r) t += *x.cl.map_shared_rank(hist + threadIdx.x, r);
+      htot[threadIdx.x] = t;
     }
     __syncthreads();
     if (threadIdx.x < 32) {
       // lane l owns digits [8 l, 8 l + 8); suffix sums from the top digit down
       const int lane = threadIdx.x;
       uint32_t mine = 0;
-      for (int d = 0; d < 8; ++d) mine += x.sm.htot[8 * lane + d];
+      for (int d = 0; d < 8; ++d) mine += htot[8 * lane + d];
       uint32_t suf = mine;   // inclusive suffix over lanes >= lane
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -652,24 +802,24 @@ __device__ void radix_select(Ctx& x, int count, int K, KeyFn key, uint32_t* tau,
         uint32_t acc = above;
         int d = 7;
         for (; d > 0; --d) {
-          const uint32_t cnt = x.sm.htot[8 * lane + d];
+          const uint32_t cnt = htot[8 * lane + d];
           if (acc + cnt >= (uint32_t)nd) break;
           acc += cnt;
         }
-        x.sm.iscr[0] = 8 * lane + d;
-        x.sm.iscr[1] = (int)acc;                      // keys strictly above the digit
-        x.sm.iscr[2] = (int)x.sm.htot[8 * lane + d];  // keys equal to the digit (so far)
+        iscr[0] = 8 * lane + d;
+        iscr[1] = (int)acc;                      // keys strictly above the digit
+        iscr[2] = (int)htot[8 * lane + d];       // keys equal to the digit (so far)
       }
-      if (lane == 0 && suf < (uint32_t)nd) {          // fewer candidates than requested
-        x.sm.iscr[0] = -1;
-        x.sm.iscr[1] = (int)suf;
-        x.sm.iscr[2] = 0;
+      if (lane == 0 && suf < (uint32_t)nd) {     // fewer candidates than requested
+        iscr[0] = -1;
+        iscr[1] = (int)suf;
+        iscr[2] = 0;
       }
     }
     __syncthreads();
-    const int dig = x.sm.iscr[0];
-    const int above = x.sm.iscr[1];
-    last_eq = x.sm.iscr[2];
+    const int dig = iscr[0];
+    const int above = iscr[1];
+    last_eq = iscr[2];
     __syncthreads();
     x.hist_slot ^= 1;
     if (dig < 0) {   // take every candidate (uniform decision)
@@ -693,7 +843,7 @@ __device__ void select_topk(Ctx& x, int count, int K, KeyFn key, IdxFn nidx, Mar
   int need, eq;
   radix_select(x, count, K, key, &tau, &need, &eq);
   if (need > 0 && eq > need) {
-    const uint32_t N = (uint32_t)x.N;
+    const uint32_t N = (uint32_t)x.g.N;
     uint32_t tau2;
     int need2, eq2;
     radix_select(
@@ -713,6 +863,11 @@ __device__ void select_topk(Ctx& x, int count, int K, KeyFn key, IdxFn nidx, Mar
 
 __device__ __forceinline__ uint32_t abs_key(float v) { return (__float_as_uint(v) & 0x7fffffffu) + 1u; }
 
+// Correlation c(sigma) = d_n (C^T ...)_n held in the A buffer.
+__device__ __forceinline__ float corr_at(const float2* A, const uint32_t* signw, int sg) {
+  return slot_ref(const_cast<float2*>(A), sg) * sgn_bits(signw, sg);
+}
+
 // ------------------------------------------------------------------------------------ CG
 enum R0Src : int { R0_FROM_A = 0, R0_FROM_CY = 1 };
 
@@ -723,15 +878,23 @@ enum R0Src : int { R0_FROM_A = 0, R0_FROM_CY = 1 };
 // ||r_j|| > tol ||b|| (the printed loop test is read as its negation) and j < maxit.
 __device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r0src, float tol, int maxit) {
   float* xd = x.xd[wi];
+  const float* cy = x.cy;
+  const float2* A = shp(x.sm.A);
+  const uint32_t* signw = shp(x.sm.signw);
+  const int* list = x.list;
+  float* cgx = x.cgx;
+  float* cgr = x.cgr;
+  float* cgp = x.cgp;
+  float* cgq = x.cgq;
   float v[2] = {0.f, 0.f};
   for (int i = threadIdx.x; i < nloc; i += NT) {
-    const int sg = x.list[i];
+    const int sg = list[i];
     const float x0 = warm ? xd[sg] : 0.f;
-    const float r0 = r0src == R0_FROM_A ? slot_ref(x.sm.A, sg) * sgn(x, sg) : x.cy[sg];
-    const float b = x.cy[sg];
-    x.cgx[i] = x0;
-    x.cgr[i] = r0;
-    x.cgp[i] = r0;
+    const float r0 = r0src == R0_FROM_A ? corr_at(A, signw, sg) : cy[sg];
+    const float b = cy[sg];
+    cgx[i] = x0;
+    cgr[i] = r0;
+    cgp[i] = r0;
     v[0] = fmaf(r0, r0, v[0]);
     v[1] = fmaf(b, b, v[1]);
   }
@@ -743,29 +906,28 @@ __device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r
     transform(x, SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
     float pq = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
-      const int sg = x.list[i];
-      const float q = slot_ref(x.sm.A, sg) * sgn(x, sg);
-      x.cgq[i] = q;
-      pq = fmaf(x.cgp[i], q, pq);
+      const float q = corr_at(A, signw, list[i]);
+      cgq[i] = q;
+      pq = fmaf(cgp[i], q, pq);
     }
     cluster_sum(x, &pq, 1);
     const float alpha = rr / pq;
     float rn = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
-      x.cgx[i] = fmaf(alpha, x.cgp[i], x.cgx[i]);
-      const float r = fmaf(-alpha, x.cgq[i], x.cgr[i]);
-      x.cgr[i] = r;
+      cgx[i] = fmaf(alpha, cgp[i], cgx[i]);
+      const float r = fmaf(-alpha, cgq[i], cgr[i]);
+      cgr[i] = r;
       rn = fmaf(r, r, rn);
     }
     cluster_sum(x, &rn, 1);
     const float beta = rn / rr;
     rr = rn;
-    for (int i = threadIdx.x; i < nloc; i += NT) x.cgp[i] = fmaf(beta, x.cgp[i], x.cgr[i]);
+    for (int i = threadIdx.x; i < nloc; i += NT) cgp[i] = fmaf(beta, cgp[i], cgr[i]);
     ++it;
   }
   x.cg_total += it;
   if (it >= maxit && rr > stop2) x.cg_hits += 1;
-  for (int i = threadIdx.x; i < nloc; i += NT) xd[x.list[i]] = x.cgx[i];
+  for (int i = threadIdx.x; i < nloc; i += NT) xd[list[i]] = cgx[i];
   __syncthreads();
 }
 
@@ -776,61 +938,65 @@ __device__ __noinline__ float resid_corr(Ctx& x, int wi, int nloc, const float* 
   return v;
 }
 
-// Correlation of the slot c(sigma) = d_n (C^T ...)_n held in the A buffer.
-__device__ __forceinline__ float corr(const Ctx& x, int sg) { return slot_ref(x.sm.A, sg) * sgn(x, sg); }
-
 // ------------------------------------------------------------------------ task execution
 __device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int nloc, float rn2, int outer) {
-  const int N = x.N, P = x.P;
+  const Geo g = x.g;
+  const int N = g.N, P = g.P;
   // zero s_out and the output bitmask (contiguous share per CTA)
   const int per = N / P;
-  for (int i = threadIdx.x; i < per; i += NT) t.out[x.c * per + i] = 0.f;
+  for (int i = threadIdx.x; i < per; i += NT) t.out[g.c * per + i] = 0.f;
   const int W = (N + 31) / 32;
   const int wper = (W + P - 1) / P;
   for (int i = threadIdx.x; i < wper; i += NT) {
-    const int w = x.c * wper + i;
+    const int w = g.c * wper + i;
     if (w < W) x.bits[w] = 0u;
   }
   x.cl.sync();
-  for (int i = threadIdx.x; i < nloc; i += NT) {
-    const int sg = x.list[i];
-    const int n = n_of_slot(x, sg);
-    t.out[n] = x.xd[wi][sg];
-    atomicOr(&x.bits[n >> 5], 1u << (n & 31));
+  {
+    const int* list = x.list;
+    const float* xd = x.xd[wi];
+    for (int i = threadIdx.x; i < nloc; i += NT) {
+      const int sg = list[i];
+      const int n = n_of_slot(g, sg);
+      t.out[n] = xd[sg];
+      atomicOr(&x.bits[n >> 5], 1u << (n & 31));
+    }
   }
   x.cl.sync();
   // sorted support: CTA c compacts words [c wper, (c+1) wper)
   int cnt = 0;
   for (int i = threadIdx.x; i < wper; i += NT) {
-    const int w = x.c * wper + i;
+    const int w = g.c * wper + i;
     if (w < W) cnt += __popc(x.bits[w]);
   }
   float fc = (float)cnt;   // counts < 2^24: exact in FP32
-  // per-CTA total into ring, then exclusive prefix over ranks
+  float* ring = shp(x.sm.ring);
+  int* iscr = shp(x.sm.iscr);
   {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* wsum = shp(x.sm.wsum);
     float s = warp_sum(fc);
-    if (lane == 0) x.sm.wsum[warp] = s;
+    if (lane == 0) wsum[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
       float tt = 0.f;
-      for (int w = 0; w < NT / 32; ++w) tt += x.sm.wsum[w];
-      x.sm.ring[4 * x.ring_slot] = tt;
+      for (int w = 0; w < NT / 32; ++w) tt += wsum[w];
+      ring[4 * x.ring_slot] = tt;
     }
     x.cl.sync();
     if (threadIdx.x == 0) {
       float off = 0.f;
-      for (int r = 0; r < x.c; ++r) off += *x.cl.map_shared_rank(x.sm.ring + 4 * x.ring_slot, r);
-      x.sm.iscr[40] = (int)off;
+      for (int r = 0; r < g.c; ++r) off += *x.cl.map_shared_rank(ring + 4 * x.ring_slot, r);
+      iscr[40] = (int)off;
     }
     __syncthreads();
     x.ring_slot = (x.ring_slot + 1) & 3;
   }
-  int base = x.sm.iscr[40];
+  int base = iscr[40];
   __syncthreads();
   // block-ordered compaction: wper words per CTA, processed NT at a time
   for (int w0 = 0; w0 < wper; w0 += NT) {
-    const int w = x.c * wper + w0 + threadIdx.x;
+    const int w = g.c * wper + w0 + threadIdx.x;
     const uint32_t word = (w0 + threadIdx.x < wper && w < W) ? x.bits[w] : 0u;
     int tot;
     int off = base + block_scan(x, __popc(word), &tot);
@@ -843,7 +1009,7 @@ __device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int n
     }
     base += tot;
   }
-  if (x.c == 0 && threadIdx.x == 0 && t.stats) {
+  if (g.c == 0 && threadIdx.x == 0 && t.stats) {
     cs_stats st;
     st.outer_iters = outer;
     st.cg_iters_total = x.cg_total;
@@ -860,7 +1026,10 @@ __device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int n
 // A^T y into cy (dense by slot, signed) and the A buffer; returns ||y||^2.
 __device__ __noinline__ float init_correlation(Ctx& x, const float* y) {
   float v = transform(x, SRC_NONE, 0, nullptr, nullptr, MID_RESID, true, y, nullptr);
-  for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) x.cy[sg] = corr(x, sg);
+  const float2* A = shp(x.sm.A);
+  const uint32_t* signw = shp(x.sm.signw);
+  float* cy = x.cy;
+  for (int sg = threadIdx.x; sg < 2 * x.g.F; sg += NT) cy[sg] = corr_at(A, signw, sg);
   cluster_sum(x, &v, 1);
   return v;
 }
@@ -872,37 +1041,41 @@ __device__ void zero_mask(Ctx& x, uint32_t* m) {
 
 // Top-K of |c| over the local slots not in `excl` (may be null); marks into `dst`.
 __device__ __noinline__ void topk_corr(Ctx& x, int K, const uint32_t* excl, uint32_t* dst) {
+  const Geo g = x.g;
+  float2* A = shp(x.sm.A);
   select_topk(
-      x, 2 * x.F, K,
+      x, 2 * g.F, K,
       [&](int sg) -> uint32_t {
         if (excl && mask_bit(excl, sg)) return 0u;
-        return abs_key(slot_ref(x.sm.A, sg));
+        return abs_key(slot_ref(A, sg));
       },
-      [&](int sg) { return n_of_slot(x, sg); },
+      [&](int sg) { return n_of_slot(g, sg); },
       [&](int sg) { atomicOr(&dst[sg >> 5], 1u << (sg & 31)); });
 }
 
 __device__ __noinline__ void run_omp(Ctx& x, const Task& t) {
   const float* y = t.in;
   init_correlation(x, y);
-  uint32_t* mA = x.sm.mask[0];
+  uint32_t* mA = shp(x.sm.mask[0]);
   zero_mask(x, mA);
   int nloc = 0;
   float rn2 = 0.f;
+  const Geo g = x.g;
+  float2* A = shp(x.sm.A);
   for (int it = 0; it < t.K; ++it) {
     unsigned long long key = 0;
-    for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) {
+    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
       if (mask_bit(mA, sg)) continue;
-      const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(x.sm.A, sg)) << 32) |
-                                    (0xffffffffu - (uint32_t)n_of_slot(x, sg));
+      const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(A, sg)) << 32) |
+                                    (0xffffffffu - (uint32_t)n_of_slot(g, sg));
       key = kk > key ? kk : key;
     }
     cluster_max64(x, &key, 1);
     if (key == 0ull) break;   // no candidate left (uniform: key is cluster-reduced)
     const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
     int owner, sg;
-    slot_of_n(x, n, owner, sg);
-    if (owner == x.c && threadIdx.x == 0) {
+    slot_of_n(g, n, owner, sg);
+    if (owner == g.c && threadIdx.x == 0) {
       mA[sg >> 5] |= 1u << (sg & 31);
       x.xd[0][sg] = 0.f;
     }
@@ -918,36 +1091,46 @@ __device__ __noinline__ void run_sp(Ctx& x, const Task& t) {
   const float* y = t.in;
   init_correlation(x, y);
   int acc = 0;   // index of the accepted (support, solution) pair
-  uint32_t* mA = x.sm.mask[acc];
+  uint32_t* mA = shp(x.sm.mask[acc]);
   zero_mask(x, mA);
   topk_corr(x, t.K, nullptr, mA);
   int nloc = build_list(x, mA);
   cg_solve(x, acc, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
   float rn2 = resid_corr(x, acc, nloc, y);
   int rounds = 0;
+  const Geo g = x.g;
   while (rounds < t.outer_max) {
     ++rounds;
     const int wi = acc ^ 1;
-    uint32_t* mW = x.sm.mask[wi];
-    mA = x.sm.mask[acc];
+    uint32_t* mW = shp(x.sm.mask[wi]);
+    mA = shp(x.sm.mask[acc]);
     // S~ = S u topK_{not in S} |A^T r|
     for (int w = threadIdx.x; w < x.nwords; w += NT) mW[w] = mA[w];
     __syncthreads();
     topk_corr(x, t.K, mA, mW);
     int nW = build_list(x, mW);
     // warm start: x0 = s on S, 0 on the new entries; r0 = c on S~
-    for (int i = threadIdx.x; i < nW; i += NT) {
-      const int sg = x.list[i];
-      x.xd[wi][sg] = mask_bit(mA, sg) ? x.xd[acc][sg] : 0.f;
+    {
+      const int* list = x.list;
+      float* xw = x.xd[wi];
+      const float* xa = x.xd[acc];
+      for (int i = threadIdx.x; i < nW; i += NT) {
+        const int sg = list[i];
+        xw[sg] = mask_bit(mA, sg) ? xa[sg] : 0.f;
+      }
     }
     __syncthreads();
     cg_solve(x, wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
     // S' = topK_{j in S~} |u_j|
     zero_mask(x, mW);
-    select_topk(
-        x, nW, t.K, [&](int i) -> uint32_t { return abs_key(x.xd[wi][x.list[i]]); },
-        [&](int i) { return n_of_slot(x, x.list[i]); },
-        [&](int i) { const int sg = x.list[i]; atomicOr(&mW[sg >> 5], 1u << (sg & 31)); });
+    {
+      const int* list = x.list;
+      const float* xw = x.xd[wi];
+      select_topk(
+          x, nW, t.K, [&](int i) -> uint32_t { return abs_key(xw[list[i]]); },
+          [&](int i) { return n_of_slot(g, list[i]); },
+          [&](int i) { const int sg = list[i]; atomicOr(&mW[sg >> 5], 1u << (sg & 31)); });
+    }
     nW = build_list(x, mW);
     // r0 for the warm start on S' (x0 = u restricted to S')
     resid_corr(x, wi, nW, y);
@@ -962,32 +1145,36 @@ __device__ __noinline__ void run_sp(Ctx& x, const Task& t) {
     nloc = nW;
   }
   // the returned pair is `acc`; rebuild its list (the working list may differ)
-  nloc = build_list(x, x.sm.mask[acc]);
+  nloc = build_list(x, shp(x.sm.mask[acc]));
   write_recovery(x, t, acc, nloc, rn2, rounds);
 }
 
 __device__ __noinline__ void run_ompr(Ctx& x, const Task& t) {
   const float* y = t.in;
   init_correlation(x, y);
-  uint32_t* mA = x.sm.mask[0];
+  uint32_t* mA = shp(x.sm.mask[0]);
   zero_mask(x, mA);
   topk_corr(x, t.K, nullptr, mA);
   int nloc = build_list(x, mA);
   cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
   float rn2 = resid_corr(x, 0, nloc, y);
   int swaps = 0;
+  const Geo g = x.g;
+  const float2* A = shp(x.sm.A);
+  const uint32_t* signw = shp(x.sm.signw);
   while (swaps < t.outer_max) {
     // z = s + A^T r: j = argmax_{not in S} |z|, i = argmin_{in S} |z| (lowest index on ties)
     unsigned long long key[2] = {0ull, 0ull};
-    for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) {
-      const uint32_t lo = 0xffffffffu - (uint32_t)n_of_slot(x, sg);
+    const float* xd = x.xd[0];
+    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+      const uint32_t lo = 0xffffffffu - (uint32_t)n_of_slot(g, sg);
       if (mask_bit(mA, sg)) {
-        const float z = x.xd[0][sg] + corr(x, sg);
+        const float z = xd[sg] + corr_at(A, signw, sg);
         const unsigned long long kk =
             ((unsigned long long)(0xffffffffu - (__float_as_uint(z) & 0x7fffffffu)) << 32) | lo;
         key[1] = kk > key[1] ? kk : key[1];
       } else {
-        const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(x.sm.A, sg)) << 32) | lo;
+        const unsigned long long kk = ((unsigned long long)abs_key(corr_at(A, signw, sg)) << 32) | lo;
         key[0] = kk > key[0] ? kk : key[0];
       }
     }
@@ -998,11 +1185,11 @@ __device__ __noinline__ void run_ompr(Ctx& x, const Task& t) {
     const int nj = (int)(0xffffffffu - (uint32_t)(key[0] & 0xffffffffu));
     const int ni = (int)(0xffffffffu - (uint32_t)(key[1] & 0xffffffffu));
     int oj, sj, oi, si;
-    slot_of_n(x, nj, oj, sj);
-    slot_of_n(x, ni, oi, si);
+    slot_of_n(g, nj, oj, sj);
+    slot_of_n(g, ni, oi, si);
     if (threadIdx.x == 0) {
-      if (oi == x.c) { mA[si >> 5] &= ~(1u << (si & 31)); x.xd[0][si] = 0.f; }
-      if (oj == x.c) { mA[sj >> 5] |= 1u << (sj & 31); x.xd[0][sj] = 0.f; }
+      if (oi == g.c) { mA[si >> 5] &= ~(1u << (si & 31)); x.xd[0][si] = 0.f; }
+      if (oj == g.c) { mA[sj >> 5] |= 1u << (sj & 31); x.xd[0][sj] = 0.f; }
     }
     __syncthreads();
     ++swaps;
@@ -1017,58 +1204,59 @@ __device__ __noinline__ void run_ompr(Ctx& x, const Task& t) {
 // Fixed support from a sorted global index list: set the bits this CTA owns.
 __device__ __noinline__ void mask_from_support(Ctx& x, const int32_t* supp, int k, uint32_t* m) {
   zero_mask(x, m);
+  const Geo g = x.g;
   for (int i = threadIdx.x; i < k; i += NT) {
     const int n = supp[i];
-    if (n < 0 || n >= x.N) continue;
+    if (n < 0 || n >= g.N) continue;
     int owner, sg;
-    slot_of_n(x, n, owner, sg);
-    if (owner == x.c) atomicOr(&m[sg >> 5], 1u << (sg & 31));
+    slot_of_n(g, n, owner, sg);
+    if (owner == g.c) atomicOr(&m[sg >> 5], 1u << (sg & 31));
   }
   __syncthreads();
 }
 
 __device__ __noinline__ void run_ls_solve(Ctx& x, const Task& t) {
   init_correlation(x, t.in);
-  uint32_t* m = x.sm.mask[0];
+  uint32_t* m = shp(x.sm.mask[0]);
   mask_from_support(x, t.supp_in, t.k_in, m);
   const int nloc = build_list(x, m);
   cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  const Geo g = x.g;
   for (int i = threadIdx.x; i < t.k_in; i += NT) {
     const int n = t.supp_in[i];
-    if (n < 0 || n >= x.N) continue;
+    if (n < 0 || n >= g.N) continue;
     int owner, sg;
-    slot_of_n(x, n, owner, sg);
-    if (owner == x.c) t.out[i] = x.xd[0][sg];
+    slot_of_n(g, n, owner, sg);
+    if (owner == g.c) t.out[i] = x.xd[0][sg];
   }
-  if (x.c == 0 && threadIdx.x == 0 && t.stats) {
+  if (g.c == 0 && threadIdx.x == 0 && t.stats) {
     cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK, x.ntrans};
     *t.stats = st;
   }
 }
 
 __device__ __noinline__ void run_ls_backward(Ctx& x, const Task& t) {
-  uint32_t* m = x.sm.mask[0];
+  uint32_t* m = shp(x.sm.mask[0]);
   mask_from_support(x, t.supp_in, t.k_in, m);
+  const Geo g = x.g;
   // b = g placed by slot (cy doubles as the right-hand side)
   for (int i = threadIdx.x; i < t.k_in; i += NT) {
     const int n = t.supp_in[i];
-    if (n < 0 || n >= x.N) continue;
+    if (n < 0 || n >= g.N) continue;
     int owner, sg;
-    slot_of_n(x, n, owner, sg);
-    if (owner == x.c) x.cy[sg] = t.in[i];
+    slot_of_n(g, n, owner, sg);
+    if (owner == g.c) x.cy[sg] = t.in[i];
   }
   __syncthreads();
   const int nloc = build_list(x, m);
   cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
   // dy = A_S z
   transform(x, SRC_DENSE_SLOTS, nloc, x.xd[0], nullptr, MID_OUT, false, nullptr, t.out);
-  if (x.c == 0 && threadIdx.x == 0 && t.stats) {
+  if (g.c == 0 && threadIdx.x == 0 && t.stats) {
     cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK, x.ntrans};
     *t.stats = st;
   }
 }
-
-extern __shared__ __align__(16) unsigned char smem_raw[];
 
 __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   cg::cluster_group cl = cg::this_cluster();
@@ -1076,20 +1264,17 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   const int c = (int)cl.block_rank();
   const int cid = blockIdx.x / P;
   const int ncl = gridDim.x / P;
-  Ctx x{cl, carve(smem_raw, lp.F_alloc)};
-  x.c = c;
+  Ctx x{cl, carve(lp.F_alloc)};
   x.ring_slot = 0;
   x.hist_slot = 0;
+  x.cap = cg_cap(lp.F_alloc);
   float* base = lp.scratch + (size_t)cid * lp.scratch_per_cluster + (size_t)c * scratch_floats_per_cta(lp.F_alloc);
   const size_t a = 2 * (size_t)lp.F_alloc;
   x.xd[0] = base;
   x.xd[1] = base + a;
   x.cy = base + 2 * a;
-  x.list = reinterpret_cast<int*>(base + 3 * a);
-  x.cgx = base + 4 * a;
-  x.cgr = base + 5 * a;
-  x.cgp = base + 6 * a;
-  x.cgq = base + 7 * a;
+  x.glist = reinterpret_cast<int*>(base + 3 * a);
+  x.gcg = base + 4 * a;
   x.bits = lp.bits + (size_t)cid * lp.bits_per_cluster;
 
   for (int ti = cid; ti < lp.ntasks; ti += ncl) {
@@ -1099,37 +1284,52 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
       if (c == 0 && threadIdx.x == 0 && t.stats) t.stats->status = CS_ERR_INVALID_ARG;
       continue;
     }
-    x.N = op.N; x.M = op.M; x.L = op.N >> 1; x.P = P; x.F = op.F;
-    x.h = op.F / (2 * P); x.S2 = 2 * x.h; x.four_n = 4 * op.N;
+    Geo& g = x.g;
+    g.N = op.N; g.L = op.N >> 1; g.P = P; g.F = op.F; g.c = c;
+    g.h = op.F / (2 * P); g.lh = __ffs(g.h) - 1; g.S2 = 2 * g.h; g.four_n = 4 * op.N;
+    x.M = op.M;
     x.nwords = (2 * op.F + 31) / 32;
     x.omask = op.omask; x.orank = op.orank;
     x.cg_total = 0; x.cg_hits = 0; x.ntrans = 0;
+    x.list = x.glist;
+    x.cgx = x.gcg; x.cgr = x.gcg + a; x.cgp = x.gcg + 2 * a; x.cgq = x.gcg + 3 * a;
     // twiddle tables and sign bits
     const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
-    for (int i = threadIdx.x; i < nlo; i += NT) x.sm.twlo[i] = op.tw[i];
-    for (int i = threadIdx.x; i < nhi; i += NT) x.sm.twhi[i] = op.tw[nlo + i];
+    float2* twlo = shp(x.sm.twlo);
+    float2* twhi = shp(x.sm.twhi);
+    for (int i = threadIdx.x; i < nlo; i += NT) twlo[i] = op.tw[i];
+    for (int i = threadIdx.x; i < nhi; i += NT) twhi[i] = op.tw[nlo + i];
     x.tw.lo = x.sm.twlo; x.tw.hi = x.sm.twhi; x.tw.lo_bits = op.lo_bits; x.tw.lo_mask = nlo - 1;
-    x.tw.mask4n = x.four_n - 1;
-    for (int w = threadIdx.x; w < x.nwords; w += NT) {
-      uint32_t bitsw = 0u;
-      for (int b = 0; b < 32; ++b) {
-        const int sg = 32 * w + b;
-        if (sg < 2 * op.F) {
-          const uint64_t hsh = mix64(op.sign_key + (uint64_t)n_of_slot(x, sg) + 0x9E3779B97F4A7C15ull);
-          bitsw |= (uint32_t)(hsh >> 63) << b;
+    x.tw.mask4n = g.four_n - 1;
+    {
+      uint32_t* signw = shp(x.sm.signw);
+      const Geo gg = g;
+      for (int w = threadIdx.x; w < x.nwords; w += NT) {
+        uint32_t bitsw = 0u;
+        for (int b = 0; b < 32; ++b) {
+          const int sg = 32 * w + b;
+          if (sg < 2 * op.F) {
+            const uint64_t hsh = mix64(op.sign_key + (uint64_t)n_of_slot(gg, sg) + 0x9E3779B97F4A7C15ull);
+            bitsw |= (uint32_t)(hsh >> 63) << b;
+          }
         }
+        signw[w] = bitsw;
       }
-      x.sm.signw[w] = bitsw;
     }
     __syncthreads();
+    build_fbits(x);
     switch (t.mode) {
       case MODE_APPLY:
         transform(x, SRC_GLOBAL_N, 0, nullptr, t.in, MID_OUT, false, nullptr, t.out);
         break;
-      case MODE_APPLY_T:
+      case MODE_APPLY_T: {
         transform(x, SRC_NONE, 0, nullptr, nullptr, MID_IN, true, t.in, nullptr);
-        for (int sg = threadIdx.x; sg < 2 * x.F; sg += NT) t.out[n_of_slot(x, sg)] = corr(x, sg);
+        const float2* A = shp(x.sm.A);
+        const uint32_t* signw = shp(x.sm.signw);
+        const Geo gg = g;
+        for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[n_of_slot(gg, sg)] = corr_at(A, signw, sg);
         break;
+      }
       case MODE_RECOVER:
         if (t.algo == CS_OMP) run_omp(x, t);
         else if (t.algo == CS_SP) run_sp(x, t);
