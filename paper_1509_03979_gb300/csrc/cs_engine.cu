@@ -118,7 +118,9 @@ __device__ __forceinline__ T* shp(T* p) {
 __device__ __forceinline__ int aidx(int q) { return q + (q >> 4); }
 __host__ __device__ inline int apad(int F) { return F + F / 16; }
 
-// Two-level twiddle table: omega_{4N}^j = exp(-2 pi i j / 4N) = lo[j & m] * hi[j >> lo_bits].
+// Two-level twiddle table: omega_{4N}^j = exp(-2 pi i j / 4N) = lo[j & m] * hi[j >> lo_bits];
+// lo is stored with the same one-in-16 padding as the FFT buffer, which keeps the strided
+// lookups of the FFT passes and the DCT twiddles (strides 1, 4, 8) free of bank conflicts.
 struct Tw {
   const float2* lo;
   const float2* hi;
@@ -128,7 +130,7 @@ struct Tw {
   template <int DIR>
   __device__ __forceinline__ float2 get(int j) const {
     j &= mask4n;
-    const float2 w = cmul(lo[j & lo_mask], hi[j >> lo_bits]);
+    const float2 w = cmul(lo[aidx(j & lo_mask)], hi[j >> lo_bits]);
     return DIR > 0 ? cconj(w) : w;
   }
 };
@@ -196,20 +198,43 @@ __device__ __forceinline__ void fft_pass(float2* X, int F, int Ns, const Tw& tw,
   __syncthreads();
 }
 
-// Q-point FFT of the local buffer, natural order in and out (one call per FFT; the passes
-// are inlined here so registers are saved once per FFT, not once per pass).
+// Q-point FFT of the local buffer, natural order in and out.  The pass plan (radix 16 while
+// at least 16 points remain per group, then 8/4/2) is fixed at compile time for each
+// F = 2^LOGF: a runtime pass loop measured worse register allocation (spills).
+template <int LOGF, int DIR, int LOGNS = 0>
+__device__ __forceinline__ void fft_plan(float2* X, const Tw& tw, int four_n) {
+  constexpr int REM = LOGF - LOGNS;
+  if constexpr (REM >= 4) {
+    fft_pass<16, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
+    fft_plan<LOGF, DIR, LOGNS + 4>(X, tw, four_n);
+  } else if constexpr (REM == 3) {
+    fft_pass<8, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
+  } else if constexpr (REM == 2) {
+    fft_pass<4, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
+  } else if constexpr (REM == 1) {
+    fft_pass<2, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
+  }
+}
+
 template <int DIR>
 __device__ __noinline__ void local_fft(float2* X, int F, Tw tw, int four_n) {
   X = shp(X);
   tw.lo = shp(tw.lo);
   tw.hi = shp(tw.hi);
-  int Ns = 1;
-  while (Ns < F) {
-    const int rem = F / Ns;
-    if (rem >= 16) { fft_pass<16, DIR>(X, F, Ns, tw, four_n); Ns *= 16; }
-    else if (rem == 8) { fft_pass<8, DIR>(X, F, Ns, tw, four_n); Ns *= 8; }
-    else if (rem == 4) { fft_pass<4, DIR>(X, F, Ns, tw, four_n); Ns *= 4; }
-    else { fft_pass<2, DIR>(X, F, Ns, tw, four_n); Ns *= 2; }
+  switch (__ffs(F) - 1) {
+    case 1: fft_plan<1, DIR>(X, tw, four_n); break;
+    case 2: fft_plan<2, DIR>(X, tw, four_n); break;
+    case 3: fft_plan<3, DIR>(X, tw, four_n); break;
+    case 4: fft_plan<4, DIR>(X, tw, four_n); break;
+    case 5: fft_plan<5, DIR>(X, tw, four_n); break;
+    case 6: fft_plan<6, DIR>(X, tw, four_n); break;
+    case 7: fft_plan<7, DIR>(X, tw, four_n); break;
+    case 8: fft_plan<8, DIR>(X, tw, four_n); break;
+    case 9: fft_plan<9, DIR>(X, tw, four_n); break;
+    case 10: fft_plan<10, DIR>(X, tw, four_n); break;
+    case 11: fft_plan<11, DIR>(X, tw, four_n); break;
+    case 12: fft_plan<12, DIR>(X, tw, four_n); break;
+    default: fft_plan<13, DIR>(X, tw, four_n); break;
   }
 }
 
@@ -255,7 +280,8 @@ __device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
 
 // ------------------------------------------------------------------------- shared layout
 
-constexpr int CG_CAP_MAX = 3072;   // support entries per CTA whose CG vectors live on chip
+constexpr int CG_CAP_MAX = 0;      // support entries per CTA whose CG vectors live in shared memory
+                                   // (0: global, L1-cached; a larger L1 share measured faster)
 __host__ __device__ inline int cg_cap(int F_alloc) { return 2 * F_alloc < CG_CAP_MAX ? 2 * F_alloc : CG_CAP_MAX; }
 
 struct Smem {
@@ -294,7 +320,7 @@ __host__ __device__ inline void layout(int F_alloc, Bump& take, Smem* s) {
   const int cap = cg_cap(F_alloc);
   unsigned char* A = take(sizeof(float2) * apad(F_alloc));
   unsigned char* B = take(sizeof(float2) * F_alloc);
-  unsigned char* tl = take(sizeof(float2) * 1024);
+  unsigned char* tl = take(sizeof(float2) * apad(1024));
   unsigned char* th = take(sizeof(float2) * 1024);
   unsigned char* sw = take(4 * nw);
   unsigned char* m0 = take(4 * nw);
@@ -539,10 +565,14 @@ __device__ __noinline__ int block_scan(Ctx& x, int v, int* tot) {
 // The list and the CG vectors go to shared memory when this CTA's share fits, else to the
 // global fallback arrays (a per-CTA choice; no barrier depends on it).
 __device__ __noinline__ int build_list(Ctx& x, const uint32_t* m) {
-  const int w = threadIdx.x;
-  const uint32_t word = w < x.nwords ? m[w] : 0u;
-  int total;
-  int off = block_scan(x, __popc(word), &total);
+  // total first (to choose the destination), then a chunked ordered compaction
+  int total = 0;
+  for (int w0 = 0; w0 < x.nwords; w0 += NT) {
+    const int w = w0 + threadIdx.x;
+    int t;
+    block_scan(x, w < x.nwords ? __popc(m[w]) : 0, &t);
+    total += t;
+  }
   const bool on_chip = total <= x.cap;
   int* list = on_chip ? shp(x.sm.cgl) : x.glist;
   float* cg = on_chip ? shp(x.sm.cgv) : x.gcg;
@@ -552,11 +582,19 @@ __device__ __noinline__ int build_list(Ctx& x, const uint32_t* m) {
   x.cgr = cg + stride;
   x.cgp = cg + 2 * stride;
   x.cgq = cg + 3 * stride;
-  uint32_t bitsleft = word;
-  while (bitsleft) {
-    const int b = __ffs(bitsleft) - 1;
-    bitsleft &= bitsleft - 1;
-    list[off++] = w * 32 + b;
+  int base = 0;
+  for (int w0 = 0; w0 < x.nwords; w0 += NT) {
+    const int w = w0 + threadIdx.x;
+    const uint32_t word = w < x.nwords ? m[w] : 0u;
+    int t;
+    int off = base + block_scan(x, __popc(word), &t);
+    uint32_t bitsleft = word;
+    while (bitsleft) {
+      const int b = __ffs(bitsleft) - 1;
+      bitsleft &= bitsleft - 1;
+      list[off++] = w * 32 + b;
+    }
+    base += t;
   }
   __syncthreads();
   return total;
@@ -582,6 +620,190 @@ __device__ __noinline__ void build_fbits(Ctx& x) {
 }
 
 // ------------------------------------------------------------------- the transform pair
+// Forward half: scatter (W x, sign flip d and Makhoul's reordering are all in the slot map),
+// local Q-point FFT, cluster barrier, then the all-to-all pull fused with the P-point DFT:
+// the thread that owns frequency slot s loads A_p[k_q(s)] from every CTA p, multiplies by
+// omega_L^{p k_q} = (omega_L^{k_q})^p and transforms over p in registers.
+template <int PT>
+__device__ __forceinline__ void pull_fwd(const cg::cluster_group& cl, const Geo& g, const Tw& tw, float2* A, float2* B) {
+  for (int s = threadIdx.x; s < g.S2; s += NT) {
+    const int k = kq_of(g, s);
+    float2 v[PT];
+#pragma unroll
+    for (int p = 0; p < PT; ++p) v[p] = cl.map_shared_rank(A, p)[aidx(k)];
+    if constexpr (PT > 1) {
+      twiddle_powers<PT, -1>(v, tw, 8 * k);
+      dft<PT, -1>(v);
+    }
+#pragma unroll
+    for (int p = 0; p < PT; ++p) B[p * g.S2 + s] = v[p];
+  }
+}
+
+__device__ __noinline__ void scatter_fwd(Ctx& x, int src, int nloc, const float* dense, const float* gin) {
+  const Geo g = x.g;
+  float2* A = shp(x.sm.A);
+  const uint32_t* signw = shp(x.sm.signw);
+  const int F = g.F;
+  if (src == SRC_GLOBAL_N) {
+    for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(g, sg)] * sgn_bits(signw, sg);
+  } else {
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4* A4 = reinterpret_cast<float4*>(A);
+    for (int q = threadIdx.x; q < apad(F) / 2; q += NT) A4[q] = z4;
+    __syncthreads();
+    const int* list = x.list;
+    if (src == SRC_CG) {
+      const float* vals = x.cgp;
+      for (int i = threadIdx.x; i < nloc; i += NT) {
+        const int sg = list[i];
+        slot_ref(A, sg) = vals[i] * sgn_bits(signw, sg);
+      }
+    } else {
+      for (int i = threadIdx.x; i < nloc; i += NT) {
+        const int sg = list[i];
+        slot_ref(A, sg) = dense[sg] * sgn_bits(signw, sg);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Cluster barrier (every CTA's A is final), then the fused pull + P-point DFT into B.
+__device__ __noinline__ void exchange_fwd(Ctx& x) {
+  const Geo g = x.g;
+  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
+  float2* A = shp(x.sm.A);
+  float2* B = shp(x.sm.B);
+  x.cl.sync();
+  switch (g.P) {
+    case 1: pull_fwd<1>(x.cl, g, tw, A, B); break;
+    case 2: pull_fwd<2>(x.cl, g, tw, A, B); break;
+    case 4: pull_fwd<4>(x.cl, g, tw, A, B); break;
+    case 8: pull_fwd<8>(x.cl, g, tw, A, B); break;
+    default: pull_fwd<16>(x.cl, g, tw, A, B); break;
+  }
+  __syncthreads();
+}
+
+// Frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, and DCT-III
+// pre-processing back into the pair.  Returns this thread's MID_RESID sum of squares.
+__device__ __noinline__ float freq_half(Ctx& x, int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
+  const Geo g = x.g;
+  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
+  float2* B = shp(x.sm.B);
+  const uint8_t* fb = shp(x.sm.fbits);
+  const uint32_t* omask = x.omask;
+  const int32_t* orank = x.orank;
+  const int F = g.F, S2 = g.S2, L = g.L;
+  const float wk = sqrtf(2.0f / (float)g.N), w0 = sqrtf(1.0f / (float)g.N);
+  const int nt = ntasks(g);
+  float acc = 0.f;
+  for (int t = threadIdx.x; t < nt; t += NT) {
+    int sa, kpa, sb, kpb;
+    if (!task_pair(g, t, sa, kpa, sb, kpb)) continue;
+    const bool self = (sa == sb) && (kpa == kpb);
+    const int k = kq_of(g, sa) + F * kpa;
+    const uint32_t bits = fb[t];
+    float X[4] = {0.f, 0.f, 0.f, 0.f};
+    if (fwd_done) {
+      const float2 Za = B[kpa * S2 + sa];
+      const float2 Zb = B[kpb * S2 + sb];
+      const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
+      const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
+      const float2 tO = cmul(tw.get<-1>(4 * k), O);
+      const float2 u1 = cmul(tw.get<-1>(k), cadd(E, tO));
+      const float2 u2 = cmul(tw.get<-1>(k + L), csub(E, tO));
+      if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
+      else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
+    }
+    if (kind == MID_MASK) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (!((bits >> i) & 1u)) X[i] = 0.f;
+    } else {
+      int f[4];
+      const int nf = pair_outputs(g, k, self, f);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i < nf) {
+          const bool in = (bits >> i) & 1u;
+          const int rk = in ? orank[f[i] >> 5] + __popc(omask[f[i] >> 5] & ((1u << (f[i] & 31)) - 1u)) : 0;
+          if (kind == MID_RESID) {
+            X[i] = in ? vin[rk] - X[i] : 0.f;
+            acc = fmaf(X[i], X[i], acc);
+          } else if (kind == MID_OUT) {
+            if (in) vout[rk] = X[i];
+          } else {   // MID_IN
+            X[i] = in ? vin[rk] : 0.f;
+          }
+        }
+      }
+    }
+    if (inv) {
+      float X4[4];
+      if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
+      else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
+      else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
+      // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
+      const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
+      const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
+      const float2 V1 = cmul(tw.get<1>(k), u1);
+      const float2 V2 = cmul(tw.get<1>(k + L), u2);
+      const float2 E = cscale(cadd(V1, V2), 0.5f);
+      const float2 O = cmul(cscale(csub(V1, V2), 0.5f), tw.get<1>(4 * k));
+      B[kpa * S2 + sa] = cadd(E, cmuli(O));
+      if (!self) B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
+    }
+  }
+  __syncthreads();
+  return acc;
+}
+
+// Inverse exchange: P-point inverse DFT per column, cluster barrier, all-to-all pull back into
+// the stride-P layout with conj(omega_L^{c k}).  The twiddle of element
+// k = k0 + e NT is conj(omega_L^{c k0}) * conj(omega_L^{c NT})^e: one strided lookup per
+// thread and broadcast powers.
+__device__ __noinline__ void exchange_inv(Ctx& x) {
+  const Geo g = x.g;
+  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
+  float2* A = shp(x.sm.A);
+  float2* B = shp(x.sm.B);
+  const int F = g.F, S2 = g.S2;
+  pstep<1>(B, g.P, S2);
+  x.cl.sync();                                      // every CTA's B is final
+  {
+    constexpr int EPT = F_MAX / NT;
+    float2 v[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int k = threadIdx.x + e * NT;
+      if (k < F) {
+        int cc, s;
+        owner_of_kq(g, k, cc, s);
+        v[e] = x.cl.map_shared_rank(B, cc)[g.c * S2 + s];
+      }
+    }
+    if (g.c == 0) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int k = threadIdx.x + e * NT;
+        if (k < F) A[aidx(k)] = v[e];
+      }
+    } else {
+      float2 w = tw.get<1>(8 * g.c * (int)threadIdx.x);
+      const float2 step = tw.get<1>(8 * g.c * NT);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int k = threadIdx.x + e * NT;
+        if (k < F) A[aidx(k)] = cmul(v[e], w);
+        w = cmul(w, step);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // One application of A (forward), A^T (inverse) or A^T mask A, driven by src / kind.
 //   src   SRC_NONE: the forward input is zero (skip the forward transform)
 //         SRC_CG: compressed CG vector cgp on the local list (nloc entries)
@@ -593,168 +815,22 @@ __device__ __noinline__ void build_fbits(Ctx& x) {
 // Returns this thread's sum of squares of the MID_RESID residual.
 __device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* dense, const float* gin, int kind,
                                         bool inv, const float* vin, float* vout) {
-  const Geo g = x.g;
-  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
-  float2* A = shp(x.sm.A);
-  float2* B = shp(x.sm.B);
-  const uint32_t* signw = shp(x.sm.signw);
-  const cg::cluster_group cl = x.cl;
-  const int F = g.F, P = g.P, S2 = g.S2;
+  // Each step is its own call and this function holds almost nothing live across them, so
+  // every step gets the full register budget (ptxas allocates registers across calls).
   x.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
-
   if (src != SRC_NONE) {
-    // ---- scatter (W x, sign flip d, Makhoul reordering are all in the slot map)
-    if (src == SRC_GLOBAL_N) {
-      for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(g, sg)] * sgn_bits(signw, sg);
-    } else {
-      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      float4* A4 = reinterpret_cast<float4*>(A);
-      for (int q = threadIdx.x; q < apad(F) / 2; q += NT) A4[q] = z4;
-      __syncthreads();
-      const int* list = x.list;
-      const float* vals = src == SRC_CG ? x.cgp : dense;
-      if (src == SRC_CG) {
-        for (int i = threadIdx.x; i < nloc; i += NT) {
-          const int sg = list[i];
-          slot_ref(A, sg) = vals[i] * sgn_bits(signw, sg);
-        }
-      } else {
-        for (int i = threadIdx.x; i < nloc; i += NT) {
-          const int sg = list[i];
-          slot_ref(A, sg) = vals[sg] * sgn_bits(signw, sg);
-        }
-      }
-    }
-    __syncthreads();
-    local_fft<-1>(A, F, tw, g.four_n);
-    cl.sync();                                      // every CTA's A is final
-    // ---- all-to-all pull: B[p][s] = A_p[k_q(s)] * omega_L^{p k_q}; all loads issued first
-    {
-      constexpr int EPT = F_MAX / NT;
-      const int lS2 = __ffs(S2) - 1;
-      float2 v[EPT];
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int idx = threadIdx.x + e * NT;
-        if (idx < F) {
-          const int p = idx >> lS2, s = idx & (S2 - 1);
-          v[e] = cl.map_shared_rank(A, p)[aidx(kq_of(g, s))];
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int idx = threadIdx.x + e * NT;
-        if (idx < F) {
-          const int p = idx >> lS2, s = idx & (S2 - 1);
-          B[idx] = cmul(v[e], tw.get<-1>(8 * p * kq_of(g, s)));
-        }
-      }
-    }
-    __syncthreads();
-    pstep<-1>(B, P, S2);
+    scatter_fwd(x, src, nloc, dense, gin);
+    local_fft<-1>(x.sm.A, x.g.F, x.tw, x.g.four_n);
+    exchange_fwd(x);
   } else {
-    cl.sync();                                      // nobody still reads this CTA's B
+    x.cl.sync();                                    // nobody still reads this CTA's B
   }
-
-  // ---- frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, DCT-III
-  // pre-processing back into the pair
-  float acc = 0.f;
-  {
-    const bool fwd_done = src != SRC_NONE;
-    const float wk = sqrtf(2.0f / (float)g.N), w0 = sqrtf(1.0f / (float)g.N);
-    const int nt = ntasks(g);
-    const uint8_t* fb = shp(x.sm.fbits);
-    const uint32_t* omask = x.omask;
-    const int32_t* orank = x.orank;
-    const int L = g.L;
-    for (int t = threadIdx.x; t < nt; t += NT) {
-      int sa, kpa, sb, kpb;
-      if (!task_pair(g, t, sa, kpa, sb, kpb)) continue;
-      const bool self = (sa == sb) && (kpa == kpb);
-      const int k = kq_of(g, sa) + F * kpa;
-      int f[4];
-      const int nf = pair_outputs(g, k, self, f);
-      const uint32_t bits = fb[t];
-      float X[4] = {0.f, 0.f, 0.f, 0.f};
-      int rk[4] = {0, 0, 0, 0};
-      if (kind != MID_MASK) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (i < nf && ((bits >> i) & 1u))
-            rk[i] = orank[f[i] >> 5] + __popc(omask[f[i] >> 5] & ((1u << (f[i] & 31)) - 1u));
-      }
-      if (fwd_done) {
-        const float2 Za = B[kpa * S2 + sa];
-        const float2 Zb = B[kpb * S2 + sb];
-        const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
-        const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
-        const float2 tO = cmul(tw.get<-1>(4 * k), O);
-        const float2 u1 = cmul(tw.get<-1>(k), cadd(E, tO));
-        const float2 u2 = cmul(tw.get<-1>(k + L), csub(E, tO));
-        if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
-        else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (i < nf) {
-          const bool in = (bits >> i) & 1u;
-          if (kind == MID_MASK) {
-            if (!in) X[i] = 0.f;
-          } else if (kind == MID_RESID) {
-            X[i] = in ? vin[rk[i]] - X[i] : 0.f;
-            acc = fmaf(X[i], X[i], acc);
-          } else if (kind == MID_OUT) {
-            if (in) vout[rk[i]] = X[i];
-          } else {   // MID_IN
-            X[i] = in ? vin[rk[i]] : 0.f;
-          }
-        }
-      }
-      if (inv) {
-        float X4[4];
-        if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
-        else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
-        else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
-        // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
-        const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
-        const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
-        const float2 V1 = cmul(tw.get<1>(k), u1);
-        const float2 V2 = cmul(tw.get<1>(k + L), u2);
-        const float2 E = cscale(cadd(V1, V2), 0.5f);
-        const float2 O = cmul(cscale(csub(V1, V2), 0.5f), tw.get<1>(4 * k));
-        B[kpa * S2 + sa] = cadd(E, cmuli(O));
-        if (!self) B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
-      }
-    }
-  }
-  __syncthreads();
-
+  const float acc = freq_half(x, kind, src != SRC_NONE, inv, vin, vout);
   if (inv) {
-    pstep<1>(B, P, S2);
-    cl.sync();                                      // every CTA's B is final
-    // ---- all-to-all pull back: A[k] = B_{owner(k)}[c][s(k)] * conj(omega_L^{c k})
-    {
-      constexpr int EPT = F_MAX / NT;
-      float2 v[EPT];
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int k = threadIdx.x + e * NT;
-        if (k < F) {
-          int cc, s;
-          owner_of_kq(g, k, cc, s);
-          v[e] = cl.map_shared_rank(B, cc)[g.c * S2 + s];
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int k = threadIdx.x + e * NT;
-        if (k < F) A[aidx(k)] = cmul(v[e], tw.get<1>(8 * g.c * k));
-      }
-    }
-    __syncthreads();
-    local_fft<1>(A, F, tw, g.four_n);
+    exchange_inv(x);
+    local_fft<1>(x.sm.A, x.g.F, x.tw, x.g.four_n);
   } else {
-    cl.sync();                                      // nobody still reads this CTA's A
+    x.cl.sync();                                    // nobody still reads this CTA's A
   }
   return acc;
 }
@@ -904,30 +980,43 @@ __device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r
   int it = 0;
   while (it < maxit && rr > stop2) {
     transform(x, SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
+    // pointers are re-read from the context after the call (nothing held live across it)
+    const float2* Ax = shp(x.sm.A);
+    const uint32_t* sw = shp(x.sm.signw);
+    const int* li = x.list;
+    float* px = x.cgx;
+    float* pr = x.cgr;
+    float* pp = x.cgp;
+    float* pq_ = x.cgq;
     float pq = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
-      const float q = corr_at(A, signw, list[i]);
-      cgq[i] = q;
-      pq = fmaf(cgp[i], q, pq);
+      const float q = corr_at(Ax, sw, li[i]);
+      pq_[i] = q;
+      pq = fmaf(pp[i], q, pq);
     }
     cluster_sum(x, &pq, 1);
     const float alpha = rr / pq;
     float rn = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
-      cgx[i] = fmaf(alpha, cgp[i], cgx[i]);
-      const float r = fmaf(-alpha, cgq[i], cgr[i]);
-      cgr[i] = r;
+      px[i] = fmaf(alpha, pp[i], px[i]);
+      const float r = fmaf(-alpha, pq_[i], pr[i]);
+      pr[i] = r;
       rn = fmaf(r, r, rn);
     }
     cluster_sum(x, &rn, 1);
     const float beta = rn / rr;
     rr = rn;
-    for (int i = threadIdx.x; i < nloc; i += NT) cgp[i] = fmaf(beta, cgp[i], cgr[i]);
+    for (int i = threadIdx.x; i < nloc; i += NT) pp[i] = fmaf(beta, pp[i], pr[i]);
     ++it;
   }
   x.cg_total += it;
   if (it >= maxit && rr > stop2) x.cg_hits += 1;
-  for (int i = threadIdx.x; i < nloc; i += NT) xd[list[i]] = cgx[i];
+  {
+    const int* li = x.list;
+    const float* px = x.cgx;
+    float* xo = x.xd[wi];
+    for (int i = threadIdx.x; i < nloc; i += NT) xo[li[i]] = px[i];
+  }
   __syncthreads();
 }
 
@@ -1053,150 +1142,171 @@ __device__ __noinline__ void topk_corr(Ctx& x, int K, const uint32_t* excl, uint
       [&](int sg) { atomicOr(&dst[sg >> 5], 1u << (sg & 31)); });
 }
 
+// OMP argmax step: t = argmax_{j not in S} |c_j| (lowest index on ties); returns the winner's
+// signal index or -1 when no candidate is left.  Adds it to the support mask (owner CTA) and
+// zeroes its slot of the warm-start vector.
+__device__ __noinline__ int omp_select(Ctx& x, uint32_t* mA) {
+  const Geo g = x.g;
+  const float2* A = shp(x.sm.A);
+  unsigned long long key = 0;
+  for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+    if (mask_bit(mA, sg)) continue;
+    const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(const_cast<float2*>(A), sg)) << 32) |
+                                  (0xffffffffu - (uint32_t)n_of_slot(g, sg));
+    key = kk > key ? kk : key;
+  }
+  cluster_max64(x, &key, 1);
+  if (key == 0ull) return -1;   // no candidate left (uniform: key is cluster-reduced)
+  const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
+  int owner, sg;
+  slot_of_n(x.g, n, owner, sg);
+  if (owner == x.g.c && threadIdx.x == 0) {
+    mA[sg >> 5] |= 1u << (sg & 31);
+    x.xd[0][sg] = 0.f;
+  }
+  __syncthreads();
+  return n;
+}
+
 __device__ __noinline__ void run_omp(Ctx& x, const Task& t) {
-  const float* y = t.in;
-  init_correlation(x, y);
-  uint32_t* mA = shp(x.sm.mask[0]);
-  zero_mask(x, mA);
+  init_correlation(x, t.in);
+  zero_mask(x, shp(x.sm.mask[0]));
   int nloc = 0;
   float rn2 = 0.f;
-  const Geo g = x.g;
-  float2* A = shp(x.sm.A);
   for (int it = 0; it < t.K; ++it) {
-    unsigned long long key = 0;
-    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
-      if (mask_bit(mA, sg)) continue;
-      const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(A, sg)) << 32) |
-                                    (0xffffffffu - (uint32_t)n_of_slot(g, sg));
-      key = kk > key ? kk : key;
-    }
-    cluster_max64(x, &key, 1);
-    if (key == 0ull) break;   // no candidate left (uniform: key is cluster-reduced)
-    const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
-    int owner, sg;
-    slot_of_n(g, n, owner, sg);
-    if (owner == g.c && threadIdx.x == 0) {
-      mA[sg >> 5] |= 1u << (sg & 31);
-      x.xd[0][sg] = 0.f;
-    }
-    __syncthreads();
-    nloc = build_list(x, mA);
+    if (omp_select(x, shp(x.sm.mask[0])) < 0) break;
+    nloc = build_list(x, shp(x.sm.mask[0]));
     cg_solve(x, 0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    rn2 = resid_corr(x, 0, nloc, y);
+    rn2 = resid_corr(x, 0, nloc, t.in);
   }
   write_recovery(x, t, 0, nloc, rn2, t.K);
 }
 
-__device__ __noinline__ void run_sp(Ctx& x, const Task& t) {
-  const float* y = t.in;
-  init_correlation(x, y);
-  int acc = 0;   // index of the accepted (support, solution) pair
-  uint32_t* mA = shp(x.sm.mask[acc]);
-  zero_mask(x, mA);
-  topk_corr(x, t.K, nullptr, mA);
-  int nloc = build_list(x, mA);
-  cg_solve(x, acc, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
-  float rn2 = resid_corr(x, acc, nloc, y);
-  int rounds = 0;
+// SP prune: S' = topK_{j in S~} |u_j| over the working list, marked into mW.
+__device__ __noinline__ void sp_prune(Ctx& x, int wi, int nW, int K, uint32_t* mW) {
+  zero_mask(x, mW);
   const Geo g = x.g;
+  const int* list = x.list;
+  const float* xw = x.xd[wi];
+  select_topk(
+      x, nW, K, [&](int i) -> uint32_t { return abs_key(xw[list[i]]); },
+      [&](int i) { return n_of_slot(g, list[i]); },
+      [&](int i) { const int sg = list[i]; atomicOr(&mW[sg >> 5], 1u << (sg & 31)); });
+}
+
+// SP merge: S~ = S u topK_{not in S} |A^T r| into mW, its list, and the warm start x0 = s on S,
+// 0 on the new entries.  Returns the list length.
+__device__ __noinline__ int sp_merge(Ctx& x, int acc, int K) {
+  const int wi = acc ^ 1;
+  uint32_t* mW = shp(x.sm.mask[wi]);
+  const uint32_t* mA = shp(x.sm.mask[acc]);
+  for (int w = threadIdx.x; w < x.nwords; w += NT) mW[w] = mA[w];
+  __syncthreads();
+  topk_corr(x, K, mA, mW);
+  const int nW = build_list(x, mW);
+  const int* list = x.list;
+  float* xw = x.xd[wi];
+  const float* xa = x.xd[acc];
+  for (int i = threadIdx.x; i < nW; i += NT) {
+    const int sg = list[i];
+    xw[sg] = mask_bit(mA, sg) ? xa[sg] : 0.f;
+  }
+  __syncthreads();
+  return nW;
+}
+
+__device__ __noinline__ float mask_diff(Ctx& x, int a, int b) {
+  const uint32_t* ma = shp(x.sm.mask[a]);
+  const uint32_t* mb = shp(x.sm.mask[b]);
+  float diff = 0.f;
+  for (int w = threadIdx.x; w < x.nwords; w += NT) diff += (float)__popc(ma[w] ^ mb[w]);
+  cluster_sum(x, &diff, 1);
+  return diff;
+}
+
+__device__ __noinline__ void run_sp(Ctx& x, const Task& t) {
+  init_correlation(x, t.in);
+  int acc = 0;   // index of the accepted (support, solution) pair
+  zero_mask(x, shp(x.sm.mask[0]));
+  topk_corr(x, t.K, nullptr, shp(x.sm.mask[0]));
+  int nloc = build_list(x, shp(x.sm.mask[0]));
+  cg_solve(x, acc, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  float rn2 = resid_corr(x, acc, nloc, t.in);
+  int rounds = 0;
   while (rounds < t.outer_max) {
     ++rounds;
     const int wi = acc ^ 1;
-    uint32_t* mW = shp(x.sm.mask[wi]);
-    mA = shp(x.sm.mask[acc]);
-    // S~ = S u topK_{not in S} |A^T r|
-    for (int w = threadIdx.x; w < x.nwords; w += NT) mW[w] = mA[w];
-    __syncthreads();
-    topk_corr(x, t.K, mA, mW);
-    int nW = build_list(x, mW);
-    // warm start: x0 = s on S, 0 on the new entries; r0 = c on S~
-    {
-      const int* list = x.list;
-      float* xw = x.xd[wi];
-      const float* xa = x.xd[acc];
-      for (int i = threadIdx.x; i < nW; i += NT) {
-        const int sg = list[i];
-        xw[sg] = mask_bit(mA, sg) ? xa[sg] : 0.f;
-      }
-    }
-    __syncthreads();
+    int nW = sp_merge(x, acc, t.K);                     // S~ and its warm start; r0 = c on S~
     cg_solve(x, wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    // S' = topK_{j in S~} |u_j|
-    zero_mask(x, mW);
-    {
-      const int* list = x.list;
-      const float* xw = x.xd[wi];
-      select_topk(
-          x, nW, t.K, [&](int i) -> uint32_t { return abs_key(xw[list[i]]); },
-          [&](int i) { return n_of_slot(g, list[i]); },
-          [&](int i) { const int sg = list[i]; atomicOr(&mW[sg >> 5], 1u << (sg & 31)); });
-    }
-    nW = build_list(x, mW);
-    // r0 for the warm start on S' (x0 = u restricted to S')
-    resid_corr(x, wi, nW, y);
+    sp_prune(x, wi, nW, t.K, shp(x.sm.mask[wi]));       // S'
+    nW = build_list(x, shp(x.sm.mask[wi]));
+    resid_corr(x, wi, nW, t.in);                        // r0 for x0 = u restricted to S'
     cg_solve(x, wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    const float rn2_new = resid_corr(x, wi, nW, y);
-    float diff = 0.f;
-    for (int w = threadIdx.x; w < x.nwords; w += NT) diff += (float)__popc(mW[w] ^ mA[w]);
-    cluster_sum(x, &diff, 1);
+    const float rn2_new = resid_corr(x, wi, nW, t.in);
+    const float diff = mask_diff(x, wi, acc);
     if (diff == 0.f || rn2_new >= rn2) break;
     acc = wi;
     rn2 = rn2_new;
-    nloc = nW;
   }
   // the returned pair is `acc`; rebuild its list (the working list may differ)
   nloc = build_list(x, shp(x.sm.mask[acc]));
   write_recovery(x, t, acc, nloc, rn2, rounds);
 }
 
-__device__ __noinline__ void run_ompr(Ctx& x, const Task& t) {
-  const float* y = t.in;
-  init_correlation(x, y);
-  uint32_t* mA = shp(x.sm.mask[0]);
-  zero_mask(x, mA);
-  topk_corr(x, t.K, nullptr, mA);
-  int nloc = build_list(x, mA);
-  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
-  float rn2 = resid_corr(x, 0, nloc, y);
-  int swaps = 0;
+// OMPR replacement step: z = s + A^T r, j = argmax_{not in S} |z|, i = argmin_{in S} |z|
+// (lowest index on ties).  If |z_j| > |z_i| swaps them in the support (owner CTAs), zeroes both
+// slots of the warm-start vector and returns true; otherwise returns false.
+__device__ __noinline__ bool ompr_swap(Ctx& x) {
   const Geo g = x.g;
   const float2* A = shp(x.sm.A);
   const uint32_t* signw = shp(x.sm.signw);
+  uint32_t* mA = shp(x.sm.mask[0]);
+  unsigned long long key[2] = {0ull, 0ull};
+  const float* xd = x.xd[0];
+  for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+    const uint32_t lo = 0xffffffffu - (uint32_t)n_of_slot(g, sg);
+    if (mask_bit(mA, sg)) {
+      const float z = xd[sg] + corr_at(A, signw, sg);
+      const unsigned long long kk =
+          ((unsigned long long)(0xffffffffu - (__float_as_uint(z) & 0x7fffffffu)) << 32) | lo;
+      key[1] = kk > key[1] ? kk : key[1];
+    } else {
+      const unsigned long long kk = ((unsigned long long)abs_key(corr_at(A, signw, sg)) << 32) | lo;
+      key[0] = kk > key[0] ? kk : key[0];
+    }
+  }
+  cluster_max64(x, key, 2);
+  const uint32_t zj = (uint32_t)(key[0] >> 32) - 1u;                  // |z_j| bits
+  const uint32_t zi = 0xffffffffu - (uint32_t)(key[1] >> 32);         // |z_i| bits
+  if (key[0] == 0ull || key[1] == 0ull || zj <= zi) return false;     // no improving swap
+  const int nj = (int)(0xffffffffu - (uint32_t)(key[0] & 0xffffffffu));
+  const int ni = (int)(0xffffffffu - (uint32_t)(key[1] & 0xffffffffu));
+  int oj, sj, oi, si;
+  slot_of_n(g, nj, oj, sj);
+  slot_of_n(g, ni, oi, si);
+  if (threadIdx.x == 0) {
+    if (oi == g.c) { mA[si >> 5] &= ~(1u << (si & 31)); x.xd[0][si] = 0.f; }
+    if (oj == g.c) { mA[sj >> 5] |= 1u << (sj & 31); x.xd[0][sj] = 0.f; }
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ __noinline__ void run_ompr(Ctx& x, const Task& t) {
+  init_correlation(x, t.in);
+  zero_mask(x, shp(x.sm.mask[0]));
+  topk_corr(x, t.K, nullptr, shp(x.sm.mask[0]));
+  int nloc = build_list(x, shp(x.sm.mask[0]));
+  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  float rn2 = resid_corr(x, 0, nloc, t.in);
+  int swaps = 0;
   while (swaps < t.outer_max) {
-    // z = s + A^T r: j = argmax_{not in S} |z|, i = argmin_{in S} |z| (lowest index on ties)
-    unsigned long long key[2] = {0ull, 0ull};
-    const float* xd = x.xd[0];
-    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
-      const uint32_t lo = 0xffffffffu - (uint32_t)n_of_slot(g, sg);
-      if (mask_bit(mA, sg)) {
-        const float z = xd[sg] + corr_at(A, signw, sg);
-        const unsigned long long kk =
-            ((unsigned long long)(0xffffffffu - (__float_as_uint(z) & 0x7fffffffu)) << 32) | lo;
-        key[1] = kk > key[1] ? kk : key[1];
-      } else {
-        const unsigned long long kk = ((unsigned long long)abs_key(corr_at(A, signw, sg)) << 32) | lo;
-        key[0] = kk > key[0] ? kk : key[0];
-      }
-    }
-    cluster_max64(x, key, 2);
-    const uint32_t zj = (uint32_t)(key[0] >> 32) - 1u;                  // |z_j| bits
-    const uint32_t zi = 0xffffffffu - (uint32_t)(key[1] >> 32);         // |z_i| bits
-    if (key[0] == 0ull || key[1] == 0ull || zj <= zi) break;            // no improving swap
-    const int nj = (int)(0xffffffffu - (uint32_t)(key[0] & 0xffffffffu));
-    const int ni = (int)(0xffffffffu - (uint32_t)(key[1] & 0xffffffffu));
-    int oj, sj, oi, si;
-    slot_of_n(g, nj, oj, sj);
-    slot_of_n(g, ni, oi, si);
-    if (threadIdx.x == 0) {
-      if (oi == g.c) { mA[si >> 5] &= ~(1u << (si & 31)); x.xd[0][si] = 0.f; }
-      if (oj == g.c) { mA[sj >> 5] |= 1u << (sj & 31); x.xd[0][sj] = 0.f; }
-    }
-    __syncthreads();
+    if (!ompr_swap(x)) break;
     ++swaps;
-    nloc = build_list(x, mA);
-    resid_corr(x, 0, nloc, y);   // r0 for x0 = s without i, 0 at j
+    nloc = build_list(x, shp(x.sm.mask[0]));
+    resid_corr(x, 0, nloc, t.in);   // r0 for x0 = s without i, 0 at j
     cg_solve(x, 0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    rn2 = resid_corr(x, 0, nloc, y);
+    rn2 = resid_corr(x, 0, nloc, t.in);
   }
   write_recovery(x, t, 0, nloc, rn2, swaps);
 }
@@ -1258,6 +1368,74 @@ __device__ __noinline__ void run_ls_backward(Ctx& x, const Task& t) {
   }
 }
 
+// Per-task set-up (geometry, twiddle tables, sign bits, Omega bits) and dispatch.  The task is
+// read through a pointer so no copy of it stays in registers across the calls below (ptxas
+// allocates registers across calls: whatever a caller holds live is denied to its callees).
+__device__ __noinline__ void run_task(Ctx& x, const Task* tp, int P, int c, int F_alloc) {
+  const OpDev& op = tp->op;
+  if (op.P != P || op.F > F_alloc) {   // host grouping error: skip uniformly
+    if (c == 0 && threadIdx.x == 0 && tp->stats) tp->stats->status = CS_ERR_INVALID_ARG;
+    return;
+  }
+  {
+    Geo& g = x.g;
+    g.N = op.N; g.L = op.N >> 1; g.P = P; g.F = op.F; g.c = c;
+    g.h = op.F / (2 * P); g.lh = __ffs(g.h) - 1; g.S2 = 2 * g.h; g.four_n = 4 * op.N;
+    x.M = op.M;
+    x.nwords = (2 * op.F + 31) / 32;
+    x.omask = op.omask; x.orank = op.orank;
+    x.cg_total = 0; x.cg_hits = 0; x.ntrans = 0;
+    const size_t a = 2 * (size_t)F_alloc;
+    x.list = x.glist;
+    x.cgx = x.gcg; x.cgr = x.gcg + a; x.cgp = x.gcg + 2 * a; x.cgq = x.gcg + 3 * a;
+    // twiddle tables and sign bits
+    const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
+    float2* twlo = shp(x.sm.twlo);
+    float2* twhi = shp(x.sm.twhi);
+    for (int i = threadIdx.x; i < nlo; i += NT) twlo[aidx(i)] = op.tw[i];
+    for (int i = threadIdx.x; i < nhi; i += NT) twhi[i] = op.tw[nlo + i];
+    x.tw.lo = x.sm.twlo; x.tw.hi = x.sm.twhi; x.tw.lo_bits = op.lo_bits; x.tw.lo_mask = nlo - 1;
+    x.tw.mask4n = g.four_n - 1;
+    uint32_t* signw = shp(x.sm.signw);
+    const Geo gg = g;
+    for (int w = threadIdx.x; w < x.nwords; w += NT) {
+      uint32_t bitsw = 0u;
+      for (int b = 0; b < 32; ++b) {
+        const int sg = 32 * w + b;
+        if (sg < 2 * op.F) {
+          const uint64_t hsh = mix64(op.sign_key + (uint64_t)n_of_slot(gg, sg) + 0x9E3779B97F4A7C15ull);
+          bitsw |= (uint32_t)(hsh >> 63) << b;
+        }
+      }
+      signw[w] = bitsw;
+    }
+  }
+  __syncthreads();
+  build_fbits(x);
+  const Task& t = *tp;
+  switch (t.mode) {
+    case MODE_APPLY:
+      transform(x, SRC_GLOBAL_N, 0, nullptr, t.in, MID_OUT, false, nullptr, t.out);
+      break;
+    case MODE_APPLY_T: {
+      transform(x, SRC_NONE, 0, nullptr, nullptr, MID_IN, true, t.in, nullptr);
+      const float2* A = shp(x.sm.A);
+      const uint32_t* signw = shp(x.sm.signw);
+      const Geo gg = x.g;
+      for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[n_of_slot(gg, sg)] = corr_at(A, signw, sg);
+      break;
+    }
+    case MODE_RECOVER:
+      if (t.algo == CS_OMP) run_omp(x, t);
+      else if (t.algo == CS_SP) run_sp(x, t);
+      else run_ompr(x, t);
+      break;
+    case MODE_LS_SOLVE: run_ls_solve(x, t); break;
+    case MODE_LS_BACKWARD: run_ls_backward(x, t); break;
+    default: break;
+  }
+}
+
 __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   cg::cluster_group cl = cg::this_cluster();
   const int P = (int)cl.num_blocks();
@@ -1276,69 +1454,8 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   x.glist = reinterpret_cast<int*>(base + 3 * a);
   x.gcg = base + 4 * a;
   x.bits = lp.bits + (size_t)cid * lp.bits_per_cluster;
-
   for (int ti = cid; ti < lp.ntasks; ti += ncl) {
-    const Task t = lp.tasks ? lp.tasks[ti] : lp.single;
-    const OpDev& op = t.op;
-    if (op.P != P || op.F > lp.F_alloc) {   // host grouping error: skip uniformly
-      if (c == 0 && threadIdx.x == 0 && t.stats) t.stats->status = CS_ERR_INVALID_ARG;
-      continue;
-    }
-    Geo& g = x.g;
-    g.N = op.N; g.L = op.N >> 1; g.P = P; g.F = op.F; g.c = c;
-    g.h = op.F / (2 * P); g.lh = __ffs(g.h) - 1; g.S2 = 2 * g.h; g.four_n = 4 * op.N;
-    x.M = op.M;
-    x.nwords = (2 * op.F + 31) / 32;
-    x.omask = op.omask; x.orank = op.orank;
-    x.cg_total = 0; x.cg_hits = 0; x.ntrans = 0;
-    x.list = x.glist;
-    x.cgx = x.gcg; x.cgr = x.gcg + a; x.cgp = x.gcg + 2 * a; x.cgq = x.gcg + 3 * a;
-    // twiddle tables and sign bits
-    const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
-    float2* twlo = shp(x.sm.twlo);
-    float2* twhi = shp(x.sm.twhi);
-    for (int i = threadIdx.x; i < nlo; i += NT) twlo[i] = op.tw[i];
-    for (int i = threadIdx.x; i < nhi; i += NT) twhi[i] = op.tw[nlo + i];
-    x.tw.lo = x.sm.twlo; x.tw.hi = x.sm.twhi; x.tw.lo_bits = op.lo_bits; x.tw.lo_mask = nlo - 1;
-    x.tw.mask4n = g.four_n - 1;
-    {
-      uint32_t* signw = shp(x.sm.signw);
-      const Geo gg = g;
-      for (int w = threadIdx.x; w < x.nwords; w += NT) {
-        uint32_t bitsw = 0u;
-        for (int b = 0; b < 32; ++b) {
-          const int sg = 32 * w + b;
-          if (sg < 2 * op.F) {
-            const uint64_t hsh = mix64(op.sign_key + (uint64_t)n_of_slot(gg, sg) + 0x9E3779B97F4A7C15ull);
-            bitsw |= (uint32_t)(hsh >> 63) << b;
-          }
-        }
-        signw[w] = bitsw;
-      }
-    }
-    __syncthreads();
-    build_fbits(x);
-    switch (t.mode) {
-      case MODE_APPLY:
-        transform(x, SRC_GLOBAL_N, 0, nullptr, t.in, MID_OUT, false, nullptr, t.out);
-        break;
-      case MODE_APPLY_T: {
-        transform(x, SRC_NONE, 0, nullptr, nullptr, MID_IN, true, t.in, nullptr);
-        const float2* A = shp(x.sm.A);
-        const uint32_t* signw = shp(x.sm.signw);
-        const Geo gg = g;
-        for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[n_of_slot(gg, sg)] = corr_at(A, signw, sg);
-        break;
-      }
-      case MODE_RECOVER:
-        if (t.algo == CS_OMP) run_omp(x, t);
-        else if (t.algo == CS_SP) run_sp(x, t);
-        else run_ompr(x, t);
-        break;
-      case MODE_LS_SOLVE: run_ls_solve(x, t); break;
-      case MODE_LS_BACKWARD: run_ls_backward(x, t); break;
-      default: break;
-    }
+    run_task(x, lp.tasks ? lp.tasks + ti : &lp.single, P, c, lp.F_alloc);
     cl.sync();
   }
 }
