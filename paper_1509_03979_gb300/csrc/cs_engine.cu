@@ -167,11 +167,34 @@ __device__ __forceinline__ void twiddle_powers(float2* v, const Tw& tw, int t) {
   }
 }
 
-// One in-place Stockham pass of radix R over the F-point buffer X (padded indexing).
-// All R-point groups are loaded into registers before any store (F <= 16 * NT).
+// One out-of-place Stockham pass of radix R from X to Y (padded indexing): butterfly j reads
+// X[j + r F/R], applies omega_{Ns R}^{r k} (k = j mod Ns), and writes Y[(j - k) R + k + r Ns].
+// One barrier per pass; a thread keeps one butterfly live at a time.
 template <int R, int DIR>
-__device__ __forceinline__ void fft_pass(float2* X, int F, int Ns, const Tw& tw, int four_n) {
-  constexpr int BPT = 16 / R;
+__device__ __forceinline__ void fft_pass(const float2* X, float2* Y, int F, int Ns, const Tw& tw, int four_n) {
+  const int nb = F / R;
+  for (int j = threadIdx.x; j < nb; j += NT) {
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = X[aidx(j + r * nb)];
+    const int k = j & (Ns - 1);
+    if (Ns > 1) twiddle_powers<R, DIR>(v, tw, k * (four_n / (Ns * R)));
+    dft<R, DIR>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) Y[aidx(base + r * Ns)] = v[r];
+  }
+  __syncthreads();
+}
+
+// Q-point FFT of X (natural order in and out) using Y as the ping-pong buffer.  The plan is
+// fixed at compile time for each F = 2^LOGF (a runtime pass loop measured worse register
+// allocation): a radix-2/4/8 pass first when log2 F is not a multiple of 4, then radix 16,
+// and when the pass count is odd the first pass runs in place through registers so that the
+// result always lands back in X.
+template <int R, int DIR>
+__device__ __forceinline__ void fft_pass_inplace(float2* X, int F, const Tw& tw, int four_n) {
+  constexpr int BPT = (F_MAX / NT) / R;
   const int nb = F / R;
   float2 v[BPT][R];
 #pragma unroll
@@ -187,54 +210,59 @@ __device__ __forceinline__ void fft_pass(float2* X, int F, int Ns, const Tw& tw,
   for (int b = 0; b < BPT; ++b) {
     const int j = threadIdx.x + b * NT;
     if (j < nb) {
-      const int k = j & (Ns - 1);
-      if (Ns > 1) twiddle_powers<R, DIR>(v[b], tw, k * (four_n / (Ns * R)));
-      dft<R, DIR>(v[b]);
-      const int base = (j - k) * R + k;
+      dft<R, DIR>(v[b]);   // first pass: Ns = 1, no twiddles, output index j R + r
 #pragma unroll
-      for (int r = 0; r < R; ++r) X[aidx(base + r * Ns)] = v[b][r];
+      for (int r = 0; r < R; ++r) X[aidx(j * R + r)] = v[b][r];
     }
   }
   __syncthreads();
 }
 
-// Q-point FFT of the local buffer, natural order in and out.  The pass plan (radix 16 while
-// at least 16 points remain per group, then 8/4/2) is fixed at compile time for each
-// F = 2^LOGF: a runtime pass loop measured worse register allocation (spills).
-template <int LOGF, int DIR, int LOGNS = 0>
-__device__ __forceinline__ void fft_plan(float2* X, const Tw& tw, int four_n) {
-  constexpr int REM = LOGF - LOGNS;
-  if constexpr (REM >= 4) {
-    fft_pass<16, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
-    fft_plan<LOGF, DIR, LOGNS + 4>(X, tw, four_n);
-  } else if constexpr (REM == 3) {
-    fft_pass<8, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
-  } else if constexpr (REM == 2) {
-    fft_pass<4, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
-  } else if constexpr (REM == 1) {
-    fft_pass<2, DIR>(X, 1 << LOGF, 1 << LOGNS, tw, four_n);
+template <int LOGF, int DIR, int LOGNS, bool TO_Y>
+__device__ __forceinline__ void fft_rest(float2* X, float2* Y, const Tw& tw, int four_n) {
+  // remaining passes are all radix 16; TO_Y: the next pass writes Y
+  if constexpr (LOGNS < LOGF) {
+    if constexpr (TO_Y) fft_pass<16, DIR>(X, Y, 1 << LOGF, 1 << LOGNS, tw, four_n);
+    else fft_pass<16, DIR>(Y, X, 1 << LOGF, 1 << LOGNS, tw, four_n);
+    fft_rest<LOGF, DIR, LOGNS + 4, !TO_Y>(X, Y, tw, four_n);
+  }
+}
+
+template <int LOGF, int DIR>
+__device__ __forceinline__ void fft_plan(float2* X, float2* Y, const Tw& tw, int four_n) {
+  constexpr int HEAD = LOGF % 4;                       // bits of the leading small-radix pass
+  constexpr int NPASS = LOGF / 4 + (HEAD ? 1 : 0);
+  constexpr int R0 = HEAD == 0 ? 16 : (1 << HEAD);
+  if constexpr (NPASS % 2 == 1) {
+    // odd pass count: first pass in place (registers), then an even number of ping-pongs
+    fft_pass_inplace<R0, DIR>(X, 1 << LOGF, tw, four_n);
+    fft_rest<LOGF, DIR, (HEAD ? HEAD : 4), true>(X, Y, tw, four_n);
+  } else {
+    fft_pass<R0, DIR>(X, Y, 1 << LOGF, 1, tw, four_n);
+    fft_rest<LOGF, DIR, (HEAD ? HEAD : 4), false>(X, Y, tw, four_n);
   }
 }
 
 template <int DIR>
-__device__ __noinline__ void local_fft(float2* X, int F, Tw tw, int four_n) {
+__device__ __noinline__ void local_fft(float2* X, float2* Y, int F, Tw tw, int four_n) {
   X = shp(X);
+  Y = shp(Y);
   tw.lo = shp(tw.lo);
   tw.hi = shp(tw.hi);
   switch (__ffs(F) - 1) {
-    case 1: fft_plan<1, DIR>(X, tw, four_n); break;
-    case 2: fft_plan<2, DIR>(X, tw, four_n); break;
-    case 3: fft_plan<3, DIR>(X, tw, four_n); break;
-    case 4: fft_plan<4, DIR>(X, tw, four_n); break;
-    case 5: fft_plan<5, DIR>(X, tw, four_n); break;
-    case 6: fft_plan<6, DIR>(X, tw, four_n); break;
-    case 7: fft_plan<7, DIR>(X, tw, four_n); break;
-    case 8: fft_plan<8, DIR>(X, tw, four_n); break;
-    case 9: fft_plan<9, DIR>(X, tw, four_n); break;
-    case 10: fft_plan<10, DIR>(X, tw, four_n); break;
-    case 11: fft_plan<11, DIR>(X, tw, four_n); break;
-    case 12: fft_plan<12, DIR>(X, tw, four_n); break;
-    default: fft_plan<13, DIR>(X, tw, four_n); break;
+    case 1: fft_plan<1, DIR>(X, Y, tw, four_n); break;
+    case 2: fft_plan<2, DIR>(X, Y, tw, four_n); break;
+    case 3: fft_plan<3, DIR>(X, Y, tw, four_n); break;
+    case 4: fft_plan<4, DIR>(X, Y, tw, four_n); break;
+    case 5: fft_plan<5, DIR>(X, Y, tw, four_n); break;
+    case 6: fft_plan<6, DIR>(X, Y, tw, four_n); break;
+    case 7: fft_plan<7, DIR>(X, Y, tw, four_n); break;
+    case 8: fft_plan<8, DIR>(X, Y, tw, four_n); break;
+    case 9: fft_plan<9, DIR>(X, Y, tw, four_n); break;
+    case 10: fft_plan<10, DIR>(X, Y, tw, four_n); break;
+    case 11: fft_plan<11, DIR>(X, Y, tw, four_n); break;
+    case 12: fft_plan<12, DIR>(X, Y, tw, four_n); break;
+    default: fft_plan<13, DIR>(X, Y, tw, four_n); break;
   }
 }
 
@@ -286,7 +314,7 @@ __host__ __device__ inline int cg_cap(int F_alloc) { return 2 * F_alloc < CG_CAP
 
 struct Smem {
   float2* A;          // local FFT buffer (padded), signal-domain slots between transforms
-  float2* B;          // exchange / frequency buffer [P][2h]
+  float2* B;          // exchange / frequency buffer [P][2h]; FFT ping-pong buffer (padded)
   float2* twlo;
   float2* twhi;
   uint32_t* signw;    // d_n bits per local slot (1 = -1)
@@ -319,13 +347,13 @@ __host__ __device__ inline void layout(int F_alloc, Bump& take, Smem* s) {
   const int nw = (2 * F_alloc + 31) / 32;
   const int cap = cg_cap(F_alloc);
   unsigned char* A = take(sizeof(float2) * apad(F_alloc));
-  unsigned char* B = take(sizeof(float2) * F_alloc);
+  unsigned char* B = take(sizeof(float2) * apad(F_alloc));   // also the FFT ping-pong buffer (padded)
   unsigned char* tl = take(sizeof(float2) * apad(1024));
   unsigned char* th = take(sizeof(float2) * 1024);
   unsigned char* sw = take(4 * nw);
   unsigned char* m0 = take(4 * nw);
   unsigned char* m1 = take(4 * nw);
-  unsigned char* fb = take(F_alloc / 2 + 16);
+  unsigned char* fb = take(F_alloc / 2 + P_MAX + 16);   // ntasks <= F/2 + P + 1
   unsigned char* hi = take(4 * 512);
   unsigned char* ht = take(4 * 256);
   unsigned char* rg = take(4 * 16);
@@ -695,7 +723,7 @@ __device__ __noinline__ float freq_half(Ctx& x, int kind, bool fwd_done, bool in
   const uint8_t* fb = shp(x.sm.fbits);
   const uint32_t* omask = x.omask;
   const int32_t* orank = x.orank;
-  const int F = g.F, S2 = g.S2, L = g.L;
+  const int F = g.F, S2 = g.S2;
   const float wk = sqrtf(2.0f / (float)g.N), w0 = sqrtf(1.0f / (float)g.N);
   const int nt = ntasks(g);
   float acc = 0.f;
@@ -705,15 +733,21 @@ __device__ __noinline__ float freq_half(Ctx& x, int kind, bool fwd_done, bool in
     const bool self = (sa == sb) && (kpa == kpb);
     const int k = kq_of(g, sa) + F * kpa;
     const uint32_t bits = fb[t];
+    // omega_{4N}^k from the table; omega_{4N}^{k+L} = omega_{4N}^k e^{-i pi/4};
+    // omega_{4N}^{4k} = (omega_{4N}^k)^4 (two squarings)
+    const float2 wk1 = tw.get<-1>(k);
+    const float2 wkL = cmul(wk1, make_float2(0.70710678118654752f, -0.70710678118654752f));
+    const float2 wk2 = cmul(wk1, wk1);
+    const float2 w4k = cmul(wk2, wk2);
     float X[4] = {0.f, 0.f, 0.f, 0.f};
     if (fwd_done) {
       const float2 Za = B[kpa * S2 + sa];
       const float2 Zb = B[kpb * S2 + sb];
       const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
       const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
-      const float2 tO = cmul(tw.get<-1>(4 * k), O);
-      const float2 u1 = cmul(tw.get<-1>(k), cadd(E, tO));
-      const float2 u2 = cmul(tw.get<-1>(k + L), csub(E, tO));
+      const float2 tO = cmul(w4k, O);
+      const float2 u1 = cmul(wk1, cadd(E, tO));
+      const float2 u2 = cmul(wkL, csub(E, tO));
       if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
       else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
     }
@@ -748,10 +782,10 @@ __device__ __noinline__ float freq_half(Ctx& x, int kind, bool fwd_done, bool in
       // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
       const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
       const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
-      const float2 V1 = cmul(tw.get<1>(k), u1);
-      const float2 V2 = cmul(tw.get<1>(k + L), u2);
+      const float2 V1 = cmul(cconj(wk1), u1);
+      const float2 V2 = cmul(cconj(wkL), u2);
       const float2 E = cscale(cadd(V1, V2), 0.5f);
-      const float2 O = cmul(cscale(csub(V1, V2), 0.5f), tw.get<1>(4 * k));
+      const float2 O = cmul(cscale(csub(V1, V2), 0.5f), cconj(w4k));
       B[kpa * S2 + sa] = cadd(E, cmuli(O));
       if (!self) B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
     }
@@ -818,9 +852,12 @@ __device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* 
   // Each step is its own call and this function holds almost nothing live across them, so
   // every step gets the full register budget (ptxas allocates registers across calls).
   x.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
+  // B is free at the start of every transform: each transform ends with (or is followed by)
+  // a cluster barrier after the last remote read of B, so the forward FFT may use B as its
+  // ping-pong buffer.
   if (src != SRC_NONE) {
     scatter_fwd(x, src, nloc, dense, gin);
-    local_fft<-1>(x.sm.A, x.g.F, x.tw, x.g.four_n);
+    local_fft<-1>(x.sm.A, x.sm.B, x.g.F, x.tw, x.g.four_n);
     exchange_fwd(x);
   } else {
     x.cl.sync();                                    // nobody still reads this CTA's B
@@ -828,7 +865,8 @@ __device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* 
   const float acc = freq_half(x, kind, src != SRC_NONE, inv, vin, vout);
   if (inv) {
     exchange_inv(x);
-    local_fft<1>(x.sm.A, x.g.F, x.tw, x.g.four_n);
+    x.cl.sync();                                    // every pull from B is done: B is scratch again
+    local_fft<1>(x.sm.A, x.sm.B, x.g.F, x.tw, x.g.four_n);
   } else {
     x.cl.sync();                                    // nobody still reads this CTA's A
   }
@@ -961,7 +999,6 @@ __device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r
   float* cgx = x.cgx;
   float* cgr = x.cgr;
   float* cgp = x.cgp;
-  float* cgq = x.cgq;
   float v[2] = {0.f, 0.f};
   for (int i = threadIdx.x; i < nloc; i += NT) {
     const int sg = list[i];
