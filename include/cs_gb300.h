@@ -112,6 +112,23 @@ cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_
 cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float cg_tol,
                      int32_t cg_maxit, float* s_out, int32_t* support_out);
 
+/* Same recovery as cs_recover, for callers that cannot allocate device memory when they
+ * recover (a host framework that owns every device allocation, a loop that forbids allocation
+ * after start-up, or a caller for whom cudaMalloc/cudaFree would synchronise the device).
+ * The paper has no counterpart: this is a deployment variant of the same computation.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the engine's per-call
+ * scratch lives in one file-scope device array of 2 MiB + 8 KiB that every GPU loading the
+ * library holds until the process exits.  Limit: N <= 65536 (larger N returns
+ * CS_ERR_INVALID_ARG); all other argument rules are those of cs_recover.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current and caches it: make that first call before any stream capture.
+ * Every call shares the one array and the engine rewrites every scratch word it reads, so
+ * nothing is cleared between calls; calls whose work overlaps on the GPU (other streams, or
+ * other host threads) race on the array and must be serialised by the caller.
+ * cs_get_stats does not report these calls. */
+cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, cs_algo algo, float cg_tol,
+                             int32_t cg_maxit, float* s_out, int32_t* support_out);
+
 /* Batched recovery of B independent signals in one persistent launch per cluster size.
  * ops[b], y[b], K[b], algo[b], s_out[b], support_out[b] describe signal b (HOST arrays of
  * handles/device pointers).  All ops must share one stream (taken from ops[0]).

@@ -42,6 +42,7 @@ SIGNATURES = {
     "cs_op_concurrency": (_I32, [_P]),
     "cs_operator_draws": (_I32, [_I64, _I64, _U64, _P, _P]),
     "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
+    "cs_recover_noalloc": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
     "cs_recover_batched": (_I32, [_I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P]),
     "cs_ls_solve": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
     "cs_ls_backward": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
@@ -171,6 +172,20 @@ class Operator:
         _check(lib().cs_recover(self._h, _dev(y, torch.float32, self.M, "y"), int(K), a, float(cg_tol),
                                 int(cg_maxit), _dev(s_out, torch.float32, self.N, "s_out"),
                                 _dev(support_out, torch.int32, None, "support_out")))
+        return s_out, support_out[:K]
+
+    def recover_noalloc(self, y, K, algo="omp", cg_tol=1e-6, cg_maxit=100, s_out=None, support_out=None):
+        """cs_recover_noalloc: the same recovery with scratch from the library's fixed device
+        array (no device allocation by the call; N <= 65536).  Outputs must be preallocated by
+        a caller that cannot allocate; they are allocated here only when not given."""
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        s_out = torch.empty(self.N, dtype=torch.float32, device=y.device) if s_out is None else s_out
+        support_out = (torch.empty(max(K, 1), dtype=torch.int32, device=y.device)
+                       if support_out is None else support_out)
+        self._stream()
+        _check(lib().cs_recover_noalloc(self._h, _dev(y, torch.float32, self.M, "y"), int(K), a, float(cg_tol),
+                                        int(cg_maxit), _dev(s_out, torch.float32, self.N, "s_out"),
+                                        _dev(support_out, torch.int32, None, "support_out")))
         return s_out, support_out[:K]
 
     def ls_solve(self, support, y, cg_tol=1e-6, cg_maxit=100, out=None):

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -483,3 +484,84 @@ cs_status cs_get_stats(cs_op_t op, cs_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Greedy recovery that allocates nothing (cs_recover_noalloc).
+//
+// Some callers cannot allocate device memory when they recover a signal: code running under a
+// host framework that owns every device allocation (a plugin may not call cudaMalloc), loops
+// that forbid allocation after start-up, or callers for whom a cudaMalloc/cudaFree would
+// synchronise the device at the wrong moment.  For them the per-call scratch of the cluster
+// engine (solution copies, A^T y by slot, support list, CG vectors, output bitmask) lives in one
+// file-scope device array of fixed size, created when the library is loaded and held by every
+// GPU that loads it until the process exits.
+namespace {
+
+constexpr int64_t NOALLOC_N_MAX = 1 << 16;                        // largest supported N
+constexpr size_t NOALLOC_SCRATCH = (size_t)(NOALLOC_N_MAX / 2 / F_MAX) * SCRATCH_ARRAYS * 2 * F_MAX;
+constexpr size_t NOALLOC_BITS = (size_t)NOALLOC_N_MAX / 32;
+// 2 MiB of scratch floats followed by the N-bit support bitmask (8 KiB)
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH + NOALLOC_BITS];
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[64] = {};                                    // per device ordinal
+
+// The array's host-side name is only a stand-in: its device address is looked up once per
+// device, with that device current, and cached.
+cs_status noalloc_scratch(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(CS_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    float* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CS_OK;
+}
+
+}  // namespace
+
+extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, cs_algo algo, float cg_tol,
+                                        int32_t cg_maxit, float* s_out, int32_t* support_out) {
+  cs_status st = check_recover(op, y, K, (int)algo, s_out, support_out);
+  if (st != CS_OK) return st;
+  if ((st = check_cg(cg_tol, cg_maxit)) != CS_OK) return st;
+  if (op->N > NOALLOC_N_MAX)
+    return fail(CS_ERR_INVALID_ARG, "cs_recover_noalloc supports N <= 65536 (fixed scratch size)");
+  if (K == 0) {
+    cudaError_t e = cudaMemsetAsync(s_out, 0, sizeof(float) * (size_t)op->N, op->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    return CS_OK;
+  }
+  float* base = nullptr;
+  if ((st = noalloc_scratch(&base)) != CS_OK) return st;
+  Task t = base_task(op, MODE_RECOVER);
+  t.algo = (int)algo;
+  t.K = K;
+  t.cg_tol = cg_tol;
+  t.cg_maxit = cg_maxit;
+  t.outer_max = algo == CS_SP ? SP_ROUNDS : OMPR_SWAPS;
+  t.in = y;
+  t.out = s_out;
+  t.supp_out = support_out;
+  t.stats = nullptr;   // the op's statistics buffer is left untouched
+  Launch L{};
+  L.tasks = nullptr;
+  L.single = t;
+  L.ntasks = 1;
+  L.F_alloc = op->dev.F;
+  L.scratch = base;
+  L.scratch_per_cluster = (size_t)op->dev.P * scratch_floats_per_cta(op->dev.F);
+  L.bits = reinterpret_cast<uint32_t*>(base + NOALLOC_SCRATCH);
+  L.bits_per_cluster = (size_t)(op->N + 31) / 32;
+  // every scratch word the engine reads is written earlier in the same launch, so nothing
+  // needs clearing between calls
+  const cudaError_t e = launch_engine(L, op->dev.P, 1, op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "engine launch");
+  return CS_OK;
+}
