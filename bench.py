@@ -9,6 +9,7 @@ signals the GPU runs at once, one per resident thread-block cluster).  Prints ON
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -22,7 +23,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1509_03979_gb300 import synth  # noqa: E402
+from paper_1509_03979_gb300 import shard, synth  # noqa: E402
 
 WORKLOAD = synth.workload(2)
 CG_TOL, CG_MAXIT = 1e-6, 100
@@ -39,6 +40,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="signals per GPU per step (0 = fill the GPU)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-batch", type=int, default=256)
+    ap.add_argument("--workload", default="sp18", choices=["sp18", "batched"],
+                    help="sp18: SP at N=2^18 (default); batched: mixed-size batch vs a loop of single calls")
+    ap.add_argument("--batched-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -108,6 +112,29 @@ def peaks():
     return 6800.0, "fallback"
 
 
+ENGINE_SRC = os.path.join(ROOT, "paper_1509_03979_gb300", "csrc", "cs_engine.cu")
+PROFILE = os.path.join(ROOT, "profiles", "engine_kernel_sp_n262144_batch7.md")
+
+
+def engine_traffic_per_launch():
+    """DRAM bytes (read + write) of one SP recovery launch, from the committed ncu summary,
+    scaled to the benchmark's batch; None when the engine source changed since the capture."""
+    if not os.path.exists(PROFILE):
+        return None, None
+    rec = {}
+    for line in open(PROFILE):
+        if line.startswith("traffic:"):
+            for kv in line[len("traffic:"):].split():
+                k, v = kv.split("=")
+                rec[k] = v
+    if not rec:
+        return None, None
+    sha = hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
+    if rec.get("engine_sha") != sha:
+        return None, rec.get("engine_sha")
+    return float(rec["dram_bytes"]), int(rec["batch"])
+
+
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args, rank):
     """The FP64 CPU oracle timed on the host cores: each timed step recovers one signal of the
@@ -156,7 +183,7 @@ def run_gb300(args, rank, world, local_rank):
     B = args.batch or op.concurrency()
 
     # ---- inputs (seeded, synthetic, resident in HBM before timing)
-    idx = [rank * B + b for b in range(B)]
+    idx = shard.rank_signals(rank, world, B)
     S = np.zeros((B, p.N), dtype=np.float32)
     noise = np.zeros((B, p.M), dtype=np.float32)
     for b, i in enumerate(idx):
@@ -215,11 +242,15 @@ def run_gb300(args, rank, world, local_rank):
         dist.barrier()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=devc)
+    def reduce_max(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], device=devc)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * B * args.steps / total_s
+        return float(t.item())
+
+    total_s = reduce_max(total_s)
+    value = shard.aggregate_throughput(total_s, world, B, args.steps)
     ms_per_step = 1e3 * total_s / args.steps
 
     # ---- roofline of the (only) kernel: one engine launch per step
@@ -227,8 +258,11 @@ def run_gb300(args, rank, world, local_rank):
     sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak_alu = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s
     achieved = transforms * flops_per_dct(p.N) / (ms_per_step / 1e3) / 1e12
+    traffic, tb = engine_traffic_per_launch()
+    if traffic is not None and tb:
+        traffic = traffic * B / tb
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                "frac": achieved / peak_alu, "traffic": None,
+                "frac": achieved / peak_alu, "traffic": traffic,
                 "kernel": "engine_kernel (SP recovery, one launch per step)",
                 "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
 
@@ -278,12 +312,8 @@ def run_gb300(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_s = sum(e2e_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device=devc)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * B * args.steps / e2e_s, "unit": "recoveries/s",
+    e2e_s = reduce_max(sum(e2e_ms) / 1e3)
+    e2e = {"value": shard.aggregate_throughput(e2e_s, world, B, args.steps), "unit": "recoveries/s",
            "h2d_bytes_per_step": B * p.M * 4, "d2h_bytes_per_step": B * (p.N + p.K) * 4}
 
     # ---- CPU baseline: the FP64 oracle on signal 0 (also a full-size parity check)
@@ -323,6 +353,66 @@ def run_gb300(args, rank, world, local_rank):
     op.close()
 
 
+# ------------------------------------------------------------ mixed-size batched workload
+def run_batched(args, rank, world, local_rank):
+    """One cs_recover_batched launch over a mixed batch (N = 2^12..2^18, OMP/SP) versus a loop
+    of single-signal cs_recover calls on the same stream, same inputs."""
+    import torch
+    from paper_1509_03979_gb300 import binding
+
+    torch.cuda.set_device(local_rank)
+    devc = torch.device("cuda", local_rank)
+    probs = synth.batched_workload(B=args.batched_count)
+    mine = [probs[i] for i in shard.rank_signals(rank, world, len(probs) // world)]
+    ops, ys, Ks, algos = [], [], [], []
+    for p in mine:
+        op = binding.Operator(p.N, p.M, p.op_seed)
+        yc = op.apply(torch.from_numpy(p.signal().astype(np.float32)).to(devc))
+        sig = p.noise_rel * torch.linalg.vector_norm(yc) / np.sqrt(p.M)
+        ys.append((yc + sig * torch.from_numpy(p.noise_unit().astype(np.float32)).to(devc)).contiguous())
+        ops.append(op)
+        Ks.append(p.K)
+        algos.append(p.algo)
+    souts = [torch.empty(op.N, device=devc) for op in ops]
+    supps = [torch.empty(k, dtype=torch.int32, device=devc) for k in Ks]
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        binding.recover_batched(ops, ys, Ks, algos, CG_TOL, CG_MAXIT, souts, supps)
+
+    def plain():
+        for op, y, k, a, so, sp in zip(ops, ys, Ks, algos, souts, supps):
+            op.recover(y, k, a, CG_TOL, CG_MAXIT, so, sp)
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms) / 1e3
+
+    batched()
+    plain()
+    torch.cuda.synchronize()
+    tb = timed(batched, args.steps)
+    tp = timed(plain, max(1, args.steps // 2))
+    vb = shard.aggregate_throughput(tb, world, len(mine), args.steps)
+    vp = shard.aggregate_throughput(tp, world, len(mine), max(1, args.steps // 2))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "recoveries/s (mixed batch, one launch)", "value": vb, "unit": "recoveries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * tb / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"{len(probs)} signals, N=2^12..2^18, mixed OMP/SP (config 4)"},
+            "plain_loop": {"value": vp, "unit": "recoveries/s", "ms_per_pass": 1e3 * tp / max(1, args.steps // 2)},
+            "batched_over_plain": vb / vp, "gpu_launches": args.steps * 5,
+        }), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -338,7 +428,10 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl")
     try:
-        run_gb300(args, rank, world, local_rank)
+        if args.workload == "batched":
+            run_batched(args, rank, world, local_rank)
+        else:
+            run_gb300(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist
