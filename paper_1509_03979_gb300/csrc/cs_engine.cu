@@ -395,8 +395,11 @@ struct Geo {
   int N, L, P, F, h, lh, S2, c, four_n;
 };
 
+// Per-CTA context of the signal being processed.  It lives in shared memory (one copy per CTA)
+// so every function reads it with plain shared loads: a per-thread copy on the stack measured
+// as the largest source of local-memory traffic.  Fields are written by thread 0 before a
+// barrier that every later reader passes.
 struct Ctx {
-  cg::cluster_group cl;
   Smem sm;
   Tw tw;
   Geo g;
@@ -415,12 +418,17 @@ struct Ctx {
   float* cgp;
   float* cgq;
   uint32_t* bits;     // per-cluster N-bit output bitmask
-  int ring_slot;
-  int hist_slot;
-  int cg_total;
+  int ring_slot;      // next cluster-reduction slot (all CTAs advance it identically)
+  int hist_slot;      // next radix-histogram buffer
+  int cg_total;       // statistics (thread 0 only)
   int cg_hits;
   int ntrans;         // N-point DCT applications (forward or inverse)
 };
+__shared__ Ctx C;
+
+__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+template <class T>
+__device__ __forceinline__ T* cl_map(T* p, int rank) { return cg::this_cluster().map_shared_rank(p, rank); }
 
 __device__ __forceinline__ float& slot_ref(float2* A, int sigma) {
   return reinterpret_cast<float*>(A)[2 * aidx(sigma >> 1) + (sigma & 1)];
@@ -497,26 +505,28 @@ __device__ __forceinline__ int pair_outputs(const Geo& g, int k, bool self, int*
 // ---------------------------------------------------------------- cluster-wide reductions
 // Sum n (<= 4) per-thread values over the whole cluster; every thread gets the totals, and
 // every CTA adds the partials in rank order, so all CTAs hold bit-identical results.
-__device__ __noinline__ void cluster_sum(Ctx& x, float* v, int n) {
+__device__ __noinline__ void cluster_sum(float* v, int n) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* wsum = shp(x.sm.wsum);
+  float* wsum = shp(C.sm.wsum);
   for (int i = 0; i < n; ++i) {
     const float s = warp_sum(v[i]);
     if (lane == 0) wsum[i * 16 + warp] = s;
   }
+  const int slot = C.ring_slot;                    // read by every thread before the barrier
   __syncthreads();
-  float* ring = shp(x.sm.ring) + 4 * x.ring_slot;
+  float* ring = shp(C.sm.ring) + 4 * slot;
   if (threadIdx.x < n) {
     float t = 0.f;
     for (int w = 0; w < NT / 32; ++w) t += wsum[threadIdx.x * 16 + w];
     ring[threadIdx.x] = t;
   }
-  x.cl.sync();
-  float* fscr = shp(x.sm.fscr);
+  if (threadIdx.x == 0) C.ring_slot = (slot + 1) & 3;   // next reader is past the barriers below
+  cl_sync();
+  float* fscr = shp(C.sm.fscr);
   if (warp == 0) {
     for (int i = 0; i < n; ++i) {
       float t = 0.f;
-      if (lane < x.g.P) t = *x.cl.map_shared_rank(ring + i, lane);
+      if (lane < C.g.P) t = *cl_map(ring + i, lane);
       // fixed-shape tree over 32 lanes: identical order in every CTA
       t = warp_sum(t);
       if (lane == 0) fscr[i] = t;
@@ -524,30 +534,31 @@ __device__ __noinline__ void cluster_sum(Ctx& x, float* v, int n) {
   }
   __syncthreads();
   for (int i = 0; i < n; ++i) v[i] = fscr[i];
-  x.ring_slot = (x.ring_slot + 1) & 3;
 }
 
 // Max of up to two 64-bit keys over the cluster.
-__device__ __noinline__ void cluster_max64(Ctx& x, unsigned long long* v, int n) {
+__device__ __noinline__ void cluster_max64(unsigned long long* v, int n) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long* wmax = shp(x.sm.wmax);
+  unsigned long long* wmax = shp(C.sm.wmax);
   for (int i = 0; i < n; ++i) {
     const unsigned long long s = warp_max64(v[i]);
     if (lane == 0) wmax[i * 16 + warp] = s;
   }
+  const int slot = C.ring_slot;
   __syncthreads();
-  unsigned long long* ring = shp(x.sm.ring64) + 2 * x.ring_slot;
+  unsigned long long* ring = shp(C.sm.ring64) + 2 * slot;
   if (threadIdx.x < n) {
     unsigned long long t = 0;
     for (int w = 0; w < NT / 32; ++w) t = max(t, wmax[threadIdx.x * 16 + w]);
     ring[threadIdx.x] = t;
   }
-  x.cl.sync();
-  int* iscr = shp(x.sm.iscr);
+  if (threadIdx.x == 0) C.ring_slot = (slot + 1) & 3;
+  cl_sync();
+  int* iscr = shp(C.sm.iscr);
   if (warp == 0) {
     for (int i = 0; i < n; ++i) {
       unsigned long long t = 0;
-      if (lane < x.g.P) t = *x.cl.map_shared_rank(ring + i, lane);
+      if (lane < C.g.P) t = *cl_map(ring + i, lane);
       t = warp_max64(t);
       if (lane == 0) iscr[2 * i] = (int)(t & 0xffffffffu), iscr[2 * i + 1] = (int)(t >> 32);
     }
@@ -556,13 +567,12 @@ __device__ __noinline__ void cluster_max64(Ctx& x, unsigned long long* v, int n)
   for (int i = 0; i < n; ++i)
     v[i] = ((unsigned long long)(uint32_t)iscr[2 * i + 1] << 32) | (uint32_t)iscr[2 * i];
   __syncthreads();
-  x.ring_slot = (x.ring_slot + 1) & 3;
 }
 
 // Exclusive block scan of one int per thread; returns the exclusive prefix, total via *tot.
-__device__ __noinline__ int block_scan(Ctx& x, int v, int* tot) {
+__device__ __noinline__ int block_scan(int v, int* tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int* iscr = shp(x.sm.iscr);
+  int* iscr = shp(C.sm.iscr);
   int inc = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -592,30 +602,32 @@ __device__ __noinline__ int block_scan(Ctx& x, int v, int* tot) {
 // Rebuild this CTA's sorted support list (local slots) from a bitmask; returns its length.
 // The list and the CG vectors go to shared memory when this CTA's share fits, else to the
 // global fallback arrays (a per-CTA choice; no barrier depends on it).
-__device__ __noinline__ int build_list(Ctx& x, const uint32_t* m) {
+__device__ __noinline__ int build_list(const uint32_t* m) {
   // total first (to choose the destination), then a chunked ordered compaction
   int total = 0;
-  for (int w0 = 0; w0 < x.nwords; w0 += NT) {
+  for (int w0 = 0; w0 < C.nwords; w0 += NT) {
     const int w = w0 + threadIdx.x;
     int t;
-    block_scan(x, w < x.nwords ? __popc(m[w]) : 0, &t);
+    block_scan(w < C.nwords ? __popc(m[w]) : 0, &t);
     total += t;
   }
-  const bool on_chip = total <= x.cap;
-  int* list = on_chip ? shp(x.sm.cgl) : x.glist;
-  float* cg = on_chip ? shp(x.sm.cgv) : x.gcg;
-  const int stride = on_chip ? x.cap : 2 * x.g.F;
-  x.list = list;
-  x.cgx = cg;
-  x.cgr = cg + stride;
-  x.cgp = cg + 2 * stride;
-  x.cgq = cg + 3 * stride;
+  const bool on_chip = total <= C.cap;
+  int* list = on_chip ? shp(C.sm.cgl) : C.glist;
+  float* cg = on_chip ? shp(C.sm.cgv) : C.gcg;
+  const int stride = on_chip ? C.cap : 2 * C.g.F;
+  if (threadIdx.x == 0) {   // read by the callers after this function's final barrier
+    C.list = list;
+    C.cgx = cg;
+    C.cgr = cg + stride;
+    C.cgp = cg + 2 * stride;
+    C.cgq = cg + 3 * stride;
+  }
   int base = 0;
-  for (int w0 = 0; w0 < x.nwords; w0 += NT) {
+  for (int w0 = 0; w0 < C.nwords; w0 += NT) {
     const int w = w0 + threadIdx.x;
-    const uint32_t word = w < x.nwords ? m[w] : 0u;
+    const uint32_t word = w < C.nwords ? m[w] : 0u;
     int t;
-    int off = base + block_scan(x, __popc(word), &t);
+    int off = base + block_scan(__popc(word), &t);
     uint32_t bitsleft = word;
     while (bitsleft) {
       const int b = __ffs(bitsleft) - 1;
@@ -629,9 +641,9 @@ __device__ __noinline__ int build_list(Ctx& x, const uint32_t* m) {
 }
 
 // Omega membership bits of every frequency task of this CTA (bit i <-> output f[i]).
-__device__ __noinline__ void build_fbits(Ctx& x) {
-  const Geo g = x.g;
-  uint8_t* fb = shp(x.sm.fbits);
+__device__ __noinline__ void build_fbits() {
+  const Geo g = C.g;
+  uint8_t* fb = shp(C.sm.fbits);
   const int nt = ntasks(g);
   for (int t = threadIdx.x; t < nt; t += NT) {
     int sa, kpa, sb, kpb;
@@ -640,7 +652,7 @@ __device__ __noinline__ void build_fbits(Ctx& x) {
       const int k = kq_of(g, sa) + g.F * kpa;
       int f[4];
       const int nf = pair_outputs(g, k, sa == sb && kpa == kpb, f);
-      for (int i = 0; i < nf; ++i) bits |= (uint8_t)(((x.omask[f[i] >> 5] >> (f[i] & 31)) & 1u) << i);
+      for (int i = 0; i < nf; ++i) bits |= (uint8_t)(((C.omask[f[i] >> 5] >> (f[i] & 31)) & 1u) << i);
     }
     fb[t] = bits;
   }
@@ -653,12 +665,12 @@ __device__ __noinline__ void build_fbits(Ctx& x) {
 // the thread that owns frequency slot s loads A_p[k_q(s)] from every CTA p, multiplies by
 // omega_L^{p k_q} = (omega_L^{k_q})^p and transforms over p in registers.
 template <int PT>
-__device__ __forceinline__ void pull_fwd(const cg::cluster_group& cl, const Geo& g, const Tw& tw, float2* A, float2* B) {
+__device__ __forceinline__ void pull_fwd(const Geo& g, const Tw& tw, float2* A, float2* B) {
   for (int s = threadIdx.x; s < g.S2; s += NT) {
     const int k = kq_of(g, s);
     float2 v[PT];
 #pragma unroll
-    for (int p = 0; p < PT; ++p) v[p] = cl.map_shared_rank(A, p)[aidx(k)];
+    for (int p = 0; p < PT; ++p) v[p] = cl_map(A, p)[aidx(k)];
     if constexpr (PT > 1) {
       twiddle_powers<PT, -1>(v, tw, 8 * k);
       dft<PT, -1>(v);
@@ -668,10 +680,10 @@ __device__ __forceinline__ void pull_fwd(const cg::cluster_group& cl, const Geo&
   }
 }
 
-__device__ __noinline__ void scatter_fwd(Ctx& x, int src, int nloc, const float* dense, const float* gin) {
-  const Geo g = x.g;
-  float2* A = shp(x.sm.A);
-  const uint32_t* signw = shp(x.sm.signw);
+__device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, const float* gin) {
+  const Geo g = C.g;
+  float2* A = shp(C.sm.A);
+  const uint32_t* signw = shp(C.sm.signw);
   const int F = g.F;
   if (src == SRC_GLOBAL_N) {
     for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(g, sg)] * sgn_bits(signw, sg);
@@ -680,9 +692,9 @@ __device__ __noinline__ void scatter_fwd(Ctx& x, int src, int nloc, const float*
     float4* A4 = reinterpret_cast<float4*>(A);
     for (int q = threadIdx.x; q < apad(F) / 2; q += NT) A4[q] = z4;
     __syncthreads();
-    const int* list = x.list;
+    const int* list = C.list;
     if (src == SRC_CG) {
-      const float* vals = x.cgp;
+      const float* vals = C.cgp;
       for (int i = threadIdx.x; i < nloc; i += NT) {
         const int sg = list[i];
         slot_ref(A, sg) = vals[i] * sgn_bits(signw, sg);
@@ -698,31 +710,31 @@ __device__ __noinline__ void scatter_fwd(Ctx& x, int src, int nloc, const float*
 }
 
 // Cluster barrier (every CTA's A is final), then the fused pull + P-point DFT into B.
-__device__ __noinline__ void exchange_fwd(Ctx& x) {
-  const Geo g = x.g;
-  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
-  float2* A = shp(x.sm.A);
-  float2* B = shp(x.sm.B);
-  x.cl.sync();
+__device__ __noinline__ void exchange_fwd() {
+  const Geo g = C.g;
+  const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+  float2* A = shp(C.sm.A);
+  float2* B = shp(C.sm.B);
+  cl_sync();
   switch (g.P) {
-    case 1: pull_fwd<1>(x.cl, g, tw, A, B); break;
-    case 2: pull_fwd<2>(x.cl, g, tw, A, B); break;
-    case 4: pull_fwd<4>(x.cl, g, tw, A, B); break;
-    case 8: pull_fwd<8>(x.cl, g, tw, A, B); break;
-    default: pull_fwd<16>(x.cl, g, tw, A, B); break;
+    case 1: pull_fwd<1>(g, tw, A, B); break;
+    case 2: pull_fwd<2>(g, tw, A, B); break;
+    case 4: pull_fwd<4>(g, tw, A, B); break;
+    case 8: pull_fwd<8>(g, tw, A, B); break;
+    default: pull_fwd<16>(g, tw, A, B); break;
   }
   __syncthreads();
 }
 
 // Frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, and DCT-III
 // pre-processing back into the pair.  Returns this thread's MID_RESID sum of squares.
-__device__ __noinline__ float freq_half(Ctx& x, int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
-  const Geo g = x.g;
-  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
-  float2* B = shp(x.sm.B);
-  const uint8_t* fb = shp(x.sm.fbits);
-  const uint32_t* omask = x.omask;
-  const int32_t* orank = x.orank;
+__device__ __noinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
+  const Geo g = C.g;
+  const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+  float2* B = shp(C.sm.B);
+  const uint8_t* fb = shp(C.sm.fbits);
+  const uint32_t* omask = C.omask;
+  const int32_t* orank = C.orank;
   const int F = g.F, S2 = g.S2;
   const float wk = sqrtf(2.0f / (float)g.N), w0 = sqrtf(1.0f / (float)g.N);
   const int nt = ntasks(g);
@@ -798,14 +810,14 @@ __device__ __noinline__ float freq_half(Ctx& x, int kind, bool fwd_done, bool in
 // the stride-P layout with conj(omega_L^{c k}).  The twiddle of element
 // k = k0 + e NT is conj(omega_L^{c k0}) * conj(omega_L^{c NT})^e: one strided lookup per
 // thread and broadcast powers.
-__device__ __noinline__ void exchange_inv(Ctx& x) {
-  const Geo g = x.g;
-  const Tw tw = {shp(x.sm.twlo), shp(x.sm.twhi), x.tw.lo_bits, x.tw.lo_mask, x.tw.mask4n};
-  float2* A = shp(x.sm.A);
-  float2* B = shp(x.sm.B);
+__device__ __noinline__ void exchange_inv() {
+  const Geo g = C.g;
+  const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+  float2* A = shp(C.sm.A);
+  float2* B = shp(C.sm.B);
   const int F = g.F, S2 = g.S2;
   pstep<1>(B, g.P, S2);
-  x.cl.sync();                                      // every CTA's B is final
+  cl_sync();                                      // every CTA's B is final
   {
     constexpr int EPT = F_MAX / NT;
     float2 v[EPT];
@@ -815,7 +827,7 @@ __device__ __noinline__ void exchange_inv(Ctx& x) {
       if (k < F) {
         int cc, s;
         owner_of_kq(g, k, cc, s);
-        v[e] = x.cl.map_shared_rank(B, cc)[g.c * S2 + s];
+        v[e] = cl_map(B, cc)[g.c * S2 + s];
       }
     }
     if (g.c == 0) {
@@ -847,28 +859,28 @@ __device__ __noinline__ void exchange_inv(Ctx& x) {
 //         MID_OUT writes y_M = A x, MID_IN reads u_M (A^T u)
 //   inv   run the DCT-III back to the signal domain (result left in the A buffer)
 // Returns this thread's sum of squares of the MID_RESID residual.
-__device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* dense, const float* gin, int kind,
+__device__ __noinline__ float transform(int src, int nloc, const float* dense, const float* gin, int kind,
                                         bool inv, const float* vin, float* vout) {
   // Each step is its own call and this function holds almost nothing live across them, so
   // every step gets the full register budget (ptxas allocates registers across calls).
-  x.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
+  if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
   // B is free at the start of every transform: each transform ends with (or is followed by)
   // a cluster barrier after the last remote read of B, so the forward FFT may use B as its
   // ping-pong buffer.
   if (src != SRC_NONE) {
-    scatter_fwd(x, src, nloc, dense, gin);
-    local_fft<-1>(x.sm.A, x.sm.B, x.g.F, x.tw, x.g.four_n);
-    exchange_fwd(x);
+    scatter_fwd(src, nloc, dense, gin);
+    local_fft<-1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
+    exchange_fwd();
   } else {
-    x.cl.sync();                                    // nobody still reads this CTA's B
+    cl_sync();                                    // nobody still reads this CTA's B
   }
-  const float acc = freq_half(x, kind, src != SRC_NONE, inv, vin, vout);
+  const float acc = freq_half(kind, src != SRC_NONE, inv, vin, vout);
   if (inv) {
-    exchange_inv(x);
-    x.cl.sync();                                    // every pull from B is done: B is scratch again
-    local_fft<1>(x.sm.A, x.sm.B, x.g.F, x.tw, x.g.four_n);
+    exchange_inv();
+    cl_sync();                                    // every pull from B is done: B is scratch again
+    local_fft<1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
   } else {
-    x.cl.sync();                                    // nobody still reads this CTA's A
+    cl_sync();                                    // nobody still reads this CTA's A
   }
   return acc;
 }
@@ -878,24 +890,27 @@ __device__ __noinline__ float transform(Ctx& x, int src, int nloc, const float* 
 // cluster.  On return: keys > *tau are selected and *need more are to be taken among the keys
 // equal to *tau; *eq is the cluster-wide count of keys equal to *tau.
 template <class KeyFn>
-__device__ void radix_select(Ctx& x, int count, int K, KeyFn key, uint32_t* tau, int* need, int* eq) {
+__device__ void radix_select(int count, int K, KeyFn key, uint32_t* tau, int* need, int* eq) {
   uint32_t prefix = 0, pmask = 0;
   int nd = K;
   int last_eq = 0;
-  uint32_t* htot = shp(x.sm.htot);
-  int* iscr = shp(x.sm.iscr);
+  uint32_t* htot = shp(C.sm.htot);
+  int* iscr = shp(C.sm.iscr);
+  // every thread reads the histogram slot here, before the first barrier; thread 0 then keeps
+  // the shared copy one pass ahead (written before each pass's last barrier)
+  int hs = C.hist_slot;
   for (int shift = 24; shift >= 0; shift -= 8) {
-    uint32_t* hist = shp(x.sm.hist) + 256 * x.hist_slot;
+    uint32_t* hist = shp(C.sm.hist) + 256 * hs;
     if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
     __syncthreads();
     for (int i = threadIdx.x; i < count; i += NT) {
       const uint32_t kk = key(i);
       if (kk != 0u && (kk & pmask) == prefix) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
     }
-    x.cl.sync();
+    cl_sync();
     if (threadIdx.x < 256) {
       uint32_t t = 0;
-      for (int r = 0; r < x.g.P; ++r) t += *x.cl.map_shared_rank(hist + threadIdx.x, r);
+      for (int r = 0; r < C.g.P; ++r) t += *cl_map(hist + threadIdx.x, r);
       htot[threadIdx.x] = t;
     }
     __syncthreads();
@@ -934,8 +949,9 @@ __device__ void radix_select(Ctx& x, int count, int K, KeyFn key, uint32_t* tau,
     const int dig = iscr[0];
     const int above = iscr[1];
     last_eq = iscr[2];
+    hs ^= 1;
+    if (threadIdx.x == 0) C.hist_slot = hs;
     __syncthreads();
-    x.hist_slot ^= 1;
     if (dig < 0) {   // take every candidate (uniform decision)
       *tau = 0u; *need = 0; *eq = 0;
       return;
@@ -952,16 +968,16 @@ __device__ void radix_select(Ctx& x, int count, int K, KeyFn key, uint32_t* tau,
 // Select the K largest keys (ties towards the lowest signal index) and call mark(i) for each
 // selected index; the second radix pass on the index only runs when the threshold is tied.
 template <class KeyFn, class IdxFn, class MarkFn>
-__device__ void select_topk(Ctx& x, int count, int K, KeyFn key, IdxFn nidx, MarkFn mark) {
+__device__ void select_topk(int count, int K, KeyFn key, IdxFn nidx, MarkFn mark) {
   uint32_t tau;
   int need, eq;
-  radix_select(x, count, K, key, &tau, &need, &eq);
+  radix_select(count, K, key, &tau, &need, &eq);
   if (need > 0 && eq > need) {
-    const uint32_t N = (uint32_t)x.g.N;
+    const uint32_t N = (uint32_t)C.g.N;
     uint32_t tau2;
     int need2, eq2;
     radix_select(
-        x, count, need, [&](int i) { return key(i) == tau ? N - (uint32_t)nidx(i) : 0u; }, &tau2, &need2, &eq2);
+        count, need, [&](int i) { return key(i) == tau ? N - (uint32_t)nidx(i) : 0u; }, &tau2, &need2, &eq2);
     for (int i = threadIdx.x; i < count; i += NT) {
       const uint32_t kk = key(i);
       if (kk > tau || (kk == tau && N - (uint32_t)nidx(i) >= tau2)) mark(i);
@@ -990,15 +1006,15 @@ enum R0Src : int { R0_FROM_A = 0, R0_FROM_CY = 1 };
 // on the list (warm) or 0, with r0 = b - H x0 taken from the A buffer (R0_FROM_A: the caller
 // has just computed A^T (y - A x0)) or from cy (R0_FROM_CY, x0 = 0).  Loop while
 // ||r_j|| > tol ||b|| (the printed loop test is read as its negation) and j < maxit.
-__device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r0src, float tol, int maxit) {
-  float* xd = x.xd[wi];
-  const float* cy = x.cy;
-  const float2* A = shp(x.sm.A);
-  const uint32_t* signw = shp(x.sm.signw);
-  const int* list = x.list;
-  float* cgx = x.cgx;
-  float* cgr = x.cgr;
-  float* cgp = x.cgp;
+__device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, float tol, int maxit) {
+  float* xd = C.xd[wi];
+  const float* cy = C.cy;
+  const float2* A = shp(C.sm.A);
+  const uint32_t* signw = shp(C.sm.signw);
+  const int* list = C.list;
+  float* cgx = C.cgx;
+  float* cgr = C.cgr;
+  float* cgp = C.cgp;
   float v[2] = {0.f, 0.f};
   for (int i = threadIdx.x; i < nloc; i += NT) {
     const int sg = list[i];
@@ -1011,27 +1027,27 @@ __device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r
     v[0] = fmaf(r0, r0, v[0]);
     v[1] = fmaf(b, b, v[1]);
   }
-  cluster_sum(x, v, 2);
+  cluster_sum(v, 2);
   float rr = v[0];
   const float stop2 = tol * tol * v[1];
   int it = 0;
   while (it < maxit && rr > stop2) {
-    transform(x, SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
+    transform(SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
     // pointers are re-read from the context after the call (nothing held live across it)
-    const float2* Ax = shp(x.sm.A);
-    const uint32_t* sw = shp(x.sm.signw);
-    const int* li = x.list;
-    float* px = x.cgx;
-    float* pr = x.cgr;
-    float* pp = x.cgp;
-    float* pq_ = x.cgq;
+    const float2* Ax = shp(C.sm.A);
+    const uint32_t* sw = shp(C.sm.signw);
+    const int* li = C.list;
+    float* px = C.cgx;
+    float* pr = C.cgr;
+    float* pp = C.cgp;
+    float* pq_ = C.cgq;
     float pq = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
       const float q = corr_at(Ax, sw, li[i]);
       pq_[i] = q;
       pq = fmaf(pp[i], q, pq);
     }
-    cluster_sum(x, &pq, 1);
+    cluster_sum(&pq, 1);
     const float alpha = rr / pq;
     float rn = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
@@ -1040,33 +1056,35 @@ __device__ __noinline__ void cg_solve(Ctx& x, int wi, int nloc, bool warm, int r
       pr[i] = r;
       rn = fmaf(r, r, rn);
     }
-    cluster_sum(x, &rn, 1);
+    cluster_sum(&rn, 1);
     const float beta = rn / rr;
     rr = rn;
     for (int i = threadIdx.x; i < nloc; i += NT) pp[i] = fmaf(beta, pp[i], pr[i]);
     ++it;
   }
-  x.cg_total += it;
-  if (it >= maxit && rr > stop2) x.cg_hits += 1;
+  if (threadIdx.x == 0) {
+    C.cg_total += it;
+    if (it >= maxit && rr > stop2) C.cg_hits += 1;
+  }
   {
-    const int* li = x.list;
-    const float* px = x.cgx;
-    float* xo = x.xd[wi];
+    const int* li = C.list;
+    const float* px = C.cgx;
+    float* xo = C.xd[wi];
     for (int i = threadIdx.x; i < nloc; i += NT) xo[li[i]] = px[i];
   }
   __syncthreads();
 }
 
 // Residual-correlation: A buffer <- C^T P^T (y - A xd) (unsigned slots), returns ||y - A xd||^2.
-__device__ __noinline__ float resid_corr(Ctx& x, int wi, int nloc, const float* y) {
-  float v = transform(x, SRC_DENSE_SLOTS, nloc, x.xd[wi], nullptr, MID_RESID, true, y, nullptr);
-  cluster_sum(x, &v, 1);
+__device__ __noinline__ float resid_corr(int wi, int nloc, const float* y) {
+  float v = transform(SRC_DENSE_SLOTS, nloc, C.xd[wi], nullptr, MID_RESID, true, y, nullptr);
+  cluster_sum(&v, 1);
   return v;
 }
 
 // ------------------------------------------------------------------------ task execution
-__device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int nloc, float rn2, int outer) {
-  const Geo g = x.g;
+__device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, float rn2, int outer) {
+  const Geo g = C.g;
   const int N = g.N, P = g.P;
   // zero s_out and the output bitmask (contiguous share per CTA)
   const int per = N / P;
@@ -1075,57 +1093,58 @@ __device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int n
   const int wper = (W + P - 1) / P;
   for (int i = threadIdx.x; i < wper; i += NT) {
     const int w = g.c * wper + i;
-    if (w < W) x.bits[w] = 0u;
+    if (w < W) C.bits[w] = 0u;
   }
-  x.cl.sync();
+  cl_sync();
   {
-    const int* list = x.list;
-    const float* xd = x.xd[wi];
+    const int* list = C.list;
+    const float* xd = C.xd[wi];
     for (int i = threadIdx.x; i < nloc; i += NT) {
       const int sg = list[i];
       const int n = n_of_slot(g, sg);
       t.out[n] = xd[sg];
-      atomicOr(&x.bits[n >> 5], 1u << (n & 31));
+      atomicOr(&C.bits[n >> 5], 1u << (n & 31));
     }
   }
-  x.cl.sync();
+  cl_sync();
   // sorted support: CTA c compacts words [c wper, (c+1) wper)
   int cnt = 0;
   for (int i = threadIdx.x; i < wper; i += NT) {
     const int w = g.c * wper + i;
-    if (w < W) cnt += __popc(x.bits[w]);
+    if (w < W) cnt += __popc(C.bits[w]);
   }
   float fc = (float)cnt;   // counts < 2^24: exact in FP32
-  float* ring = shp(x.sm.ring);
-  int* iscr = shp(x.sm.iscr);
+  float* ring = shp(C.sm.ring);
+  int* iscr = shp(C.sm.iscr);
   {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* wsum = shp(x.sm.wsum);
+    float* wsum = shp(C.sm.wsum);
     float s = warp_sum(fc);
     if (lane == 0) wsum[warp] = s;
     __syncthreads();
+    const int slot = C.ring_slot;   // only thread 0 uses and advances it here
     if (threadIdx.x == 0) {
       float tt = 0.f;
       for (int w = 0; w < NT / 32; ++w) tt += wsum[w];
-      ring[4 * x.ring_slot] = tt;
+      ring[4 * slot] = tt;
     }
-    x.cl.sync();
+    cl_sync();
     if (threadIdx.x == 0) {
       float off = 0.f;
-      for (int r = 0; r < g.c; ++r) off += *x.cl.map_shared_rank(ring + 4 * x.ring_slot, r);
+      for (int r = 0; r < g.c; ++r) off += *cl_map(ring + 4 * slot, r);
       iscr[40] = (int)off;
+      C.ring_slot = (slot + 1) & 3;
     }
     __syncthreads();
-    x.ring_slot = (x.ring_slot + 1) & 3;
   }
   int base = iscr[40];
   __syncthreads();
   // block-ordered compaction: wper words per CTA, processed NT at a time
   for (int w0 = 0; w0 < wper; w0 += NT) {
     const int w = g.c * wper + w0 + threadIdx.x;
-    const uint32_t word = (w0 + threadIdx.x < wper && w < W) ? x.bits[w] : 0u;
+    const uint32_t word = (w0 + threadIdx.x < wper && w < W) ? C.bits[w] : 0u;
     int tot;
-    int off = base + block_scan(x, __popc(word), &tot);
+    int off = base + block_scan(__popc(word), &tot);
     uint32_t b = word;
     while (b) {
       const int j = __ffs(b) - 1;
@@ -1138,39 +1157,39 @@ __device__ __noinline__ void write_recovery(Ctx& x, const Task& t, int wi, int n
   if (g.c == 0 && threadIdx.x == 0 && t.stats) {
     cs_stats st;
     st.outer_iters = outer;
-    st.cg_iters_total = x.cg_total;
-    st.cg_maxit_hits = x.cg_hits;
+    st.cg_iters_total = C.cg_total;
+    st.cg_maxit_hits = C.cg_hits;
     st.near_ties = 0;
     st.final_resid = sqrtf(rn2);
     st.min_margin = -1.f;
     st.status = CS_OK;
-    st.transforms = x.ntrans;
+    st.transforms = C.ntrans;
     *t.stats = st;
   }
 }
 
 // A^T y into cy (dense by slot, signed) and the A buffer; returns ||y||^2.
-__device__ __noinline__ float init_correlation(Ctx& x, const float* y) {
-  float v = transform(x, SRC_NONE, 0, nullptr, nullptr, MID_RESID, true, y, nullptr);
-  const float2* A = shp(x.sm.A);
-  const uint32_t* signw = shp(x.sm.signw);
-  float* cy = x.cy;
-  for (int sg = threadIdx.x; sg < 2 * x.g.F; sg += NT) cy[sg] = corr_at(A, signw, sg);
-  cluster_sum(x, &v, 1);
+__device__ __noinline__ float init_correlation(const float* y) {
+  float v = transform(SRC_NONE, 0, nullptr, nullptr, MID_RESID, true, y, nullptr);
+  const float2* A = shp(C.sm.A);
+  const uint32_t* signw = shp(C.sm.signw);
+  float* cy = C.cy;
+  for (int sg = threadIdx.x; sg < 2 * C.g.F; sg += NT) cy[sg] = corr_at(A, signw, sg);
+  cluster_sum(&v, 1);
   return v;
 }
 
-__device__ void zero_mask(Ctx& x, uint32_t* m) {
-  for (int w = threadIdx.x; w < x.nwords; w += NT) m[w] = 0u;
+__device__ void zero_mask(uint32_t* m) {
+  for (int w = threadIdx.x; w < C.nwords; w += NT) m[w] = 0u;
   __syncthreads();
 }
 
 // Top-K of |c| over the local slots not in `excl` (may be null); marks into `dst`.
-__device__ __noinline__ void topk_corr(Ctx& x, int K, const uint32_t* excl, uint32_t* dst) {
-  const Geo g = x.g;
-  float2* A = shp(x.sm.A);
+__device__ __noinline__ void topk_corr(int K, const uint32_t* excl, uint32_t* dst) {
+  const Geo g = C.g;
+  float2* A = shp(C.sm.A);
   select_topk(
-      x, 2 * g.F, K,
+      2 * g.F, K,
       [&](int sg) -> uint32_t {
         if (excl && mask_bit(excl, sg)) return 0u;
         return abs_key(slot_ref(A, sg));
@@ -1182,9 +1201,9 @@ __device__ __noinline__ void topk_corr(Ctx& x, int K, const uint32_t* excl, uint
 // OMP argmax step: t = argmax_{j not in S} |c_j| (lowest index on ties); returns the winner's
 // signal index or -1 when no candidate is left.  Adds it to the support mask (owner CTA) and
 // zeroes its slot of the warm-start vector.
-__device__ __noinline__ int omp_select(Ctx& x, uint32_t* mA) {
-  const Geo g = x.g;
-  const float2* A = shp(x.sm.A);
+__device__ __noinline__ int omp_select(uint32_t* mA) {
+  const Geo g = C.g;
+  const float2* A = shp(C.sm.A);
   unsigned long long key = 0;
   for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
     if (mask_bit(mA, sg)) continue;
@@ -1192,58 +1211,58 @@ __device__ __noinline__ int omp_select(Ctx& x, uint32_t* mA) {
                                   (0xffffffffu - (uint32_t)n_of_slot(g, sg));
     key = kk > key ? kk : key;
   }
-  cluster_max64(x, &key, 1);
+  cluster_max64(&key, 1);
   if (key == 0ull) return -1;   // no candidate left (uniform: key is cluster-reduced)
   const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
   int owner, sg;
-  slot_of_n(x.g, n, owner, sg);
-  if (owner == x.g.c && threadIdx.x == 0) {
+  slot_of_n(C.g, n, owner, sg);
+  if (owner == C.g.c && threadIdx.x == 0) {
     mA[sg >> 5] |= 1u << (sg & 31);
-    x.xd[0][sg] = 0.f;
+    C.xd[0][sg] = 0.f;
   }
   __syncthreads();
   return n;
 }
 
-__device__ __noinline__ void run_omp(Ctx& x, const Task& t) {
-  init_correlation(x, t.in);
-  zero_mask(x, shp(x.sm.mask[0]));
+__device__ __noinline__ void run_omp(const Task& t) {
+  init_correlation(t.in);
+  zero_mask(shp(C.sm.mask[0]));
   int nloc = 0;
   float rn2 = 0.f;
   for (int it = 0; it < t.K; ++it) {
-    if (omp_select(x, shp(x.sm.mask[0])) < 0) break;
-    nloc = build_list(x, shp(x.sm.mask[0]));
-    cg_solve(x, 0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    rn2 = resid_corr(x, 0, nloc, t.in);
+    if (omp_select(shp(C.sm.mask[0])) < 0) break;
+    nloc = build_list(shp(C.sm.mask[0]));
+    cg_solve(0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    rn2 = resid_corr(0, nloc, t.in);
   }
-  write_recovery(x, t, 0, nloc, rn2, t.K);
+  write_recovery(t, 0, nloc, rn2, t.K);
 }
 
 // SP prune: S' = topK_{j in S~} |u_j| over the working list, marked into mW.
-__device__ __noinline__ void sp_prune(Ctx& x, int wi, int nW, int K, uint32_t* mW) {
-  zero_mask(x, mW);
-  const Geo g = x.g;
-  const int* list = x.list;
-  const float* xw = x.xd[wi];
+__device__ __noinline__ void sp_prune(int wi, int nW, int K, uint32_t* mW) {
+  zero_mask(mW);
+  const Geo g = C.g;
+  const int* list = C.list;
+  const float* xw = C.xd[wi];
   select_topk(
-      x, nW, K, [&](int i) -> uint32_t { return abs_key(xw[list[i]]); },
+      nW, K, [&](int i) -> uint32_t { return abs_key(xw[list[i]]); },
       [&](int i) { return n_of_slot(g, list[i]); },
       [&](int i) { const int sg = list[i]; atomicOr(&mW[sg >> 5], 1u << (sg & 31)); });
 }
 
 // SP merge: S~ = S u topK_{not in S} |A^T r| into mW, its list, and the warm start x0 = s on S,
 // 0 on the new entries.  Returns the list length.
-__device__ __noinline__ int sp_merge(Ctx& x, int acc, int K) {
+__device__ __noinline__ int sp_merge(int acc, int K) {
   const int wi = acc ^ 1;
-  uint32_t* mW = shp(x.sm.mask[wi]);
-  const uint32_t* mA = shp(x.sm.mask[acc]);
-  for (int w = threadIdx.x; w < x.nwords; w += NT) mW[w] = mA[w];
+  uint32_t* mW = shp(C.sm.mask[wi]);
+  const uint32_t* mA = shp(C.sm.mask[acc]);
+  for (int w = threadIdx.x; w < C.nwords; w += NT) mW[w] = mA[w];
   __syncthreads();
-  topk_corr(x, K, mA, mW);
-  const int nW = build_list(x, mW);
-  const int* list = x.list;
-  float* xw = x.xd[wi];
-  const float* xa = x.xd[acc];
+  topk_corr(K, mA, mW);
+  const int nW = build_list(mW);
+  const int* list = C.list;
+  float* xw = C.xd[wi];
+  const float* xa = C.xd[acc];
   for (int i = threadIdx.x; i < nW; i += NT) {
     const int sg = list[i];
     xw[sg] = mask_bit(mA, sg) ? xa[sg] : 0.f;
@@ -1252,54 +1271,54 @@ __device__ __noinline__ int sp_merge(Ctx& x, int acc, int K) {
   return nW;
 }
 
-__device__ __noinline__ float mask_diff(Ctx& x, int a, int b) {
-  const uint32_t* ma = shp(x.sm.mask[a]);
-  const uint32_t* mb = shp(x.sm.mask[b]);
+__device__ __noinline__ float mask_diff(int a, int b) {
+  const uint32_t* ma = shp(C.sm.mask[a]);
+  const uint32_t* mb = shp(C.sm.mask[b]);
   float diff = 0.f;
-  for (int w = threadIdx.x; w < x.nwords; w += NT) diff += (float)__popc(ma[w] ^ mb[w]);
-  cluster_sum(x, &diff, 1);
+  for (int w = threadIdx.x; w < C.nwords; w += NT) diff += (float)__popc(ma[w] ^ mb[w]);
+  cluster_sum(&diff, 1);
   return diff;
 }
 
-__device__ __noinline__ void run_sp(Ctx& x, const Task& t) {
-  init_correlation(x, t.in);
+__device__ __noinline__ void run_sp(const Task& t) {
+  init_correlation(t.in);
   int acc = 0;   // index of the accepted (support, solution) pair
-  zero_mask(x, shp(x.sm.mask[0]));
-  topk_corr(x, t.K, nullptr, shp(x.sm.mask[0]));
-  int nloc = build_list(x, shp(x.sm.mask[0]));
-  cg_solve(x, acc, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
-  float rn2 = resid_corr(x, acc, nloc, t.in);
+  zero_mask(shp(C.sm.mask[0]));
+  topk_corr(t.K, nullptr, shp(C.sm.mask[0]));
+  int nloc = build_list(shp(C.sm.mask[0]));
+  cg_solve(acc, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  float rn2 = resid_corr(acc, nloc, t.in);
   int rounds = 0;
   while (rounds < t.outer_max) {
     ++rounds;
     const int wi = acc ^ 1;
-    int nW = sp_merge(x, acc, t.K);                     // S~ and its warm start; r0 = c on S~
-    cg_solve(x, wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    sp_prune(x, wi, nW, t.K, shp(x.sm.mask[wi]));       // S'
-    nW = build_list(x, shp(x.sm.mask[wi]));
-    resid_corr(x, wi, nW, t.in);                        // r0 for x0 = u restricted to S'
-    cg_solve(x, wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    const float rn2_new = resid_corr(x, wi, nW, t.in);
-    const float diff = mask_diff(x, wi, acc);
+    int nW = sp_merge(acc, t.K);                     // S~ and its warm start; r0 = c on S~
+    cg_solve(wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    sp_prune(wi, nW, t.K, shp(C.sm.mask[wi]));       // S'
+    nW = build_list(shp(C.sm.mask[wi]));
+    resid_corr(wi, nW, t.in);                        // r0 for x0 = u restricted to S'
+    cg_solve(wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    const float rn2_new = resid_corr(wi, nW, t.in);
+    const float diff = mask_diff(wi, acc);
     if (diff == 0.f || rn2_new >= rn2) break;
     acc = wi;
     rn2 = rn2_new;
   }
   // the returned pair is `acc`; rebuild its list (the working list may differ)
-  nloc = build_list(x, shp(x.sm.mask[acc]));
-  write_recovery(x, t, acc, nloc, rn2, rounds);
+  nloc = build_list(shp(C.sm.mask[acc]));
+  write_recovery(t, acc, nloc, rn2, rounds);
 }
 
 // OMPR replacement step: z = s + A^T r, j = argmax_{not in S} |z|, i = argmin_{in S} |z|
 // (lowest index on ties).  If |z_j| > |z_i| swaps them in the support (owner CTAs), zeroes both
 // slots of the warm-start vector and returns true; otherwise returns false.
-__device__ __noinline__ bool ompr_swap(Ctx& x) {
-  const Geo g = x.g;
-  const float2* A = shp(x.sm.A);
-  const uint32_t* signw = shp(x.sm.signw);
-  uint32_t* mA = shp(x.sm.mask[0]);
+__device__ __noinline__ bool ompr_swap() {
+  const Geo g = C.g;
+  const float2* A = shp(C.sm.A);
+  const uint32_t* signw = shp(C.sm.signw);
+  uint32_t* mA = shp(C.sm.mask[0]);
   unsigned long long key[2] = {0ull, 0ull};
-  const float* xd = x.xd[0];
+  const float* xd = C.xd[0];
   for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
     const uint32_t lo = 0xffffffffu - (uint32_t)n_of_slot(g, sg);
     if (mask_bit(mA, sg)) {
@@ -1312,7 +1331,7 @@ __device__ __noinline__ bool ompr_swap(Ctx& x) {
       key[0] = kk > key[0] ? kk : key[0];
     }
   }
-  cluster_max64(x, key, 2);
+  cluster_max64(key, 2);
   const uint32_t zj = (uint32_t)(key[0] >> 32) - 1u;                  // |z_j| bits
   const uint32_t zi = 0xffffffffu - (uint32_t)(key[1] >> 32);         // |z_i| bits
   if (key[0] == 0ull || key[1] == 0ull || zj <= zi) return false;     // no improving swap
@@ -1322,36 +1341,36 @@ __device__ __noinline__ bool ompr_swap(Ctx& x) {
   slot_of_n(g, nj, oj, sj);
   slot_of_n(g, ni, oi, si);
   if (threadIdx.x == 0) {
-    if (oi == g.c) { mA[si >> 5] &= ~(1u << (si & 31)); x.xd[0][si] = 0.f; }
-    if (oj == g.c) { mA[sj >> 5] |= 1u << (sj & 31); x.xd[0][sj] = 0.f; }
+    if (oi == g.c) { mA[si >> 5] &= ~(1u << (si & 31)); C.xd[0][si] = 0.f; }
+    if (oj == g.c) { mA[sj >> 5] |= 1u << (sj & 31); C.xd[0][sj] = 0.f; }
   }
   __syncthreads();
   return true;
 }
 
-__device__ __noinline__ void run_ompr(Ctx& x, const Task& t) {
-  init_correlation(x, t.in);
-  zero_mask(x, shp(x.sm.mask[0]));
-  topk_corr(x, t.K, nullptr, shp(x.sm.mask[0]));
-  int nloc = build_list(x, shp(x.sm.mask[0]));
-  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
-  float rn2 = resid_corr(x, 0, nloc, t.in);
+__device__ __noinline__ void run_ompr(const Task& t) {
+  init_correlation(t.in);
+  zero_mask(shp(C.sm.mask[0]));
+  topk_corr(t.K, nullptr, shp(C.sm.mask[0]));
+  int nloc = build_list(shp(C.sm.mask[0]));
+  cg_solve(0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  float rn2 = resid_corr(0, nloc, t.in);
   int swaps = 0;
   while (swaps < t.outer_max) {
-    if (!ompr_swap(x)) break;
+    if (!ompr_swap()) break;
     ++swaps;
-    nloc = build_list(x, shp(x.sm.mask[0]));
-    resid_corr(x, 0, nloc, t.in);   // r0 for x0 = s without i, 0 at j
-    cg_solve(x, 0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
-    rn2 = resid_corr(x, 0, nloc, t.in);
+    nloc = build_list(shp(C.sm.mask[0]));
+    resid_corr(0, nloc, t.in);   // r0 for x0 = s without i, 0 at j
+    cg_solve(0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
+    rn2 = resid_corr(0, nloc, t.in);
   }
-  write_recovery(x, t, 0, nloc, rn2, swaps);
+  write_recovery(t, 0, nloc, rn2, swaps);
 }
 
 // Fixed support from a sorted global index list: set the bits this CTA owns.
-__device__ __noinline__ void mask_from_support(Ctx& x, const int32_t* supp, int k, uint32_t* m) {
-  zero_mask(x, m);
-  const Geo g = x.g;
+__device__ __noinline__ void mask_from_support(const int32_t* supp, int k, uint32_t* m) {
+  zero_mask(m);
+  const Geo g = C.g;
   for (int i = threadIdx.x; i < k; i += NT) {
     const int n = supp[i];
     if (n < 0 || n >= g.N) continue;
@@ -1362,45 +1381,45 @@ __device__ __noinline__ void mask_from_support(Ctx& x, const int32_t* supp, int 
   __syncthreads();
 }
 
-__device__ __noinline__ void run_ls_solve(Ctx& x, const Task& t) {
-  init_correlation(x, t.in);
-  uint32_t* m = shp(x.sm.mask[0]);
-  mask_from_support(x, t.supp_in, t.k_in, m);
-  const int nloc = build_list(x, m);
-  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
-  const Geo g = x.g;
+__device__ __noinline__ void run_ls_solve(const Task& t) {
+  init_correlation(t.in);
+  uint32_t* m = shp(C.sm.mask[0]);
+  mask_from_support(t.supp_in, t.k_in, m);
+  const int nloc = build_list(m);
+  cg_solve(0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  const Geo g = C.g;
   for (int i = threadIdx.x; i < t.k_in; i += NT) {
     const int n = t.supp_in[i];
     if (n < 0 || n >= g.N) continue;
     int owner, sg;
     slot_of_n(g, n, owner, sg);
-    if (owner == g.c) t.out[i] = x.xd[0][sg];
+    if (owner == g.c) t.out[i] = C.xd[0][sg];
   }
   if (g.c == 0 && threadIdx.x == 0 && t.stats) {
-    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK, x.ntrans};
+    cs_stats st = {1, C.cg_total, C.cg_hits, 0, -1.f, -1.f, CS_OK, C.ntrans};
     *t.stats = st;
   }
 }
 
-__device__ __noinline__ void run_ls_backward(Ctx& x, const Task& t) {
-  uint32_t* m = shp(x.sm.mask[0]);
-  mask_from_support(x, t.supp_in, t.k_in, m);
-  const Geo g = x.g;
+__device__ __noinline__ void run_ls_backward(const Task& t) {
+  uint32_t* m = shp(C.sm.mask[0]);
+  mask_from_support(t.supp_in, t.k_in, m);
+  const Geo g = C.g;
   // b = g placed by slot (cy doubles as the right-hand side)
   for (int i = threadIdx.x; i < t.k_in; i += NT) {
     const int n = t.supp_in[i];
     if (n < 0 || n >= g.N) continue;
     int owner, sg;
     slot_of_n(g, n, owner, sg);
-    if (owner == g.c) x.cy[sg] = t.in[i];
+    if (owner == g.c) C.cy[sg] = t.in[i];
   }
   __syncthreads();
-  const int nloc = build_list(x, m);
-  cg_solve(x, 0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
+  const int nloc = build_list(m);
+  cg_solve(0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
   // dy = A_S z
-  transform(x, SRC_DENSE_SLOTS, nloc, x.xd[0], nullptr, MID_OUT, false, nullptr, t.out);
+  transform(SRC_DENSE_SLOTS, nloc, C.xd[0], nullptr, MID_OUT, false, nullptr, t.out);
   if (g.c == 0 && threadIdx.x == 0 && t.stats) {
-    cs_stats st = {1, x.cg_total, x.cg_hits, 0, -1.f, -1.f, CS_OK, x.ntrans};
+    cs_stats st = {1, C.cg_total, C.cg_hits, 0, -1.f, -1.f, CS_OK, C.ntrans};
     *t.stats = st;
   }
 }
@@ -1408,34 +1427,38 @@ __device__ __noinline__ void run_ls_backward(Ctx& x, const Task& t) {
 // Per-task set-up (geometry, twiddle tables, sign bits, Omega bits) and dispatch.  The task is
 // read through a pointer so no copy of it stays in registers across the calls below (ptxas
 // allocates registers across calls: whatever a caller holds live is denied to its callees).
-__device__ __noinline__ void run_task(Ctx& x, const Task* tp, int P, int c, int F_alloc) {
+__device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc) {
   const OpDev& op = tp->op;
   if (op.P != P || op.F > F_alloc) {   // host grouping error: skip uniformly
     if (c == 0 && threadIdx.x == 0 && tp->stats) tp->stats->status = CS_ERR_INVALID_ARG;
     return;
   }
-  {
-    Geo& g = x.g;
+  const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
+  if (threadIdx.x == 0) {   // every CTA thread passed the previous task's cluster barrier
+    Geo& g = C.g;
     g.N = op.N; g.L = op.N >> 1; g.P = P; g.F = op.F; g.c = c;
     g.h = op.F / (2 * P); g.lh = __ffs(g.h) - 1; g.S2 = 2 * g.h; g.four_n = 4 * op.N;
-    x.M = op.M;
-    x.nwords = (2 * op.F + 31) / 32;
-    x.omask = op.omask; x.orank = op.orank;
-    x.cg_total = 0; x.cg_hits = 0; x.ntrans = 0;
+    C.M = op.M;
+    C.nwords = (2 * op.F + 31) / 32;
+    C.omask = op.omask; C.orank = op.orank;
+    C.cg_total = 0; C.cg_hits = 0; C.ntrans = 0;
     const size_t a = 2 * (size_t)F_alloc;
-    x.list = x.glist;
-    x.cgx = x.gcg; x.cgr = x.gcg + a; x.cgp = x.gcg + 2 * a; x.cgq = x.gcg + 3 * a;
+    C.list = C.glist;
+    C.cgx = C.gcg; C.cgr = C.gcg + a; C.cgp = C.gcg + 2 * a; C.cgq = C.gcg + 3 * a;
+    C.tw.lo = C.sm.twlo; C.tw.hi = C.sm.twhi; C.tw.lo_bits = op.lo_bits; C.tw.lo_mask = nlo - 1;
+    C.tw.mask4n = g.four_n - 1;
+  }
+  __syncthreads();
+  {
     // twiddle tables and sign bits
-    const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
-    float2* twlo = shp(x.sm.twlo);
-    float2* twhi = shp(x.sm.twhi);
+    float2* twlo = shp(C.sm.twlo);
+    float2* twhi = shp(C.sm.twhi);
     for (int i = threadIdx.x; i < nlo; i += NT) twlo[aidx(i)] = op.tw[i];
     for (int i = threadIdx.x; i < nhi; i += NT) twhi[i] = op.tw[nlo + i];
-    x.tw.lo = x.sm.twlo; x.tw.hi = x.sm.twhi; x.tw.lo_bits = op.lo_bits; x.tw.lo_mask = nlo - 1;
-    x.tw.mask4n = g.four_n - 1;
-    uint32_t* signw = shp(x.sm.signw);
-    const Geo gg = g;
-    for (int w = threadIdx.x; w < x.nwords; w += NT) {
+    uint32_t* signw = shp(C.sm.signw);
+    const Geo gg = C.g;
+    const int nwords = C.nwords;
+    for (int w = threadIdx.x; w < nwords; w += NT) {
       uint32_t bitsw = 0u;
       for (int b = 0; b < 32; ++b) {
         const int sg = 32 * w + b;
@@ -1448,27 +1471,27 @@ __device__ __noinline__ void run_task(Ctx& x, const Task* tp, int P, int c, int 
     }
   }
   __syncthreads();
-  build_fbits(x);
+  build_fbits();
   const Task& t = *tp;
   switch (t.mode) {
     case MODE_APPLY:
-      transform(x, SRC_GLOBAL_N, 0, nullptr, t.in, MID_OUT, false, nullptr, t.out);
+      transform(SRC_GLOBAL_N, 0, nullptr, t.in, MID_OUT, false, nullptr, t.out);
       break;
     case MODE_APPLY_T: {
-      transform(x, SRC_NONE, 0, nullptr, nullptr, MID_IN, true, t.in, nullptr);
-      const float2* A = shp(x.sm.A);
-      const uint32_t* signw = shp(x.sm.signw);
-      const Geo gg = x.g;
+      transform(SRC_NONE, 0, nullptr, nullptr, MID_IN, true, t.in, nullptr);
+      const float2* A = shp(C.sm.A);
+      const uint32_t* signw = shp(C.sm.signw);
+      const Geo gg = C.g;
       for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[n_of_slot(gg, sg)] = corr_at(A, signw, sg);
       break;
     }
     case MODE_RECOVER:
-      if (t.algo == CS_OMP) run_omp(x, t);
-      else if (t.algo == CS_SP) run_sp(x, t);
-      else run_ompr(x, t);
+      if (t.algo == CS_OMP) run_omp(t);
+      else if (t.algo == CS_SP) run_sp(t);
+      else run_ompr(t);
       break;
-    case MODE_LS_SOLVE: run_ls_solve(x, t); break;
-    case MODE_LS_BACKWARD: run_ls_backward(x, t); break;
+    case MODE_LS_SOLVE: run_ls_solve(t); break;
+    case MODE_LS_BACKWARD: run_ls_backward(t); break;
     default: break;
   }
 }
@@ -1479,20 +1502,23 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   const int c = (int)cl.block_rank();
   const int cid = blockIdx.x / P;
   const int ncl = gridDim.x / P;
-  Ctx x{cl, carve(lp.F_alloc)};
-  x.ring_slot = 0;
-  x.hist_slot = 0;
-  x.cap = cg_cap(lp.F_alloc);
-  float* base = lp.scratch + (size_t)cid * lp.scratch_per_cluster + (size_t)c * scratch_floats_per_cta(lp.F_alloc);
-  const size_t a = 2 * (size_t)lp.F_alloc;
-  x.xd[0] = base;
-  x.xd[1] = base + a;
-  x.cy = base + 2 * a;
-  x.glist = reinterpret_cast<int*>(base + 3 * a);
-  x.gcg = base + 4 * a;
-  x.bits = lp.bits + (size_t)cid * lp.bits_per_cluster;
+  if (threadIdx.x == 0) {
+    C.sm = carve(lp.F_alloc);
+    C.ring_slot = 0;
+    C.hist_slot = 0;
+    C.cap = cg_cap(lp.F_alloc);
+    float* base = lp.scratch + (size_t)cid * lp.scratch_per_cluster + (size_t)c * scratch_floats_per_cta(lp.F_alloc);
+    const size_t a = 2 * (size_t)lp.F_alloc;
+    C.xd[0] = base;
+    C.xd[1] = base + a;
+    C.cy = base + 2 * a;
+    C.glist = reinterpret_cast<int*>(base + 3 * a);
+    C.gcg = base + 4 * a;
+    C.bits = lp.bits + (size_t)cid * lp.bits_per_cluster;
+  }
+  __syncthreads();
   for (int ti = cid; ti < lp.ntasks; ti += ncl) {
-    run_task(x, lp.tasks ? lp.tasks + ti : &lp.single, P, c, lp.F_alloc);
+    run_task(lp.tasks ? lp.tasks + ti : &lp.single, P, c, lp.F_alloc);
     cl.sync();
   }
 }
