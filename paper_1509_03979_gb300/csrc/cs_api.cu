@@ -65,8 +65,8 @@ int8_t draw_sign(uint64_t sign_key, int64_t n) {
 }
 
 cs_status check_nm(int64_t N, int64_t M) {
-  if (!is_pow2(N) || N < N_MIN || N > N_MAX)
-    return fail(CS_ERR_UNSUPPORTED_N, "N must be a power of two in [16, 2^18], got " + std::to_string(N));
+  if (!is_pow2(N) || N < N_MIN || N > N_MAX_GRID)
+    return fail(CS_ERR_UNSUPPORTED_N, "N must be a power of two in [16, 2^22], got " + std::to_string(N));
   if (M < 1 || M > N) return fail(CS_ERR_INVALID_ARG, "M must satisfy 1 <= M <= N");
   return CS_OK;
 }
@@ -84,9 +84,10 @@ struct cs_op {
   float2* d_tw = nullptr;
   std::vector<int32_t> h_omega;
   cudaStream_t stream = nullptr;
-  float* d_scratch = nullptr;   // one cluster's scratch
+  float* d_scratch = nullptr;   // one cluster's scratch (or the whole grid's)
   uint32_t* d_bits = nullptr;
   cs_stats* d_stats = nullptr;
+  void* d_grid = nullptr;       // streamed geometry: rows, signal rows, barrier and reduction state
 };
 
 namespace {
@@ -100,6 +101,7 @@ void free_op(cs_op* op) {
   cudaFree(op->d_scratch);
   cudaFree(op->d_bits);
   cudaFree(op->d_stats);
+  cudaFree(op->d_grid);
   delete op;
 }
 
@@ -114,6 +116,8 @@ Task base_task(const cs_op* op, int mode) {
   t.cg_maxit = 100;
   t.outer_max = 0;
   t.stats = op->d_stats;
+  t.grid_scratch = op->d_scratch;
+  t.grid_bits = op->d_bits;
   return t;
 }
 
@@ -123,6 +127,7 @@ Launch single_launch(const cs_op* op, const Task& t) {
   L.single = t;
   L.ntasks = 1;
   L.F_alloc = op->dev.F;
+  L.plan = op->dev.grid ? grid_plan(op->dev) : cluster_plan(op->dev.F);
   L.scratch = op->d_scratch;
   L.scratch_per_cluster = (size_t)op->dev.P * scratch_floats_per_cta(op->dev.F);
   L.bits = op->d_bits;
@@ -132,7 +137,14 @@ Launch single_launch(const cs_op* op, const Task& t) {
 
 cs_status run_single(cs_op* op, const Task& t) {
   const Launch L = single_launch(op, t);
-  cudaError_t e = launch_engine(L, op->dev.P, 1, op->stream);
+  cudaError_t e;
+  if (op->dev.grid) {
+    if ((e = cudaMemsetAsync(op->dev.gerr, 0, sizeof(int), op->stream)) != cudaSuccess) return cuda_fail(e, "memset");
+    e = launch_grid(L, op->dev.G, op->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid launch");
+    return CS_OK;
+  }
+  e = launch_engine(L, op->dev.P, 1, op->stream);
   if (e != cudaSuccess) return cuda_fail(e, "engine launch");
   return CS_OK;
 }
@@ -190,16 +202,31 @@ cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) {
     tw[(size_t)(nlo + j)] = make_float2((float)std::cos(a), (float)-std::sin(a));
   }
   const int64_t L = N / 2;
-  int P = 1, F = (int)L;
-  if (L > F_MAX) { P = (int)(L / F_MAX); F = F_MAX; }
   OpDev& d = op->dev;
   d.N = (int)N;
   d.M = (int)M;
-  d.P = P;
-  d.F = F;
   d.lo_bits = lo_bits;
   d.hi_bits = hi_bits;
   d.sign_key = seed ^ SIGN_SALT;
+  d.grid = N > N_MAX ? 1 : 0;
+  int P = 1, F = (int)L;
+  if (d.grid) {
+    // streamed geometry: rows of S1 points, G CTAs owning R rows each, column blocks of W
+    d.S1 = GRID_S1;
+    d.S2 = (int)(L / GRID_S1);
+    d.G = std::min(GRID_G_MAX, d.S2);
+    d.R = d.S2 / d.G;
+    d.W = GRID_BLOCK / d.S2;
+    d.NB = d.S1 / d.W;
+    d.bpc = d.NB / d.G;
+    P = d.G;
+    F = d.R * d.S1;
+  } else if (L > F_MAX) {
+    P = (int)(L / F_MAX);
+    F = F_MAX;
+  }
+  d.P = P;
+  d.F = F;
   cudaError_t e;
   const size_t scratch = (size_t)P * scratch_floats_per_cta(F) * sizeof(float);
 #define CSG_TRY(call)                                   \
@@ -225,6 +252,41 @@ cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) {
   d.omask = op->d_omask;
   d.orank = op->d_orank;
   d.tw = op->d_tw;
+  if (d.grid) {
+    // one allocation: rows [S2][S1], signal rows [G][R][apad(S1)], barrier (2) + status (1),
+    // reduction partials [4][G][4] floats and [4][G][2] u64, histograms [2][G][256]
+    const size_t nY = (size_t)L, nsig = (size_t)d.G * d.R * (d.S1 + d.S1 / 16);
+    const size_t off_sig = nY * sizeof(float2);
+    const size_t off_bar = off_sig + nsig * sizeof(float2);
+    const size_t off_red = off_bar + 64;
+    const size_t off_red64 = off_red + (size_t)4 * d.G * 4 * sizeof(float);
+    const size_t off_hist = off_red64 + (size_t)4 * d.G * 2 * sizeof(unsigned long long);
+    const size_t total = off_hist + (size_t)2 * d.G * 256 * sizeof(uint32_t);
+    if ((e = cudaMalloc(&op->d_grid, total)) != cudaSuccess) {
+      cuda_fail(e, "cudaMalloc(grid state)");
+      free_op(op);
+      return nullptr;
+    }
+    if ((e = cudaMemset(op->d_grid, 0, total)) != cudaSuccess) {
+      cuda_fail(e, "cudaMemset(grid state)");
+      free_op(op);
+      return nullptr;
+    }
+    unsigned char* b = static_cast<unsigned char*>(op->d_grid);
+    d.gY = reinterpret_cast<float2*>(b);
+    d.gsig = reinterpret_cast<float2*>(b + off_sig);
+    d.gbar = reinterpret_cast<unsigned*>(b + off_bar);
+    d.gerr = reinterpret_cast<int*>(b + off_bar + 8);
+    d.gred = reinterpret_cast<float*>(b + off_red);
+    d.gred64 = reinterpret_cast<unsigned long long*>(b + off_red64);
+    d.ghist = reinterpret_cast<uint32_t*>(b + off_hist);
+    if (!grid_fits(d)) {
+      fail(CS_ERR_UNSUPPORTED_N, "the streamed geometry's cooperative launch does not fit this device");
+      free_op(op);
+      return nullptr;
+    }
+    return op;
+  }
   if (max_active_clusters(P, F) < 1) {
     fail(CS_ERR_UNSUPPORTED_N, "a cluster of " + std::to_string(P) + " CTAs cannot be scheduled on this device");
     free_op(op);
@@ -292,6 +354,7 @@ cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X)
 
 int32_t cs_op_concurrency(cs_op_t op) {
   if (!op) return 1;
+  if (op->dev.grid) return 1;
   return std::max(1, max_active_clusters(op->dev.P, op->dev.F));
 }
 
@@ -338,7 +401,25 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
 // stream-ordered allocator and are released on the same stream.
 static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
   std::map<int, std::vector<Task>> groups;
-  for (const Task& t : tasks) groups[t.op.P].push_back(t);
+  for (const Task& t : tasks) {
+    if (t.op.grid) {   // streamed geometry: the whole GPU per signal, one launch each
+      Launch L{};
+      L.tasks = nullptr;
+      L.single = t;
+      L.ntasks = 1;
+      L.F_alloc = t.op.F;
+      L.plan = grid_plan(t.op);
+      L.scratch = t.grid_scratch;
+      L.scratch_per_cluster = 0;
+      L.bits = t.grid_bits;
+      L.bits_per_cluster = 0;
+      cudaError_t e;
+      if ((e = cudaMemsetAsync(t.op.gerr, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "memset");
+      if ((e = launch_grid(L, t.op.G, stream)) != cudaSuccess) return cuda_fail(e, "grid launch");
+      continue;
+    }
+    groups[t.op.P].push_back(t);
+  }
   for (auto& kv : groups) {
     const int P = kv.first;
     std::vector<Task>& g = kv.second;
@@ -354,6 +435,7 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     Launch L{};
     L.ntasks = (int)g.size();
     L.F_alloc = F_alloc;
+    L.plan = cluster_plan(F_alloc);
     L.scratch_per_cluster = (size_t)P * scratch_floats_per_cta(F_alloc);
     L.bits_per_cluster = (size_t)(Nmax + 31) / 32;
     Task* d_tasks = nullptr;
@@ -555,6 +637,7 @@ extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, c
   L.single = t;
   L.ntasks = 1;
   L.F_alloc = op->dev.F;
+  L.plan = cluster_plan(op->dev.F);
   L.scratch = base;
   L.scratch_per_cluster = (size_t)op->dev.P * scratch_floats_per_cta(op->dev.F);
   L.bits = reinterpret_cast<uint32_t*>(base + NOALLOC_SCRATCH);

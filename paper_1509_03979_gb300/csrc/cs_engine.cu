@@ -343,17 +343,17 @@ struct Bump {
   }
 };
 
-__host__ __device__ inline void layout(int F_alloc, Bump& take, Smem* s) {
-  const int nw = (2 * F_alloc + 31) / 32;
-  const int cap = cg_cap(F_alloc);
-  unsigned char* A = take(sizeof(float2) * apad(F_alloc));
-  unsigned char* B = take(sizeof(float2) * apad(F_alloc));   // also the FFT ping-pong buffer (padded)
-  unsigned char* tl = take(sizeof(float2) * apad(1024));
-  unsigned char* th = take(sizeof(float2) * 1024);
+__host__ __device__ inline void layout(const SmemPlan& pl, Bump& take, Smem* s) {
+  const int nw = pl.slot_words;
+  const int cap = cg_cap(pl.fft_n);
+  unsigned char* A = take(sizeof(float2) * apad(pl.fft_n));
+  unsigned char* B = take(sizeof(float2) * apad(pl.fft_n));   // also the FFT ping-pong buffer (padded)
+  unsigned char* tl = take(sizeof(float2) * apad(pl.tw_lo_n));
+  unsigned char* th = take(sizeof(float2) * pl.tw_hi_n);
   unsigned char* sw = take(4 * nw);
   unsigned char* m0 = take(4 * nw);
   unsigned char* m1 = take(4 * nw);
-  unsigned char* fb = take(F_alloc / 2 + P_MAX + 16);   // ntasks <= F/2 + P + 1
+  unsigned char* fb = take(pl.fb_bytes);
   unsigned char* hi = take(4 * 512);
   unsigned char* ht = take(4 * 256);
   unsigned char* rg = take(4 * 16);
@@ -373,16 +373,40 @@ __host__ __device__ inline void layout(int F_alloc, Bump& take, Smem* s) {
   }
 }
 
-__device__ Smem carve(int F_alloc) {
+__device__ Smem carve(const SmemPlan& pl) {
   Smem s;
   Bump b{smem_raw, 0};
-  layout(F_alloc, b, &s);
+  layout(pl, b, &s);
   return s;
 }
 
-size_t smem_bytes(int F_alloc) {
+// Cluster launches: FFT buffers of F points, twiddle levels of <= 1024 entries (4N <= 2^20),
+// 2F slots, and CTA 0's F/2 + P + 1 frequency tasks.
+SmemPlan cluster_plan(int F_alloc) {
+  SmemPlan p;
+  p.fft_n = F_alloc;
+  p.tw_lo_n = 1024;
+  p.tw_hi_n = 1024;
+  p.slot_words = (2 * F_alloc + 31) / 32;
+  p.fb_bytes = F_alloc / 2 + P_MAX + 16;
+  return p;
+}
+
+// Grid launches: FFT buffers of S1 points (rows and column blocks), the op's twiddle levels,
+// 2 R S1 slots, and the frequency tasks of the CTA's column blocks (each h S2 + S2 + 1).
+SmemPlan grid_plan(const OpDev& op) {
+  SmemPlan p;
+  p.fft_n = op.S1;
+  p.tw_lo_n = 1 << op.lo_bits;
+  p.tw_hi_n = 1 << op.hi_bits;
+  p.slot_words = (2 * op.R * op.S1 + 31) / 32;
+  p.fb_bytes = op.bpc * ((op.W / 2) * op.S2 + op.S2 + 1) + 16;
+  return p;
+}
+
+size_t smem_bytes(const SmemPlan& pl) {
   Bump b{nullptr, 0};
-  layout(F_alloc, b, nullptr);
+  layout(pl, b, nullptr);
   return b.off;
 }
 
@@ -418,6 +442,12 @@ struct Ctx {
   float* cgp;
   float* cgq;
   uint32_t* bits;     // per-cluster N-bit output bitmask
+  // signal-domain values by slot: the FFT buffer A (cluster launches) or the CTA's rows in
+  // global memory (grid launches); slot q lives at (q & rmask) * rowstride + aidx(q >> rshift)
+  float2* sig;
+  int rmask, rshift, rowstride;
+  int grid;           // 0: cluster launch, 1: cooperative grid launch
+  OpDev op;           // the operator (grid launches read its streamed geometry and buffers)
   int ring_slot;      // next cluster-reduction slot (all CTAs advance it identically)
   int hist_slot;      // next radix-histogram buffer
   int cg_total;       // statistics (thread 0 only)
@@ -429,6 +459,60 @@ __shared__ Ctx C;
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
 template <class T>
 __device__ __forceinline__ T* cl_map(T* p, int rank) { return cg::this_cluster().map_shared_rank(p, rank); }
+
+// Bounded software barrier over the CTAs of a cooperative (grid) launch.  The launch guarantees
+// co-residency; a wait that still exceeds GRID_SPIN_LIMIT polls sets CS_ERR_TIMEOUT in the
+// op's status word and continues, and later barriers stop waiting once the status is set, so
+// the launch always ends.
+constexpr unsigned long long GRID_SPIN_LIMIT = 1ull << 26;
+__device__ __noinline__ void grid_sync() {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* count = C.op.gbar;
+    volatile unsigned* gen = C.op.gbar + 1;
+    volatile int* err = C.op.gerr;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == (unsigned)C.op.G - 1u) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(const_cast<unsigned*>(gen), 1u);
+    } else if (*err == 0) {
+      unsigned long long spins = 0;
+      while (*gen == g0) {
+        if (++spins > GRID_SPIN_LIMIT) {
+          atomicExch(const_cast<int*>(err), (int)CS_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Barrier over the CTAs that share one signal: the cluster, or the whole cooperative grid.
+__device__ __forceinline__ void group_sync() {
+  if (C.grid) grid_sync();
+  else cl_sync();
+}
+
+// Signal-domain values by slot (A buffer for clusters, the CTA's global rows for the grid).
+struct SigView {
+  float* base;
+  int rmask, rshift, rowstride;
+  __device__ __forceinline__ float& at(int sg) const {
+    const int q = sg >> 1;
+    return base[2 * ((q & rmask) * rowstride + aidx(q >> rshift)) + (sg & 1)];
+  }
+};
+__device__ __forceinline__ SigView sigview() {
+  SigView v;
+  if (C.grid) { v.base = reinterpret_cast<float*>(C.sig); v.rmask = C.rmask; v.rshift = C.rshift; v.rowstride = C.rowstride; }
+  else { v.base = reinterpret_cast<float*>(shp(C.sm.A)); v.rmask = 0; v.rshift = 0; v.rowstride = 0; }
+  return v;
+}
 
 __device__ __forceinline__ float& slot_ref(float2* A, int sigma) {
   return reinterpret_cast<float*>(A)[2 * aidx(sigma >> 1) + (sigma & 1)];
@@ -502,6 +586,15 @@ __device__ __forceinline__ int pair_outputs(const Geo& g, int k, bool self, int*
   return 4;
 }
 
+// Geometry of column block b in the frequency-stage conventions: P = S2 column-FFT outputs,
+// F = S1 (Q), 2h = W slots, block index in the role of the CTA rank.
+__device__ __forceinline__ Geo block_geo(const OpDev& op, int b) {
+  Geo gb;
+  gb.N = op.N; gb.L = op.N >> 1; gb.P = op.S2; gb.F = op.S1;
+  gb.h = op.W >> 1; gb.lh = __ffs(gb.h) - 1; gb.S2 = op.W; gb.c = b; gb.four_n = 4 * op.N;
+  return gb;
+}
+
 // ---------------------------------------------------------------- cluster-wide reductions
 // Sum n (<= 4) per-thread values over the whole cluster; every thread gets the totals, and
 // every CTA adds the partials in rank order, so all CTAs hold bit-identical results.
@@ -515,19 +608,27 @@ __device__ __noinline__ void cluster_sum(float* v, int n) {
   const int slot = C.ring_slot;                    // read by every thread before the barrier
   __syncthreads();
   float* ring = shp(C.sm.ring) + 4 * slot;
+  const bool grid = C.grid;
+  const int G = C.g.P;
+  float* gred = grid ? C.op.gred + (size_t)slot * G * 4 : nullptr;
   if (threadIdx.x < n) {
     float t = 0.f;
     for (int w = 0; w < NT / 32; ++w) t += wsum[threadIdx.x * 16 + w];
-    ring[threadIdx.x] = t;
+    if (grid) gred[C.g.c * 4 + threadIdx.x] = t;
+    else ring[threadIdx.x] = t;
   }
   if (threadIdx.x == 0) C.ring_slot = (slot + 1) & 3;   // next reader is past the barriers below
-  cl_sync();
+  group_sync();
   float* fscr = shp(C.sm.fscr);
   if (warp == 0) {
     for (int i = 0; i < n; ++i) {
       float t = 0.f;
-      if (lane < C.g.P) t = *cl_map(ring + i, lane);
-      // fixed-shape tree over 32 lanes: identical order in every CTA
+      if (grid) {
+        for (int r = lane; r < G; r += 32) t += __ldcg(gred + r * 4 + i);
+      } else if (lane < G) {
+        t = *cl_map(ring + i, lane);
+      }
+      // fixed lane assignment and fixed-shape tree: identical order in every CTA
       t = warp_sum(t);
       if (lane == 0) fscr[i] = t;
     }
@@ -547,18 +648,26 @@ __device__ __noinline__ void cluster_max64(unsigned long long* v, int n) {
   const int slot = C.ring_slot;
   __syncthreads();
   unsigned long long* ring = shp(C.sm.ring64) + 2 * slot;
+  const bool grid = C.grid;
+  const int G = C.g.P;
+  unsigned long long* gred = grid ? C.op.gred64 + (size_t)slot * G * 2 : nullptr;
   if (threadIdx.x < n) {
     unsigned long long t = 0;
     for (int w = 0; w < NT / 32; ++w) t = max(t, wmax[threadIdx.x * 16 + w]);
-    ring[threadIdx.x] = t;
+    if (grid) gred[C.g.c * 2 + threadIdx.x] = t;
+    else ring[threadIdx.x] = t;
   }
   if (threadIdx.x == 0) C.ring_slot = (slot + 1) & 3;
-  cl_sync();
+  group_sync();
   int* iscr = shp(C.sm.iscr);
   if (warp == 0) {
     for (int i = 0; i < n; ++i) {
       unsigned long long t = 0;
-      if (lane < C.g.P) t = *cl_map(ring + i, lane);
+      if (grid) {
+        for (int r = lane; r < G; r += 32) t = max(t, __ldcg(gred + r * 2 + i));
+      } else if (lane < G) {
+        t = *cl_map(ring + i, lane);
+      }
       t = warp_max64(t);
       if (lane == 0) iscr[2 * i] = (int)(t & 0xffffffffu), iscr[2 * i + 1] = (int)(t >> 32);
     }
@@ -642,6 +751,29 @@ __device__ __noinline__ int build_list(const uint32_t* m) {
 
 // Omega membership bits of every frequency task of this CTA (bit i <-> output f[i]).
 __device__ __noinline__ void build_fbits() {
+  if (C.grid) {
+    // one table per column block of this CTA, each of h S2 + S2 + 1 entries
+    const OpDev& op = C.op;
+    const int fbstride = (op.W / 2) * op.S2 + op.S2 + 1;
+    for (int j = 0; j < op.bpc; ++j) {
+      const Geo gb = block_geo(op, C.g.c + j * op.G);
+      uint8_t* fb = shp(C.sm.fbits) + j * fbstride;
+      const int nt = ntasks(gb);
+      for (int t = threadIdx.x; t < nt; t += NT) {
+        int sa, kpa, sb, kpb;
+        uint8_t bits = 0;
+        if (task_pair(gb, t, sa, kpa, sb, kpb)) {
+          const int k = kq_of(gb, sa) + gb.F * kpa;
+          int f[4];
+          const int nf = pair_outputs(gb, k, sa == sb && kpa == kpb, f);
+          for (int i = 0; i < nf; ++i) bits |= (uint8_t)(((C.omask[f[i] >> 5] >> (f[i] & 31)) & 1u) << i);
+        }
+        fb[t] = bits;
+      }
+    }
+    __syncthreads();
+    return;
+  }
   const Geo g = C.g;
   uint8_t* fb = shp(C.sm.fbits);
   const int nt = ntasks(g);
@@ -728,11 +860,9 @@ __device__ __noinline__ void exchange_fwd() {
 
 // Frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, and DCT-III
 // pre-processing back into the pair.  Returns this thread's MID_RESID sum of squares.
-__device__ __noinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
-  const Geo g = C.g;
+__device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, int kind, bool fwd_done,
+                                           bool inv, const float* vin, float* vout) {
   const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
-  float2* B = shp(C.sm.B);
-  const uint8_t* fb = shp(C.sm.fbits);
   const uint32_t* omask = C.omask;
   const int32_t* orank = C.orank;
   const int F = g.F, S2 = g.S2;
@@ -806,6 +936,11 @@ __device__ __noinline__ float freq_half(int kind, bool fwd_done, bool inv, const
   return acc;
 }
 
+__device__ __noinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
+  const Geo g = C.g;
+  return freq_core(g, shp(C.sm.B), shp(C.sm.fbits), kind, fwd_done, inv, vin, vout);
+}
+
 // Inverse exchange: P-point inverse DFT per column, cluster barrier, all-to-all pull back into
 // the stride-P layout with conj(omega_L^{c k}).  The twiddle of element
 // k = k0 + e NT is conj(omega_L^{c k0}) * conj(omega_L^{c NT})^e: one strided lookup per
@@ -850,6 +985,186 @@ __device__ __noinline__ void exchange_inv() {
   __syncthreads();
 }
 
+// ------------------------------------------------------ streamed transform (grid launches)
+// L = S1 S2 with rows of S1 points: z[m] with m = S2 n1 + n2 is element (n2, n1).  Pass 1 runs
+// the S1-point FFT of each row and multiplies by omega_L^{n2 k1}; pass 2 runs the S2-point
+// FFT of each column k1, so Z[k1 + S1 k2] = column k1, entry k2.  Columns are processed in
+// blocks of W that pair k1 with its mirror S1 - k1 (the same assignment as the cluster
+// layout, with the block index in the role of the CTA rank), so the DCT post-/pre-processing
+// of every pair (k, L - k) stays inside one block.  Intermediate rows live in global memory
+// (L2-resident), signal-domain rows in each CTA's own global rows.
+
+// One out-of-place Stockham pass over the first index of a [Lc][W] array (W contiguous).
+template <int R, int DIR>
+__device__ __forceinline__ void col_pass(const float2* X, float2* Y, int Lc, int lw, int Ns, const Tw& tw, int four_n) {
+  const int W = 1 << lw;
+  const int nb = Lc / R;
+  const int total = nb << lw;
+  for (int t = threadIdx.x; t < total; t += NT) {
+    const int sidx = t & (W - 1), j = t >> lw;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = X[((j + r * nb) << lw) + sidx];
+    const int k = j & (Ns - 1);
+    if (Ns > 1) twiddle_powers<R, DIR>(v, tw, k * (four_n / (Ns * R)));
+    dft<R, DIR>(v);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) Y[((base + r * Ns) << lw) + sidx] = v[r];
+  }
+  __syncthreads();
+}
+
+template <int LOGL, int DIR, int LOGNS, bool TO_Y>
+__device__ __forceinline__ void col_rest(float2* X, float2* Y, int lw, const Tw& tw, int four_n) {
+  if constexpr (LOGNS < LOGL) {
+    if constexpr (TO_Y) col_pass<16, DIR>(X, Y, 1 << LOGL, lw, 1 << LOGNS, tw, four_n);
+    else col_pass<16, DIR>(Y, X, 1 << LOGL, lw, 1 << LOGNS, tw, four_n);
+    col_rest<LOGL, DIR, LOGNS + 4, !TO_Y>(X, Y, lw, tw, four_n);
+  } else if constexpr (!TO_Y) {
+    // odd number of passes: the result is in Y, copy it back to X
+    const int n = (1 << LOGL) << lw;
+    for (int i = threadIdx.x; i < n; i += NT) X[i] = Y[i];
+    __syncthreads();
+  }
+}
+
+// Batched FFT of length Lc = 2^LOGL along the first index of X [Lc][W]; Y is scratch.
+template <int LOGL, int DIR>
+__device__ __forceinline__ void col_plan(float2* X, float2* Y, int lw, const Tw& tw, int four_n) {
+  constexpr int HEAD = LOGL % 4;
+  constexpr int R0 = HEAD == 0 ? 16 : (1 << HEAD);
+  col_pass<R0, DIR>(X, Y, 1 << LOGL, lw, 1, tw, four_n);
+  col_rest<LOGL, DIR, (HEAD ? HEAD : 4), false>(X, Y, lw, tw, four_n);
+}
+
+template <int DIR>
+__device__ __noinline__ void col_fft(float2* X, float2* Y, int Lc, int lw, Tw tw, int four_n) {
+  X = shp(X);
+  Y = shp(Y);
+  tw.lo = shp(tw.lo);
+  tw.hi = shp(tw.hi);
+  switch (__ffs(Lc) - 1) {
+    case 5: col_plan<5, DIR>(X, Y, lw, tw, four_n); break;
+    case 6: col_plan<6, DIR>(X, Y, lw, tw, four_n); break;
+    case 7: col_plan<7, DIR>(X, Y, lw, tw, four_n); break;
+    case 8: col_plan<8, DIR>(X, Y, lw, tw, four_n); break;
+    case 9: col_plan<9, DIR>(X, Y, lw, tw, four_n); break;
+    default: col_plan<10, DIR>(X, Y, lw, tw, four_n); break;
+  }
+}
+
+// Pass 1, forward, row lr of this CTA (n2 = c + lr G): build the row from the source, FFT,
+// multiply by omega_L^{n2 k1} and store it.  Element k1 = k0 + e NT uses
+// omega_L^{n2 k0} (omega_L^{n2 NT})^e: one strided lookup per thread plus broadcast powers.
+__device__ __noinline__ void grid_row_forward(int lr, int src, int nloc, const float* dense, const float* gin) {
+  const Geo g = C.g;
+  const int S1 = C.op.S1, R = C.op.R, n2 = g.c + lr * C.op.G;
+  const int rmask = C.rmask, rshift = C.rshift;
+  float2* X = shp(C.sm.A);
+  const uint32_t* signw = shp(C.sm.signw);
+  if (src == SRC_GLOBAL_N) {
+    for (int n1 = threadIdx.x; n1 < S1; n1 += NT) {
+      const int q = n1 * R + lr;
+      X[aidx(n1)] = make_float2(gin[n_of_slot(g, 2 * q)] * sgn_bits(signw, 2 * q),
+                                gin[n_of_slot(g, 2 * q + 1)] * sgn_bits(signw, 2 * q + 1));
+    }
+  } else {
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4* X4 = reinterpret_cast<float4*>(X);
+    for (int q = threadIdx.x; q < apad(S1) / 2; q += NT) X4[q] = z4;
+    __syncthreads();
+    const int* list = C.list;
+    const float* vals = src == SRC_CG ? C.cgp : dense;
+    for (int i = threadIdx.x; i < nloc; i += NT) {
+      const int sg = list[i];
+      const int q = sg >> 1;
+      if ((q & rmask) != lr) continue;
+      const float v = (src == SRC_CG ? vals[i] : vals[sg]) * sgn_bits(signw, sg);
+      reinterpret_cast<float*>(X)[2 * aidx(q >> rshift) + (sg & 1)] = v;
+    }
+  }
+  __syncthreads();
+  local_fft<-1>(C.sm.A, C.sm.B, S1, C.tw, g.four_n);
+  {
+    const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+    float2* row = C.op.gY + (size_t)n2 * S1;
+    float2 w = tw.get<-1>(8 * n2 * (int)threadIdx.x);
+    const float2 step = tw.get<-1>(8 * n2 * NT);
+    for (int k1 = threadIdx.x; k1 < S1; k1 += NT) {
+      row[k1] = cmul(X[aidx(k1)], w);
+      w = cmul(w, step);
+    }
+  }
+  __syncthreads();
+}
+
+// Pass 2 for column block j of this CTA: load, column FFT, frequency stage, inverse column FFT,
+// store.  Returns this thread's MID_RESID partial.
+__device__ __noinline__ float grid_col_block(int j, int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
+  const OpDev& op = C.op;
+  const Geo gb = block_geo(op, C.g.c + j * op.G);
+  const int S1 = op.S1, S2 = op.S2, W = op.W, lw = __ffs(W) - 1;
+  float2* X = shp(C.sm.A);
+  if (fwd_done) {
+    for (int idx = threadIdx.x; idx < (S2 << lw); idx += NT) {
+      const int n2 = idx >> lw, sidx = idx & (W - 1);
+      X[idx] = __ldcg(op.gY + (size_t)n2 * S1 + kq_of(gb, sidx));
+    }
+    __syncthreads();
+    col_fft<-1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
+  }
+  const int fbstride = (W / 2) * S2 + S2 + 1;
+  const float acc = freq_core(gb, X, shp(C.sm.fbits) + j * fbstride, kind, fwd_done, inv, vin, vout);
+  __syncthreads();
+  if (inv) {
+    col_fft<1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
+    for (int idx = threadIdx.x; idx < (S2 << lw); idx += NT) {
+      const int n2 = idx >> lw, sidx = idx & (W - 1);
+      op.gY[(size_t)n2 * S1 + kq_of(gb, sidx)] = X[idx];
+    }
+  }
+  __syncthreads();
+  return acc;
+}
+
+// Pass 1, inverse, row lr: load with conj(omega_L^{n2 k1}), inverse FFT, store the row of
+// signal-domain values into this CTA's rows (slot q = n1 R + lr).
+__device__ __noinline__ void grid_row_inverse(int lr) {
+  const Geo g = C.g;
+  const int S1 = C.op.S1, n2 = g.c + lr * C.op.G;
+  float2* X = shp(C.sm.A);
+  {
+    const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+    const float2* row = C.op.gY + (size_t)n2 * S1;
+    float2 w = tw.get<1>(8 * n2 * (int)threadIdx.x);
+    const float2 step = tw.get<1>(8 * n2 * NT);
+    for (int k1 = threadIdx.x; k1 < S1; k1 += NT) {
+      X[aidx(k1)] = cmul(__ldcg(row + k1), w);
+      w = cmul(w, step);
+    }
+  }
+  __syncthreads();
+  local_fft<1>(C.sm.A, C.sm.B, S1, C.tw, g.four_n);
+  float2* sig = C.sig + (size_t)lr * C.rowstride;
+  for (int n1 = threadIdx.x; n1 < S1; n1 += NT) sig[aidx(n1)] = X[aidx(n1)];
+  __syncthreads();
+}
+
+__device__ __noinline__ float transform_grid(int src, int nloc, const float* dense, const float* gin, int kind, bool inv,
+                                             const float* vin, float* vout) {
+  if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
+  if (src != SRC_NONE)
+    for (int lr = 0; lr < C.op.R; ++lr) grid_row_forward(lr, src, nloc, dense, gin);
+  grid_sync();                                      // every row of pass 1 is stored
+  float acc = 0.f;
+  for (int j = 0; j < C.op.bpc; ++j) acc += grid_col_block(j, kind, src != SRC_NONE, inv, vin, vout);
+  grid_sync();                                      // every column block is stored
+  if (inv)
+    for (int lr = 0; lr < C.op.R; ++lr) grid_row_inverse(lr);
+  return acc;
+}
+
 // One application of A (forward), A^T (inverse) or A^T mask A, driven by src / kind.
 //   src   SRC_NONE: the forward input is zero (skip the forward transform)
 //         SRC_CG: compressed CG vector cgp on the local list (nloc entries)
@@ -861,6 +1176,7 @@ __device__ __noinline__ void exchange_inv() {
 // Returns this thread's sum of squares of the MID_RESID residual.
 __device__ __noinline__ float transform(int src, int nloc, const float* dense, const float* gin, int kind,
                                         bool inv, const float* vin, float* vout) {
+  if (C.grid) return transform_grid(src, nloc, dense, gin, kind, inv, vin, vout);
   // Each step is its own call and this function holds almost nothing live across them, so
   // every step gets the full register budget (ptxas allocates registers across calls).
   if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
@@ -907,10 +1223,21 @@ __device__ void radix_select(int count, int K, KeyFn key, uint32_t* tau, int* ne
       const uint32_t kk = key(i);
       if (kk != 0u && (kk & pmask) == prefix) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
     }
-    cl_sync();
+    const bool grid = C.grid;
+    const int G = C.g.P;
+    uint32_t* gh = grid ? C.op.ghist + (size_t)hs * G * 256 : nullptr;
+    if (grid) {
+      __syncthreads();
+      if (threadIdx.x < 256) gh[C.g.c * 256 + threadIdx.x] = hist[threadIdx.x];
+    }
+    group_sync();
     if (threadIdx.x < 256) {
       uint32_t t = 0;
-      for (int r = 0; r < C.g.P; ++r) t += *cl_map(hist + threadIdx.x, r);
+      if (grid) {
+        for (int r = 0; r < G; ++r) t += __ldcg(gh + r * 256 + threadIdx.x);
+      } else {
+        for (int r = 0; r < G; ++r) t += *cl_map(hist + threadIdx.x, r);
+      }
       htot[threadIdx.x] = t;
     }
     __syncthreads();
@@ -993,9 +1320,9 @@ __device__ void select_topk(int count, int K, KeyFn key, IdxFn nidx, MarkFn mark
 
 __device__ __forceinline__ uint32_t abs_key(float v) { return (__float_as_uint(v) & 0x7fffffffu) + 1u; }
 
-// Correlation c(sigma) = d_n (C^T ...)_n held in the A buffer.
-__device__ __forceinline__ float corr_at(const float2* A, const uint32_t* signw, int sg) {
-  return slot_ref(const_cast<float2*>(A), sg) * sgn_bits(signw, sg);
+// Correlation c(sigma) = d_n (C^T ...)_n held in the signal buffer.
+__device__ __forceinline__ float corr_at(const SigView& sv, const uint32_t* signw, int sg) {
+  return sv.at(sg) * sgn_bits(signw, sg);
 }
 
 // ------------------------------------------------------------------------------------ CG
@@ -1009,7 +1336,7 @@ enum R0Src : int { R0_FROM_A = 0, R0_FROM_CY = 1 };
 __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, float tol, int maxit) {
   float* xd = C.xd[wi];
   const float* cy = C.cy;
-  const float2* A = shp(C.sm.A);
+  const SigView A = sigview();
   const uint32_t* signw = shp(C.sm.signw);
   const int* list = C.list;
   float* cgx = C.cgx;
@@ -1034,7 +1361,7 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
   while (it < maxit && rr > stop2) {
     transform(SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
     // pointers are re-read from the context after the call (nothing held live across it)
-    const float2* Ax = shp(C.sm.A);
+    const SigView Ax = sigview();
     const uint32_t* sw = shp(C.sm.signw);
     const int* li = C.list;
     float* px = C.cgx;
@@ -1095,7 +1422,7 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
     const int w = g.c * wper + i;
     if (w < W) C.bits[w] = 0u;
   }
-  cl_sync();
+  group_sync();
   {
     const int* list = C.list;
     const float* xd = C.xd[wi];
@@ -1106,12 +1433,12 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
       atomicOr(&C.bits[n >> 5], 1u << (n & 31));
     }
   }
-  cl_sync();
+  group_sync();
   // sorted support: CTA c compacts words [c wper, (c+1) wper)
   int cnt = 0;
   for (int i = threadIdx.x; i < wper; i += NT) {
     const int w = g.c * wper + i;
-    if (w < W) cnt += __popc(C.bits[w]);
+    if (w < W) cnt += __popc(__ldcg(C.bits + w));   // written by other CTAs' atomics
   }
   float fc = (float)cnt;   // counts < 2^24: exact in FP32
   float* ring = shp(C.sm.ring);
@@ -1123,15 +1450,18 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
     if (lane == 0) wsum[warp] = s;
     __syncthreads();
     const int slot = C.ring_slot;   // only thread 0 uses and advances it here
+    const bool grid = C.grid;
+    float* gred = grid ? C.op.gred + (size_t)slot * P * 4 : nullptr;
     if (threadIdx.x == 0) {
       float tt = 0.f;
       for (int w = 0; w < NT / 32; ++w) tt += wsum[w];
-      ring[4 * slot] = tt;
+      if (grid) gred[g.c * 4] = tt;
+      else ring[4 * slot] = tt;
     }
-    cl_sync();
+    group_sync();
     if (threadIdx.x == 0) {
       float off = 0.f;
-      for (int r = 0; r < g.c; ++r) off += *cl_map(ring + 4 * slot, r);
+      for (int r = 0; r < g.c; ++r) off += grid ? __ldcg(gred + r * 4) : *cl_map(ring + 4 * slot, r);
       iscr[40] = (int)off;
       C.ring_slot = (slot + 1) & 3;
     }
@@ -1142,7 +1472,7 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
   // block-ordered compaction: wper words per CTA, processed NT at a time
   for (int w0 = 0; w0 < wper; w0 += NT) {
     const int w = g.c * wper + w0 + threadIdx.x;
-    const uint32_t word = (w0 + threadIdx.x < wper && w < W) ? C.bits[w] : 0u;
+    const uint32_t word = (w0 + threadIdx.x < wper && w < W) ? __ldcg(C.bits + w) : 0u;
     int tot;
     int off = base + block_scan(__popc(word), &tot);
     uint32_t b = word;
@@ -1162,7 +1492,7 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
     st.near_ties = 0;
     st.final_resid = sqrtf(rn2);
     st.min_margin = -1.f;
-    st.status = CS_OK;
+    st.status = C.grid ? *(volatile int*)C.op.gerr : CS_OK;
     st.transforms = C.ntrans;
     *t.stats = st;
   }
@@ -1171,7 +1501,7 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
 // A^T y into cy (dense by slot, signed) and the A buffer; returns ||y||^2.
 __device__ __noinline__ float init_correlation(const float* y) {
   float v = transform(SRC_NONE, 0, nullptr, nullptr, MID_RESID, true, y, nullptr);
-  const float2* A = shp(C.sm.A);
+  const SigView A = sigview();
   const uint32_t* signw = shp(C.sm.signw);
   float* cy = C.cy;
   for (int sg = threadIdx.x; sg < 2 * C.g.F; sg += NT) cy[sg] = corr_at(A, signw, sg);
@@ -1187,12 +1517,12 @@ __device__ void zero_mask(uint32_t* m) {
 // Top-K of |c| over the local slots not in `excl` (may be null); marks into `dst`.
 __device__ __noinline__ void topk_corr(int K, const uint32_t* excl, uint32_t* dst) {
   const Geo g = C.g;
-  float2* A = shp(C.sm.A);
+  const SigView A = sigview();
   select_topk(
       2 * g.F, K,
       [&](int sg) -> uint32_t {
         if (excl && mask_bit(excl, sg)) return 0u;
-        return abs_key(slot_ref(A, sg));
+        return abs_key(A.at(sg));
       },
       [&](int sg) { return n_of_slot(g, sg); },
       [&](int sg) { atomicOr(&dst[sg >> 5], 1u << (sg & 31)); });
@@ -1203,11 +1533,11 @@ __device__ __noinline__ void topk_corr(int K, const uint32_t* excl, uint32_t* ds
 // zeroes its slot of the warm-start vector.
 __device__ __noinline__ int omp_select(uint32_t* mA) {
   const Geo g = C.g;
-  const float2* A = shp(C.sm.A);
+  const SigView A = sigview();
   unsigned long long key = 0;
   for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
     if (mask_bit(mA, sg)) continue;
-    const unsigned long long kk = ((unsigned long long)abs_key(slot_ref(const_cast<float2*>(A), sg)) << 32) |
+    const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) |
                                   (0xffffffffu - (uint32_t)n_of_slot(g, sg));
     key = kk > key ? kk : key;
   }
@@ -1314,7 +1644,7 @@ __device__ __noinline__ void run_sp(const Task& t) {
 // slots of the warm-start vector and returns true; otherwise returns false.
 __device__ __noinline__ bool ompr_swap() {
   const Geo g = C.g;
-  const float2* A = shp(C.sm.A);
+  const SigView A = sigview();
   const uint32_t* signw = shp(C.sm.signw);
   uint32_t* mA = shp(C.sm.mask[0]);
   unsigned long long key[2] = {0ull, 0ull};
@@ -1429,15 +1759,25 @@ __device__ __noinline__ void run_ls_backward(const Task& t) {
 // allocates registers across calls: whatever a caller holds live is denied to its callees).
 __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc) {
   const OpDev& op = tp->op;
-  if (op.P != P || op.F > F_alloc) {   // host grouping error: skip uniformly
+  if (op.P != P || op.F > F_alloc || op.grid != C.grid) {   // host grouping error: skip uniformly
     if (c == 0 && threadIdx.x == 0 && tp->stats) tp->stats->status = CS_ERR_INVALID_ARG;
     return;
   }
   const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
-  if (threadIdx.x == 0) {   // every CTA thread passed the previous task's cluster barrier
+  if (threadIdx.x == 0) {   // every CTA thread passed the previous task's barrier
     Geo& g = C.g;
     g.N = op.N; g.L = op.N >> 1; g.P = P; g.F = op.F; g.c = c;
     g.h = op.F / (2 * P); g.lh = __ffs(g.h) - 1; g.S2 = 2 * g.h; g.four_n = 4 * op.N;
+    C.op = op;
+    if (C.grid) {
+      // CTA c owns rows c + lr G (lr < R); slot q = n1 R + lr is point m = q G + c, as in a
+      // cluster of G CTAs holding F = R S1 points each
+      g.h = 1; g.lh = 0; g.S2 = 2;   // not used by the streamed transform
+      C.sig = op.gsig + (size_t)c * op.R * apad(op.S1);
+      C.rmask = op.R - 1;
+      C.rshift = __ffs(op.R) - 1;
+      C.rowstride = apad(op.S1);
+    }
     C.M = op.M;
     C.nwords = (2 * op.F + 31) / 32;
     C.omask = op.omask; C.orank = op.orank;
@@ -1479,7 +1819,7 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
       break;
     case MODE_APPLY_T: {
       transform(SRC_NONE, 0, nullptr, nullptr, MID_IN, true, t.in, nullptr);
-      const float2* A = shp(C.sm.A);
+      const SigView A = sigview();
       const uint32_t* signw = shp(C.sm.signw);
       const Geo gg = C.g;
       for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[n_of_slot(gg, sg)] = corr_at(A, signw, sg);
@@ -1503,7 +1843,8 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   const int cid = blockIdx.x / P;
   const int ncl = gridDim.x / P;
   if (threadIdx.x == 0) {
-    C.sm = carve(lp.F_alloc);
+    C.sm = carve(lp.plan);
+    C.grid = 0;
     C.ring_slot = 0;
     C.hist_slot = 0;
     C.cap = cg_cap(lp.F_alloc);
@@ -1523,8 +1864,36 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   }
 }
 
+// Cooperative launch of G CTAs (one per SM, co-resident) that process one signal of the
+// streamed geometry; the task list is walked one task at a time by the whole grid.
+__global__ void __launch_bounds__(NT, 1) grid_kernel(const Launch lp) {
+  const int G = gridDim.x;
+  const int c = blockIdx.x;
+  if (threadIdx.x == 0) {
+    C.sm = carve(lp.plan);
+    C.grid = 1;
+    C.ring_slot = 0;
+    C.hist_slot = 0;
+    C.cap = cg_cap(lp.F_alloc);
+    float* base = lp.scratch + (size_t)c * scratch_floats_per_cta(lp.F_alloc);
+    const size_t a = 2 * (size_t)lp.F_alloc;
+    C.xd[0] = base;
+    C.xd[1] = base + a;
+    C.cy = base + 2 * a;
+    C.glist = reinterpret_cast<int*>(base + 3 * a);
+    C.gcg = base + 4 * a;
+    C.bits = lp.bits;
+    C.op = lp.tasks ? lp.tasks[0].op : lp.single.op;   // barrier state for the first task
+  }
+  __syncthreads();
+  for (int ti = 0; ti < lp.ntasks; ++ti) {
+    run_task(lp.tasks ? lp.tasks + ti : &lp.single, G, c, lp.F_alloc);
+    grid_sync();
+  }
+}
+
 cudaError_t launch_engine(const Launch& L, int P, int num_clusters, cudaStream_t stream) {
-  const size_t smem = smem_bytes(L.F_alloc);
+  const size_t smem = smem_bytes(L.plan);
   cudaError_t e = cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (P > 8) {
@@ -1547,7 +1916,7 @@ cudaError_t launch_engine(const Launch& L, int P, int num_clusters, cudaStream_t
 }
 
 int max_active_clusters(int P, int F_alloc) {
-  const size_t smem = smem_bytes(F_alloc);
+  const size_t smem = smem_bytes(cluster_plan(F_alloc));
   if (cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   if (P > 8 && cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
@@ -1569,6 +1938,37 @@ int max_active_clusters(int P, int F_alloc) {
     return 0;
   }
   return n;
+}
+
+cudaError_t launch_grid(const Launch& L, int G, cudaStream_t stream) {
+  const size_t smem = smem_bytes(L.plan);
+  cudaError_t e = cudaFuncSetAttribute(grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, grid_kernel, L);
+}
+
+int grid_fits(const OpDev& op) {
+  const size_t smem = smem_bytes(grid_plan(op));
+  if (smem > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_kernel, NT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms >= op.G ? 1 : 0;
 }
 
 }  // namespace csg

@@ -15,6 +15,22 @@ constexpr int P_MAX = 16;           // CTAs per cluster (non-portable size 16 on
 constexpr int N_MIN = 16;
 constexpr int N_MAX = 2 * F_MAX * P_MAX;   // 2^18: the largest N one cluster holds on chip
 constexpr int SCRATCH_ARRAYS = 8;   // per-CTA global arrays of 2F words (see Scratch below)
+// Streamed ("grid") geometry for N > N_MAX: the L = N/2 point FFT is split into S2 rows of
+// S1 = GRID_S1 points; G = min(GRID_G_MAX, S2) CTAs of one cooperative launch own R = S2/G
+// rows each, and a second pass runs S2-point column FFTs over blocks of W columns.
+constexpr int GRID_S1 = 4096;
+constexpr int GRID_G_MAX = 128;
+constexpr int GRID_BLOCK = 4096;    // complex points per column block (W = GRID_BLOCK / S2)
+constexpr int N_MAX_GRID = 1 << 22;
+
+// Shared-memory sizing of one launch.
+struct SmemPlan {
+  int fft_n;        // complex points of each FFT buffer (A, B)
+  int tw_lo_n;      // entries of the low twiddle table
+  int tw_hi_n;      // entries of the high twiddle table
+  int slot_words;   // 32-bit words of each per-slot bitmask (2F slots)
+  int fb_bytes;     // Omega bits of the CTA's frequency tasks
+};
 
 enum Mode : int {
   MODE_APPLY = 0,        // out[M] = A in[N]
@@ -33,6 +49,16 @@ struct OpDev {
   const uint32_t* omask;     // [N/32] bitmask of Omega
   const int32_t* orank;      // [N/32] number of Omega members below word w
   const float2* tw;          // [2^lo_bits] then [2^hi_bits]: omega_{4N}^j = lo[j & m] * hi[j >> lo]
+  // streamed geometry (grid != 0 only)
+  int grid;
+  int S1, S2, G, R, W, NB, bpc;  // row length, rows, CTAs, rows per CTA, block width, blocks, blocks per CTA
+  float2* gY;                // [S2][S1] row-major intermediate between the two passes
+  float2* gsig;              // [G][R][apad(S1)] signal-domain rows owned by each CTA
+  unsigned* gbar;            // [2] grid barrier: arrival count, generation
+  int* gerr;                 // device-side status of the last grid launch (0 = ok)
+  float* gred;               // [4][G][4] reduction partials
+  unsigned long long* gred64;   // [4][G][2]
+  uint32_t* ghist;           // [2][G][256] radix histograms
 };
 
 // One unit of work for a cluster.
@@ -49,6 +75,8 @@ struct Task {
   float* out;
   int32_t* supp_out;         // [K] (recover)
   cs_stats* stats;           // device, may be null
+  float* grid_scratch;       // streamed geometry: the op's own scratch and output bitmask
+  uint32_t* grid_bits;
 };
 
 // Kernel launch parameters (passed by value).
@@ -56,7 +84,8 @@ struct Launch {
   const Task* tasks;         // device array, or null when ntasks == 1 (then `single` is used)
   Task single;
   int ntasks;
-  int F_alloc;               // shared-memory sizing (max F over the tasks)
+  int F_alloc;               // scratch strides (max F over the tasks)
+  SmemPlan plan;             // shared-memory sizing
   float* scratch;            // per cluster: P_MAX-strided per-CTA arrays, see scratch_floats()
   size_t scratch_per_cluster;   // floats
   uint32_t* bits;            // per cluster: N_MAX/32 words for the sorted support output
@@ -66,8 +95,12 @@ struct Launch {
 // Per-CTA global scratch: SCRATCH_ARRAYS arrays of 2*F_alloc 32-bit words.
 __host__ __device__ inline size_t scratch_floats_per_cta(int F_alloc) { return (size_t)SCRATCH_ARRAYS * 2 * F_alloc; }
 
-size_t smem_bytes(int F_alloc);
+SmemPlan cluster_plan(int F_alloc);
+SmemPlan grid_plan(const OpDev& op);
+size_t smem_bytes(const SmemPlan& plan);
 cudaError_t launch_engine(const Launch& L, int P, int num_clusters, cudaStream_t stream);
+cudaError_t launch_grid(const Launch& L, int G, cudaStream_t stream);
 int max_active_clusters(int P, int F_alloc);   // 0 if the configuration cannot be scheduled
+int grid_fits(const OpDev& op);                // 1 if a cooperative launch of G CTAs fits
 
 }  // namespace csg
