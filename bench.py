@@ -40,8 +40,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="signals per GPU per step (0 = fill the GPU)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-batch", type=int, default=256)
-    ap.add_argument("--workload", default="sp18", choices=["sp18", "batched"],
-                    help="sp18: SP at N=2^18 (default); batched: mixed-size batch vs a loop of single calls")
+    ap.add_argument("--workload", default="sp18", choices=["sp18", "batched", "ompr22", "ls16"],
+                    help="sp18: SP at N=2^18 (default); batched: mixed-size batch vs a loop of single "
+                         "calls; ompr22: OMPR at N=2^22; ls16: differentiable LS, 32 signals at N=2^16")
     ap.add_argument("--batched-count", type=int, default=256)
     return ap.parse_args()
 
@@ -413,6 +414,71 @@ def run_batched(args, rank, world, local_rank):
         }), flush=True)
 
 
+# ------------------------------------------------------------------- single-signal workloads
+def run_single_workload(args, rank, world, local_rank):
+    """ompr22: OMPR + CG-LS at N = 2^22, M = 2^20, K = 83886, power-law signal (one recovery per
+    step, the whole GPU per signal).  ls16: forward LS solve + hand-written adjoint for 32
+    signals at N = 2^16, M = 2^14, k = 1024 (one step = both batched launches)."""
+    import torch
+    from paper_1509_03979_gb300 import binding
+
+    torch.cuda.set_device(local_rank)
+    devc = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    if args.workload == "ompr22":
+        p = synth.workload(3)
+        op = binding.Operator(p.N, p.M, p.op_seed)
+        s = torch.from_numpy(p.signal().astype(np.float32)).to(devc)
+        y = op.apply(s).contiguous()
+        s_out = torch.empty(p.N, device=devc)
+        k_out = torch.empty(p.K, dtype=torch.int32, device=devc)
+
+        def step():
+            op.recover(y, p.K, "ompr", CG_TOL, CG_MAXIT, s_out, k_out)
+        units, unit, metric = 1, "recoveries/s", "recoveries/s (OMPR + CG-LS, N=2^22)"
+        cfgname = "OMPR+CG-LS N=2^22 M=2^20 K=83886 power-law (config 3)"
+    else:
+        p = synth.workload(5)
+        op = binding.Operator(p.N, p.M, p.op_seed)
+        Bn = 32
+        g = np.random.default_rng(5)
+        supp = np.stack([np.sort(g.choice(p.N, p.K, replace=False)) for _ in range(Bn)]).astype(np.int32)
+        S = torch.from_numpy(supp).to(devc)
+        Y = torch.randn((Bn, p.M), device=devc)
+        G = torch.randn((Bn, p.K), device=devc)
+        out = torch.empty((Bn, p.K), device=devc)
+        dy = torch.empty((Bn, p.M), device=devc)
+
+        def step():
+            op.ls_solve(S, Y, CG_TOL, CG_MAXIT, out)
+            op.ls_backward(S, G, CG_TOL, CG_MAXIT, dy)
+        units, unit, metric = Bn, "signals/s", "LS forward+adjoint signals/s (N=2^16, k=1024)"
+        cfgname = "32 x (LS solve + adjoint) N=2^16 M=2^14 k=1024 (config 5)"
+    step()
+    torch.cuda.synchronize()
+    stats = op.stats()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = sum(ms) / 1e3
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric, "value": units * args.steps / t, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": cfgname}, "stats_last": stats,
+        }), flush=True)
+    op.close()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -430,6 +496,8 @@ def main():
     try:
         if args.workload == "batched":
             run_batched(args, rank, world, local_rank)
+        elif args.workload in ("ompr22", "ls16"):
+            run_single_workload(args, rank, world, local_rank)
         else:
             run_gb300(args, rank, world, local_rank)
     finally:
