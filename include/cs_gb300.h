@@ -21,8 +21,13 @@
  *     FP32 values and int32 indices, contiguous, unless a comment says "host".
  *   - Calls are asynchronous on the operator's stream (cs_op_set_stream); they return after
  *     the launch.  Argument errors are returned synchronously and nothing is launched.
- *   - N must be a power of two with 16 <= N <= 2^18 (else CS_ERR_UNSUPPORTED_N);
+ *   - N must be a power of two with 16 <= N <= 2^22 (else CS_ERR_UNSUPPORTED_N);
  *     1 <= M <= N; 0 <= K <= M; for SP also 2K <= M (else CS_ERR_INVALID_ARG).
+ *     N <= 2^18 runs on one thread-block cluster per signal; 2^18 < N <= 2^22 runs on a
+ *     cooperative grid of up to 128 CTAs per signal that streams the transform through L2
+ *     (such signals are processed one after another, also inside the batched calls).
+ *     A grid-wide wait that does not finish within its iteration limit ends the launch early:
+ *     recoveries report CS_ERR_TIMEOUT in cs_stats.status, every call through cs_op_sync.
  *   - cg_tol is RELATIVE: CG stops when ||r_j|| <= cg_tol * ||W A^T y|| (or after cg_maxit
  *     steps; reaching cg_maxit is not an error, it is counted in cs_stats.cg_maxit_hits).
  *   - cs_last_error() returns a thread-local message describing the last failure.
@@ -117,7 +122,7 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
  * after start-up, or a caller for whom cudaMalloc/cudaFree would synchronise the device).
  * The paper has no counterpart: this is a deployment variant of the same computation.
  * It calls no cudaMalloc, cudaFree or allocating library routine: the engine's per-call
- * scratch lives in one file-scope device array of 2 MiB + 8 KiB that every GPU loading the
+ * scratch lives in one file-scope device array of 2.25 MiB + 8 KiB that every GPU loading the
  * library holds until the process exits.  Limit: N <= 65536 (larger N returns
  * CS_ERR_INVALID_ARG); all other argument rules are those of cs_recover.
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress) with
@@ -162,6 +167,12 @@ cs_status cs_ls_backward_batched(cs_op_t op, int32_t B, const int32_t* support, 
 
 /* Statistics of the last single-signal call on this op (synchronises the op's stream). */
 cs_status cs_get_stats(cs_op_t op, cs_stats* out);
+
+/* Wait for the op's stream and report how its last launch ended: CS_ERR_CUDA if the stream
+ * holds a CUDA error, CS_ERR_TIMEOUT if the op runs on the streamed path (N > 2^18) and a
+ * grid-wide wait of its last launch gave up (its outputs are then undefined), else CS_OK.
+ * Apply and LS calls have no cs_stats; this is how their callers see a timeout. */
+cs_status cs_op_sync(cs_op_t op);
 
 /* Thread-local description of the last error (never NULL). */
 const char* cs_last_error(void);

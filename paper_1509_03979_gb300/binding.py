@@ -49,6 +49,7 @@ SIGNATURES = {
     "cs_ls_solve_batched": (_I32, [_P, _I32, _P, _I32, _P, _F32, _I32, _P]),
     "cs_ls_backward_batched": (_I32, [_P, _I32, _P, _I32, _P, _F32, _I32, _P]),
     "cs_get_stats": (_I32, [_P, _P]),
+    "cs_op_sync": (_I32, [_P]),
     "cs_last_error": (ctypes.c_char_p, []),
 }
 
@@ -216,6 +217,10 @@ class Operator:
         st = CsStats()
         _check(lib().cs_get_stats(self._h, ctypes.byref(st)))
         return st.as_dict()
+
+    def sync(self):
+        """Wait for this operator's stream; raises if its last launch failed or timed out."""
+        _check(lib().cs_op_sync(self._h))
 
 
 def recover_batched(ops, ys, Ks, algos, cg_tol=1e-6, cg_maxit=100, s_outs=None, supports=None, want_stats=False):

@@ -565,6 +565,18 @@ cs_status cs_get_stats(cs_op_t op, cs_stats* out) {
   return CS_OK;
 }
 
+cs_status cs_op_sync(cs_op_t op) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  cudaError_t e = cudaStreamSynchronize(op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  if (!op->dev.grid) return CS_OK;
+  int err = 0;
+  e = cudaMemcpy(&err, op->dev.gerr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  if (err != 0) return fail(CS_ERR_TIMEOUT, "a grid-wide wait of the last streamed launch gave up");
+  return CS_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------
@@ -580,9 +592,9 @@ cs_status cs_get_stats(cs_op_t op, cs_stats* out) {
 namespace {
 
 constexpr int64_t NOALLOC_N_MAX = 1 << 16;                        // largest supported N
-constexpr size_t NOALLOC_SCRATCH = (size_t)(NOALLOC_N_MAX / 2 / F_MAX) * SCRATCH_ARRAYS * 2 * F_MAX;
+constexpr size_t NOALLOC_SCRATCH = (size_t)(NOALLOC_N_MAX / 2 / F_MAX) * scratch_floats_per_cta(F_MAX);
 constexpr size_t NOALLOC_BITS = (size_t)NOALLOC_N_MAX / 32;
-// 2 MiB of scratch floats followed by the N-bit support bitmask (8 KiB)
+// 2.25 MiB of scratch floats followed by the N-bit support bitmask (8 KiB)
 static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH + NOALLOC_BITS];
 
 std::mutex g_noalloc_mu;

@@ -243,26 +243,32 @@ __device__ __forceinline__ void fft_plan(float2* X, float2* Y, const Tw& tw, int
   }
 }
 
-template <int DIR>
-__device__ __noinline__ void local_fft(float2* X, float2* Y, int F, Tw tw, int four_n) {
+// One function per plan, so that each plan's register allocation is its own.
+template <int LOGF, int DIR>
+__device__ __noinline__ void fft_plan_call(float2* X, float2* Y, Tw tw, int four_n) {
   X = shp(X);
   Y = shp(Y);
   tw.lo = shp(tw.lo);
   tw.hi = shp(tw.hi);
+  fft_plan<LOGF, DIR>(X, Y, tw, four_n);
+}
+
+template <int DIR>
+__device__ __noinline__ void local_fft(float2* X, float2* Y, int F, Tw tw, int four_n) {
   switch (__ffs(F) - 1) {
-    case 1: fft_plan<1, DIR>(X, Y, tw, four_n); break;
-    case 2: fft_plan<2, DIR>(X, Y, tw, four_n); break;
-    case 3: fft_plan<3, DIR>(X, Y, tw, four_n); break;
-    case 4: fft_plan<4, DIR>(X, Y, tw, four_n); break;
-    case 5: fft_plan<5, DIR>(X, Y, tw, four_n); break;
-    case 6: fft_plan<6, DIR>(X, Y, tw, four_n); break;
-    case 7: fft_plan<7, DIR>(X, Y, tw, four_n); break;
-    case 8: fft_plan<8, DIR>(X, Y, tw, four_n); break;
-    case 9: fft_plan<9, DIR>(X, Y, tw, four_n); break;
-    case 10: fft_plan<10, DIR>(X, Y, tw, four_n); break;
-    case 11: fft_plan<11, DIR>(X, Y, tw, four_n); break;
-    case 12: fft_plan<12, DIR>(X, Y, tw, four_n); break;
-    default: fft_plan<13, DIR>(X, Y, tw, four_n); break;
+    case 1: fft_plan_call<1, DIR>(X, Y, tw, four_n); break;
+    case 2: fft_plan_call<2, DIR>(X, Y, tw, four_n); break;
+    case 3: fft_plan_call<3, DIR>(X, Y, tw, four_n); break;
+    case 4: fft_plan_call<4, DIR>(X, Y, tw, four_n); break;
+    case 5: fft_plan_call<5, DIR>(X, Y, tw, four_n); break;
+    case 6: fft_plan_call<6, DIR>(X, Y, tw, four_n); break;
+    case 7: fft_plan_call<7, DIR>(X, Y, tw, four_n); break;
+    case 8: fft_plan_call<8, DIR>(X, Y, tw, four_n); break;
+    case 9: fft_plan_call<9, DIR>(X, Y, tw, four_n); break;
+    case 10: fft_plan_call<10, DIR>(X, Y, tw, four_n); break;
+    case 11: fft_plan_call<11, DIR>(X, Y, tw, four_n); break;
+    case 12: fft_plan_call<12, DIR>(X, Y, tw, four_n); break;
+    default: fft_plan_call<13, DIR>(X, Y, tw, four_n); break;
   }
 }
 
@@ -442,6 +448,9 @@ struct Ctx {
   float* cgp;
   float* cgq;
   uint32_t* bits;     // per-cluster N-bit output bitmask
+  int4* rank4;        // cluster launches: per frequency task, the rank in Omega of each of its
+                      // (up to 4) DCT outputs, -1 where the output is not kept (global scratch)
+  const void* setup_key;   // operator whose twiddles, sign bits and Omega tables are loaded
   // signal-domain values by slot: the FFT buffer A (cluster launches) or the CTA's rows in
   // global memory (grid launches); slot q lives at (q & rmask) * rowstride + aidx(q >> rshift)
   float2* sig;
@@ -774,19 +783,32 @@ __device__ __noinline__ void build_fbits() {
     __syncthreads();
     return;
   }
+  // cluster launches also store the rank in Omega of every kept output (the position of its
+  // value in y), so the frequency stage reads or writes y without touching omask / orank
   const Geo g = C.g;
   uint8_t* fb = shp(C.sm.fbits);
+  int4* rank4 = C.rank4;
+  const uint32_t* omask = C.omask;
+  const int32_t* orank = C.orank;
   const int nt = ntasks(g);
   for (int t = threadIdx.x; t < nt; t += NT) {
     int sa, kpa, sb, kpb;
     uint8_t bits = 0;
+    int rk[4] = {-1, -1, -1, -1};
     if (task_pair(g, t, sa, kpa, sb, kpb)) {
       const int k = kq_of(g, sa) + g.F * kpa;
       int f[4];
       const int nf = pair_outputs(g, k, sa == sb && kpa == kpb, f);
-      for (int i = 0; i < nf; ++i) bits |= (uint8_t)(((C.omask[f[i] >> 5] >> (f[i] & 31)) & 1u) << i);
+      for (int i = 0; i < nf; ++i) {
+        const uint32_t w = omask[f[i] >> 5];
+        if ((w >> (f[i] & 31)) & 1u) {
+          bits |= (uint8_t)(1u << i);
+          rk[i] = orank[f[i] >> 5] + __popc(w & ((1u << (f[i] & 31)) - 1u));
+        }
+      }
     }
     fb[t] = bits;
+    rank4[t] = make_int4(rk[0], rk[1], rk[2], rk[3]);
   }
   __syncthreads();
 }
@@ -818,7 +840,21 @@ __device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, 
   const uint32_t* signw = shp(C.sm.signw);
   const int F = g.F;
   if (src == SRC_GLOBAL_N) {
-    for (int sg = threadIdx.x; sg < 2 * F; sg += NT) slot_ref(A, sg) = gin[n_of_slot(g, sg)] * sgn_bits(signw, sg);
+    // the slots of one CTA are 2P floats apart in x: keep 8 loads in flight per thread
+    constexpr int U = 8;
+    for (int s0 = threadIdx.x; s0 < 2 * F; s0 += U * NT) {
+      float v[U];
+#pragma unroll
+      for (int e = 0; e < U; ++e) {
+        const int sg = s0 + e * NT;
+        v[e] = sg < 2 * F ? __ldg(gin + n_of_slot(g, sg)) : 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < U; ++e) {
+        const int sg = s0 + e * NT;
+        if (sg < 2 * F) slot_ref(A, sg) = v[e] * sgn_bits(signw, sg);
+      }
+    }
   } else {
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4* A4 = reinterpret_cast<float4*>(A);
@@ -860,8 +896,8 @@ __device__ __noinline__ void exchange_fwd() {
 
 // Frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, and DCT-III
 // pre-processing back into the pair.  Returns this thread's MID_RESID sum of squares.
-__device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, int kind, bool fwd_done,
-                                           bool inv, const float* vin, float* vout) {
+__device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, const int4* rank4, int kind,
+                                           bool fwd_done, bool inv, const float* vin, float* vout) {
   const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
   const uint32_t* omask = C.omask;
   const int32_t* orank = C.orank;
@@ -869,67 +905,104 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
   const float wk = sqrtf(2.0f / (float)g.N), w0 = sqrtf(1.0f / (float)g.N);
   const int nt = ntasks(g);
   float acc = 0.f;
-  for (int t = threadIdx.x; t < nt; t += NT) {
-    int sa, kpa, sb, kpb;
-    if (!task_pair(g, t, sa, kpa, sb, kpb)) continue;
-    const bool self = (sa == sb) && (kpa == kpb);
-    const int k = kq_of(g, sa) + F * kpa;
-    const uint32_t bits = fb[t];
-    // omega_{4N}^k from the table; omega_{4N}^{k+L} = omega_{4N}^k e^{-i pi/4};
-    // omega_{4N}^{4k} = (omega_{4N}^k)^4 (two squarings)
-    const float2 wk1 = tw.get<-1>(k);
-    const float2 wkL = cmul(wk1, make_float2(0.70710678118654752f, -0.70710678118654752f));
-    const float2 wk2 = cmul(wk1, wk1);
-    const float2 w4k = cmul(wk2, wk2);
-    float X[4] = {0.f, 0.f, 0.f, 0.f};
-    if (fwd_done) {
-      const float2 Za = B[kpa * S2 + sa];
-      const float2 Zb = B[kpb * S2 + sb];
-      const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
-      const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
-      const float2 tO = cmul(w4k, O);
-      const float2 u1 = cmul(wk1, cadd(E, tO));
-      const float2 u2 = cmul(wkL, csub(E, tO));
-      if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
-      else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
-    }
-    if (kind == MID_MASK) {
+  // Two tasks per iteration: the y-side ranks and loads of both are issued before either
+  // task's arithmetic, so their global latencies overlap.
+  for (int t0 = threadIdx.x; t0 < nt; t0 += 2 * NT) {
+    int rk[2][4];
+    float xin[2][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (!((bits >> i) & 1u)) X[i] = 0.f;
-    } else {
-      int f[4];
-      const int nf = pair_outputs(g, k, self, f);
+    for (int u = 0; u < 2; ++u) {
+      const int t = t0 + u * NT;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (i < nf) {
-          const bool in = (bits >> i) & 1u;
-          const int rk = in ? orank[f[i] >> 5] + __popc(omask[f[i] >> 5] & ((1u << (f[i] & 31)) - 1u)) : 0;
-          if (kind == MID_RESID) {
-            X[i] = in ? vin[rk] - X[i] : 0.f;
-            acc = fmaf(X[i], X[i], acc);
-          } else if (kind == MID_OUT) {
-            if (in) vout[rk] = X[i];
-          } else {   // MID_IN
-            X[i] = in ? vin[rk] : 0.f;
-          }
+        rk[u][i] = -1;
+        xin[u][i] = 0.f;
+      }
+      if (kind == MID_MASK || t >= nt) continue;
+      if (rank4) {
+        const int4 r = rank4[t];
+        rk[u][0] = r.x; rk[u][1] = r.y; rk[u][2] = r.z; rk[u][3] = r.w;
+      } else {
+        int sa, kpa, sb, kpb;
+        if (task_pair(g, t, sa, kpa, sb, kpb)) {
+          const int k = kq_of(g, sa) + F * kpa;
+          int f[4];
+          const int nf = pair_outputs(g, k, sa == sb && kpa == kpb, f);
+          const uint32_t bits = fb[t];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (i < nf && ((bits >> i) & 1u))
+              rk[u][i] = orank[f[i] >> 5] + __popc(omask[f[i] >> 5] & ((1u << (f[i] & 31)) - 1u));
         }
       }
     }
-    if (inv) {
-      float X4[4];
-      if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
-      else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
-      else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
-      // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
-      const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
-      const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
-      const float2 V1 = cmul(cconj(wk1), u1);
-      const float2 V2 = cmul(cconj(wkL), u2);
-      const float2 E = cscale(cadd(V1, V2), 0.5f);
-      const float2 O = cmul(cscale(csub(V1, V2), 0.5f), cconj(w4k));
-      B[kpa * S2 + sa] = cadd(E, cmuli(O));
-      if (!self) B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
+    if (kind == MID_RESID || kind == MID_IN) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (rk[u][i] >= 0) xin[u][i] = __ldg(vin + rk[u][i]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int t = t0 + u * NT;
+      if (t >= nt) continue;
+      int sa, kpa, sb, kpb;
+      if (!task_pair(g, t, sa, kpa, sb, kpb)) continue;
+      const bool self = (sa == sb) && (kpa == kpb);
+      const int k = kq_of(g, sa) + F * kpa;
+      // omega_{4N}^k from the table; omega_{4N}^{k+L} = omega_{4N}^k e^{-i pi/4};
+      // omega_{4N}^{4k} = (omega_{4N}^k)^4 (two squarings)
+      const float2 wk1 = tw.get<-1>(k);
+      const float2 wkL = cmul(wk1, make_float2(0.70710678118654752f, -0.70710678118654752f));
+      const float2 wk2 = cmul(wk1, wk1);
+      const float2 w4k = cmul(wk2, wk2);
+      float X[4] = {0.f, 0.f, 0.f, 0.f};
+      if (fwd_done) {
+        const float2 Za = B[kpa * S2 + sa];
+        const float2 Zb = B[kpb * S2 + sb];
+        const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
+        const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
+        const float2 tO = cmul(w4k, O);
+        const float2 u1 = cmul(wk1, cadd(E, tO));
+        const float2 u2 = cmul(wkL, csub(E, tO));
+        if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
+        else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
+      }
+      if (kind == MID_MASK) {
+        const uint32_t bits = fb[t];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (!((bits >> i) & 1u)) X[i] = 0.f;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const bool in = rk[u][i] >= 0;
+          if (kind == MID_RESID) {
+            X[i] = in ? xin[u][i] - X[i] : 0.f;
+            acc = fmaf(X[i], X[i], acc);
+          } else if (kind == MID_OUT) {
+            if (in) vout[rk[u][i]] = X[i];
+          } else {   // MID_IN
+            X[i] = in ? xin[u][i] : 0.f;
+          }
+        }
+      }
+      if (inv) {
+        float X4[4];
+        if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
+        else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
+        else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
+        // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
+        const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
+        const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
+        const float2 V1 = cmul(cconj(wk1), u1);
+        const float2 V2 = cmul(cconj(wkL), u2);
+        const float2 E = cscale(cadd(V1, V2), 0.5f);
+        const float2 O = cmul(cscale(csub(V1, V2), 0.5f), cconj(w4k));
+        B[kpa * S2 + sa] = cadd(E, cmuli(O));
+        if (!self) B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
+      }
     }
   }
   __syncthreads();
@@ -938,7 +1011,7 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
 
 __device__ __noinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
   const Geo g = C.g;
-  return freq_core(g, shp(C.sm.B), shp(C.sm.fbits), kind, fwd_done, inv, vin, vout);
+  return freq_core(g, shp(C.sm.B), shp(C.sm.fbits), C.rank4, kind, fwd_done, inv, vin, vout);
 }
 
 // Inverse exchange: P-point inverse DFT per column, cluster barrier, all-to-all pull back into
@@ -1115,7 +1188,7 @@ __device__ __noinline__ float grid_col_block(int j, int kind, bool fwd_done, boo
     col_fft<-1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
   }
   const int fbstride = (W / 2) * S2 + S2 + 1;
-  const float acc = freq_core(gb, X, shp(C.sm.fbits) + j * fbstride, kind, fwd_done, inv, vin, vout);
+  const float acc = freq_core(gb, X, shp(C.sm.fbits) + j * fbstride, nullptr, kind, fwd_done, inv, vin, vout);
   __syncthreads();
   if (inv) {
     col_fft<1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
@@ -1764,6 +1837,10 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     return;
   }
   const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
+  // Twiddles, sign bits and the Omega tables depend only on the operator (and this CTA's fixed
+  // rank and cluster size): consecutive tasks on one operator load them once.  Every thread
+  // reads the key here, before the first barrier; thread 0 updates it after the last one.
+  const bool loaded = C.setup_key == (const void*)op.omask;
   if (threadIdx.x == 0) {   // every CTA thread passed the previous task's barrier
     Geo& g = C.g;
     g.N = op.N; g.L = op.N >> 1; g.P = P; g.F = op.F; g.c = c;
@@ -1789,7 +1866,7 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     C.tw.mask4n = g.four_n - 1;
   }
   __syncthreads();
-  {
+  if (!loaded) {
     // twiddle tables and sign bits
     float2* twlo = shp(C.sm.twlo);
     float2* twhi = shp(C.sm.twhi);
@@ -1809,9 +1886,10 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
       }
       signw[w] = bitsw;
     }
+    __syncthreads();
+    build_fbits();
+    if (threadIdx.x == 0) C.setup_key = (const void*)op.omask;
   }
-  __syncthreads();
-  build_fbits();
   const Task& t = *tp;
   switch (t.mode) {
     case MODE_APPLY:
@@ -1855,6 +1933,8 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
     C.cy = base + 2 * a;
     C.glist = reinterpret_cast<int*>(base + 3 * a);
     C.gcg = base + 4 * a;
+    C.rank4 = reinterpret_cast<int4*>(base + 8 * a);
+    C.setup_key = nullptr;
     C.bits = lp.bits + (size_t)cid * lp.bits_per_cluster;
   }
   __syncthreads();
@@ -1882,6 +1962,8 @@ __global__ void __launch_bounds__(NT, 1) grid_kernel(const Launch lp) {
     C.cy = base + 2 * a;
     C.glist = reinterpret_cast<int*>(base + 3 * a);
     C.gcg = base + 4 * a;
+    C.rank4 = nullptr;
+    C.setup_key = nullptr;
     C.bits = lp.bits;
     C.op = lp.tasks ? lp.tasks[0].op : lp.single.op;   // barrier state for the first task
   }

@@ -92,8 +92,12 @@ struct Launch {
   size_t bits_per_cluster;   // words
 };
 
-// Per-CTA global scratch: SCRATCH_ARRAYS arrays of 2*F_alloc 32-bit words.
-__host__ __device__ inline size_t scratch_floats_per_cta(int F_alloc) { return (size_t)SCRATCH_ARRAYS * 2 * F_alloc; }
+// Per-CTA global scratch: SCRATCH_ARRAYS arrays of 2*F_alloc 32-bit words, then the rank
+// table (4 ints per frequency task; a CTA runs at most F/2 + P_MAX + 1 tasks).
+__host__ __device__ constexpr size_t rank_ints_per_cta(int F_alloc) { return 4 * ((size_t)F_alloc / 2 + P_MAX + 16); }
+__host__ __device__ constexpr size_t scratch_floats_per_cta(int F_alloc) {
+  return (size_t)SCRATCH_ARRAYS * 2 * F_alloc + rank_ints_per_cta(F_alloc);
+}
 
 SmemPlan cluster_plan(int F_alloc);
 SmemPlan grid_plan(const OpDev& op);
