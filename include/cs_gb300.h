@@ -87,9 +87,35 @@ cs_status cs_op_apply(cs_op_t op, const float* x_N, float* y_M);
 cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N);
 
 /* Batched A / A^T: B independent vectors through the same operator, one persistent launch.
- * X [B][N] and Y [B][M] device, row-major contiguous; U [B][M] -> X [B][N] for the transpose. */
+ * X [B][N] and Y [B][M] device, row-major contiguous; U [B][M] -> X [B][N] for the transpose.
+ * Two implementations compute the same operator (results agree to rounding, not bitwise):
+ *   CS_BATCHED_CLUSTER   one thread-block cluster per vector, the transform resident in the
+ *                        cluster's shared memory (the engine the decoders use);
+ *   CS_BATCHED_STREAMED  a small cluster of CTAs per vector for 2^15 <= N <= 2^18: a
+ *                        decimation-in-frequency split into 8192-point rows, a column pass
+ *                        and a row pass through a per-cluster buffer in L2, x read and written
+ *                        in coalesced 16-byte groups.  Uses 1.1 MiB (N = 2^18) of stream-
+ *                        ordered temporary device memory per resident cluster, allocated and
+ *                        freed on the op's stream per call.
+ * CS_BATCHED_AUTO (the default) takes the choice of cs_op_tune_batched when it has run, else
+ * the streamed kernel (2 CTAs per vector) whenever N allows it and B >= 2. */
 cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y);
 cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X);
+
+enum { CS_BATCHED_AUTO = 0, CS_BATCHED_CLUSTER = 1, CS_BATCHED_STREAMED = 2 };
+/* Choose the implementation of cs_op_apply_batched / cs_op_apply_t_batched for this op.
+ * CS_ERR_UNSUPPORTED_N if CS_BATCHED_STREAMED is asked for outside 2^15 <= N <= 2^18. */
+cs_status cs_op_set_batched_impl(cs_op_t op, int32_t impl);
+
+/* Autotuner of the batched operator (no counterpart in the paper): times every candidate that
+ * can run this op -- the cluster engine, and the streamed kernel with 1, 2, 4 or 8 CTAs per
+ * vector (at most P/2 = N/2^15) -- on B internally generated vectors, for A and A^T
+ * separately, and keeps the fastest for later batched calls under CS_BATCHED_AUTO (under
+ * CS_BATCHED_STREAMED the tuned CTAs per vector are kept when the winner is streamed).
+ * ms_out: HOST [2][5] or NULL, milliseconds per call in the order {cluster engine, 1, 2, 4, 8}
+ * for A then A^T, -1 where a candidate does not apply.  Allocates and frees B (N + M) floats
+ * of device memory, runs on the op's stream and returns after synchronising it. */
+cs_status cs_op_tune_batched(cs_op_t op, int32_t B, float* ms_out);
 
 /* Number of signals of this operator's size that the device runs at the same time (one per
  * resident thread-block cluster); a batch of this many fills the GPU.  >= 1. */

@@ -40,6 +40,8 @@ SIGNATURES = {
     "cs_op_apply_batched": (_I32, [_P, _I32, _P, _P]),
     "cs_op_apply_t_batched": (_I32, [_P, _I32, _P, _P]),
     "cs_op_concurrency": (_I32, [_P]),
+    "cs_op_set_batched_impl": (_I32, [_P, _I32]),
+    "cs_op_tune_batched": (_I32, [_P, _I32, _P]),
     "cs_operator_draws": (_I32, [_I64, _I64, _U64, _P, _P]),
     "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
     "cs_recover_noalloc": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
@@ -156,6 +158,25 @@ class Operator:
     def concurrency(self):
         """Signals of this size the GPU runs at once (resident clusters)."""
         return int(lib().cs_op_concurrency(self._h))
+
+    BATCHED_IMPLS = {"auto": 0, "cluster": 1, "streamed": 2}
+
+    def set_batched_impl(self, impl):
+        """Implementation of apply_batched / apply_t_batched: 'auto', 'cluster' or 'streamed'."""
+        _check(lib().cs_op_set_batched_impl(self._h, self.BATCHED_IMPLS[impl]))
+
+    TUNE_CANDIDATES = ("cluster", "streamed x1", "streamed x2", "streamed x4", "streamed x8")
+
+    def tune_batched(self, B):
+        """Time every batched candidate on B vectors and keep the fastest (per direction).
+        Returns {"A": {candidate: ms}, "AT": {...}} for the candidates that apply."""
+        ms = (ctypes.c_float * 10)()
+        self._stream()
+        _check(lib().cs_op_tune_batched(self._h, int(B), ms))
+        out = {}
+        for d, name in enumerate(("A", "AT")):
+            out[name] = {c: ms[5 * d + i] for i, c in enumerate(self.TUNE_CANDIDATES) if ms[5 * d + i] >= 0}
+        return out
 
     def export(self):
         import numpy as np

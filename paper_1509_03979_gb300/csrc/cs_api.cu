@@ -88,6 +88,10 @@ struct cs_op {
   uint32_t* d_bits = nullptr;
   cs_stats* d_stats = nullptr;
   void* d_grid = nullptr;       // streamed geometry: rows, signal rows, barrier and reduction state
+  uint32_t* d_dbits = nullptr;  // [N/32] sign bits of d, for the streamed batched operator
+  int32_t* d_prank = nullptr;   // [N/4 + 1][4] Omega ranks of the streamed row pass's pair outputs
+  int batched_impl = CS_BATCHED_AUTO;
+  int tuned_nc[2] = {0, 0};     // per mode (A, A^T): 0 untuned, -1 cluster engine, else CTAs per vector
 };
 
 namespace {
@@ -102,6 +106,8 @@ void free_op(cs_op* op) {
   cudaFree(op->d_bits);
   cudaFree(op->d_stats);
   cudaFree(op->d_grid);
+  cudaFree(op->d_dbits);
+  cudaFree(op->d_prank);
   delete op;
 }
 
@@ -155,6 +161,7 @@ cs_status check_cg(float cg_tol, int32_t cg_maxit) {
 }
 
 constexpr int SP_ROUNDS = 50;     // SP outer-iteration cap
+constexpr int STREAM_CLUSTER = 2;  // default CTAs per vector of the streamed batched operator
 constexpr int OMPR_SWAPS = 100;   // OMPR replacement cap
 
 }  // namespace
@@ -248,6 +255,43 @@ cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) {
   CSG_TRY(cudaMemcpy(op->d_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
   CSG_TRY(cudaMemset(op->d_scratch, 0, scratch));
   CSG_TRY(cudaMemset(op->d_stats, 0, sizeof(cs_stats)));
+  if (!d.grid && N >= STREAM_N_MIN) {
+    std::vector<uint32_t> dbits((size_t)W, 0u);
+    for (int64_t n = 0; n < N; ++n)
+      if (draw_sign(d.sign_key, n) < 0) dbits[(size_t)(n >> 5)] |= 1u << (n & 31);
+    CSG_TRY(cudaMalloc(&op->d_dbits, sizeof(uint32_t) * (size_t)W));
+    CSG_TRY(cudaMemcpy(op->d_dbits, dbits.data(), sizeof(uint32_t) * (size_t)W, cudaMemcpyHostToDevice));
+    // the row pass visits the pairs (Z_k, Z_{L-k}) unit by unit (ra = 0 .. P/2), k = ra + P k1;
+    // store the rank in Omega of each pair output (-1: not in Omega) in that order
+    const int SF = STREAM_F, SP = (int)(L / STREAM_F);
+    auto rank_of = [&](int64_t f) -> int32_t {
+      const uint32_t w = omask[(size_t)(f >> 5)];
+      if (!((w >> (f & 31)) & 1u)) return -1;
+      return orank[(size_t)(f >> 5)] + (int32_t)__builtin_popcount(w & ((1u << (f & 31)) - 1u));
+    };
+    std::vector<int32_t> prank((size_t)(L / 2 + 1) * 4, -1);
+    size_t idx = 0;
+    for (int ra = 0; ra <= SP / 2; ++ra) {
+      const int np = ra == 0 ? SF / 2 + 1 : (2 * ra == SP ? SF / 2 : SF);
+      for (int k1 = 0; k1 < np; ++k1, ++idx) {
+        const int64_t k = ra + (int64_t)SP * k1;
+        const bool self = ra == 0 && (k1 == 0 || 2 * k1 == SF);
+        int64_t f[4];
+        int nf = 4;
+        if (k == 0) { f[0] = 0; f[1] = L; nf = 2; }
+        else if (self) { f[0] = k; f[1] = N - k; nf = 2; }
+        else { f[0] = k; f[1] = N - k; f[2] = L + k; f[3] = L - k; }
+        for (int i = 0; i < nf; ++i) prank[idx * 4 + (size_t)i] = rank_of(f[i]);
+      }
+    }
+    if (idx != (size_t)(L / 2 + 1)) {
+      fail(CS_ERR_INVALID_ARG, "internal: streamed pair table size");
+      free_op(op);
+      return nullptr;
+    }
+    CSG_TRY(cudaMalloc(&op->d_prank, sizeof(int32_t) * prank.size()));
+    CSG_TRY(cudaMemcpy(op->d_prank, prank.data(), sizeof(int32_t) * prank.size(), cudaMemcpyHostToDevice));
+  }
 #undef CSG_TRY
   d.omask = op->d_omask;
   d.orank = op->d_orank;
@@ -326,9 +370,42 @@ cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N) {
 
 static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream);
 
-static cs_status apply_batched(cs_op_t op, int mode, int32_t B, const float* in, float* out) {
-  if (!op || B < 0 || (B > 0 && (!in || !out))) return fail(CS_ERR_INVALID_ARG, "null argument or B < 0");
-  if (B == 0) return CS_OK;
+// Streamed batched operator: one cluster of nc CTAs per vector, a per-cluster intermediate
+// freed after the launch.
+static int stream_default_nc(int P) { return std::min(STREAM_CLUSTER, P / 2); }
+
+static cs_status stream_apply(cs_op_t op, int mode, int32_t B, const float* in, float* out, int nc) {
+  const int clusters = std::min<int>(B, stream_clusters(nc));
+  if (clusters < 1) return fail(CS_ERR_CUDA, "the streamed operator kernel cannot be launched on this device");
+  StreamArgs a{};
+  a.op = op->dev;
+  a.dbits = op->d_dbits;
+  a.prank = reinterpret_cast<const int4*>(op->d_prank);
+  a.mode = mode;
+  a.B = B;
+  a.in = in;
+  a.out = out;
+  cudaError_t e;
+  const size_t bytes = sizeof(float) * stream_row_floats() * (size_t)op->dev.P * (size_t)clusters;
+  if ((e = cudaMallocAsync(&a.T, bytes, op->stream)) != cudaSuccess) return cuda_fail(e, "alloc stream rows");
+  e = launch_stream(a, nc, clusters, op->stream);
+  cudaFreeAsync(a.T, op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream launch");
+  return CS_OK;
+}
+
+// The batched path for one call: 0 = cluster engine, else the streamed kernel with that many
+// CTAs per vector (the tuned choice when there is one).
+static int batched_choice(const cs_op* op, int mode, int32_t B) {
+  if (!op->d_dbits || op->batched_impl == CS_BATCHED_CLUSTER) return 0;
+  const int tuned = op->tuned_nc[mode == MODE_APPLY ? 0 : 1];
+  if (op->batched_impl == CS_BATCHED_STREAMED) return tuned > 0 ? tuned : stream_default_nc(op->dev.P);
+  if (tuned != 0) return tuned < 0 ? 0 : tuned;
+  return B >= 2 ? stream_default_nc(op->dev.P) : 0;
+}
+
+static cs_status apply_with(cs_op_t op, int mode, int32_t B, const float* in, float* out, int nc) {
+  if (nc > 0) return stream_apply(op, mode, B, in, out, nc);
   const size_t nin = mode == MODE_APPLY ? (size_t)op->N : (size_t)op->M;
   const size_t nout = mode == MODE_APPLY ? (size_t)op->M : (size_t)op->N;
   std::vector<Task> tasks;
@@ -344,12 +421,81 @@ static cs_status apply_batched(cs_op_t op, int mode, int32_t B, const float* in,
   return launch_tasks(tasks, op->stream);
 }
 
+static cs_status apply_batched(cs_op_t op, int mode, int32_t B, const float* in, float* out) {
+  if (!op || B < 0 || (B > 0 && (!in || !out))) return fail(CS_ERR_INVALID_ARG, "null argument or B < 0");
+  if (B == 0) return CS_OK;
+  return apply_with(op, mode, B, in, out, batched_choice(op, mode, B));
+}
+
 cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y) {
   return apply_batched(op, MODE_APPLY, B, X, Y);
 }
 
 cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X) {
   return apply_batched(op, MODE_APPLY_T, B, U, X);
+}
+
+cs_status cs_op_set_batched_impl(cs_op_t op, int32_t impl) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  if (impl != CS_BATCHED_AUTO && impl != CS_BATCHED_CLUSTER && impl != CS_BATCHED_STREAMED)
+    return fail(CS_ERR_INVALID_ARG, "unknown batched implementation");
+  if (impl == CS_BATCHED_STREAMED && !op->d_dbits)
+    return fail(CS_ERR_UNSUPPORTED_N, "the streamed batched operator needs 2^15 <= N <= 2^18");
+  op->batched_impl = impl;
+  return CS_OK;
+}
+
+cs_status cs_op_tune_batched(cs_op_t op, int32_t B, float* ms_out) {
+  if (!op || B < 1) return fail(CS_ERR_INVALID_ARG, "null operator or B < 1");
+  constexpr int NCAND = 5;
+  const int cand[NCAND] = {0, 1, 2, 4, 8};   // cluster engine, then CTAs per vector
+  if (ms_out)
+    for (int i = 0; i < 2 * NCAND; ++i) ms_out[i] = -1.f;
+  const size_t nx = (size_t)B * (size_t)op->N, ny = (size_t)B * (size_t)op->M;
+  float* X = nullptr;
+  float* Y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&X, sizeof(float) * nx);
+  if (e == cudaSuccess) e = cudaMalloc(&Y, sizeof(float) * ny);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0x3c, sizeof(float) * nx, op->stream);   // 0.0115 in every entry
+  if (e == cudaSuccess) e = cudaMemsetAsync(Y, 0x3c, sizeof(float) * ny, op->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  cs_status st = e == cudaSuccess ? CS_OK : cuda_fail(e, "tuning buffers");
+  for (int mi = 0; mi < 2 && st == CS_OK; ++mi) {
+    const int mode = mi == 0 ? MODE_APPLY : MODE_APPLY_T;
+    const float* in = mi == 0 ? X : Y;
+    float* out = mi == 0 ? Y : X;
+    float best = 0.f;
+    int best_nc = -1;
+    for (int ci = 0; ci < NCAND && st == CS_OK; ++ci) {
+      const int nc = cand[ci];
+      if (nc > 0 && (!op->d_dbits || nc > op->dev.P / 2 || stream_clusters(nc) < 1)) continue;
+      float ms = -1.f;
+      for (int rep = 0; rep < 3 && st == CS_OK; ++rep) {   // one warm-up, then the faster of two
+        if ((e = cudaEventRecord(e0, op->stream)) != cudaSuccess) { st = cuda_fail(e, "event"); break; }
+        st = apply_with(op, mode, B, in, out, nc);
+        if (st != CS_OK) break;
+        if ((e = cudaEventRecord(e1, op->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+          st = cuda_fail(e, "event");
+          break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0 && (ms < 0.f || t < ms)) ms = t;
+      }
+      if (st != CS_OK) break;
+      if (ms_out) ms_out[mi * NCAND + ci] = ms;
+      if (best_nc < 0 || ms < best) { best = ms; best_nc = nc; }
+    }
+    if (st == CS_OK) op->tuned_nc[mi] = best_nc > 0 ? best_nc : -1;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(op->stream);
+  cudaFree(X);
+  cudaFree(Y);
+  return st;
 }
 
 int32_t cs_op_concurrency(cs_op_t op) {

@@ -894,6 +894,54 @@ __device__ __noinline__ void exchange_fwd() {
   __syncthreads();
 }
 
+// Makhoul's pair step between the L-point FFT Z of the reordered, paired sequence and the
+// orthonormal DCT-II X (both directions share these twiddles): for the pair (Z_k, Z_{L-k}),
+// E and O are the spectra of the even and odd reordered samples, and
+//   X_k = w_k Re(omega_{4N}^k (E + omega_N^k O)),  X_{N-k} = -w_k Im(...),
+//   X_{L-k} and X_{L+k} likewise from omega_{4N}^{k+L} (E - omega_N^k O).
+struct PairTw {
+  float2 wk1;   // omega_{4N}^k
+  float2 wkL;   // omega_{4N}^{k+L} = omega_{4N}^k e^{-i pi/4}
+  float2 w4k;   // omega_{4N}^{4k} = omega_N^k
+};
+__device__ __forceinline__ PairTw pair_tw(const Tw& tw, int k) {
+  PairTw p;
+  p.wk1 = tw.get<-1>(k);
+  p.wkL = cmul(p.wk1, make_float2(0.70710678118654752f, -0.70710678118654752f));
+  const float2 wk2 = cmul(p.wk1, p.wk1);
+  p.w4k = cmul(wk2, wk2);
+  return p;
+}
+// DCT-II outputs of the pair: X = {X_k, X_{N-k}, X_{L+k}, X_{L-k}} (k = 0: {X_0, X_L}).
+__device__ __forceinline__ void dct2_pair(float2 Za, float2 Zb, int k, const PairTw& p, float wk, float w0,
+                                          float* X) {
+  const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
+  const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
+  const float2 tO = cmul(p.w4k, O);
+  const float2 u1 = cmul(p.wk1, cadd(E, tO));
+  const float2 u2 = cmul(p.wkL, csub(E, tO));
+  if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
+  else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
+}
+// Inverse (DCT-III pre-processing) with the 1/w_k and 1/L factors folded in: from the pair's
+// X values (same order as dct2_pair), the values to store at Z_k (Va) and Z_{L-k} (Vb).
+__device__ __forceinline__ void dct3_pair(const float* X, int k, bool self, const PairTw& p, float wk, float w0,
+                                          float2& Va, float2& Vb) {
+  float X4[4];
+  if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
+  else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
+  else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
+  // (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
+  const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
+  const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
+  const float2 V1 = cmul(cconj(p.wk1), u1);
+  const float2 V2 = cmul(cconj(p.wkL), u2);
+  const float2 E = cscale(cadd(V1, V2), 0.5f);
+  const float2 O = cmul(cscale(csub(V1, V2), 0.5f), cconj(p.w4k));
+  Va = cadd(E, cmuli(O));
+  Vb = cadd(cconj(E), cmuli(cconj(O)));
+}
+
 // Frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, and DCT-III
 // pre-processing back into the pair.  Returns this thread's MID_RESID sum of squares.
 __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, const int4* rank4, int kind,
@@ -951,24 +999,9 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
       if (!task_pair(g, t, sa, kpa, sb, kpb)) continue;
       const bool self = (sa == sb) && (kpa == kpb);
       const int k = kq_of(g, sa) + F * kpa;
-      // omega_{4N}^k from the table; omega_{4N}^{k+L} = omega_{4N}^k e^{-i pi/4};
-      // omega_{4N}^{4k} = (omega_{4N}^k)^4 (two squarings)
-      const float2 wk1 = tw.get<-1>(k);
-      const float2 wkL = cmul(wk1, make_float2(0.70710678118654752f, -0.70710678118654752f));
-      const float2 wk2 = cmul(wk1, wk1);
-      const float2 w4k = cmul(wk2, wk2);
+      const PairTw pt = pair_tw(tw, k);
       float X[4] = {0.f, 0.f, 0.f, 0.f};
-      if (fwd_done) {
-        const float2 Za = B[kpa * S2 + sa];
-        const float2 Zb = B[kpb * S2 + sb];
-        const float2 E = cscale(cadd(Za, cconj(Zb)), 0.5f);
-        const float2 O = cscale(make_float2(Za.y + Zb.y, Zb.x - Za.x), 0.5f);   // (Za - conj Zb) / 2i
-        const float2 tO = cmul(w4k, O);
-        const float2 u1 = cmul(wk1, cadd(E, tO));
-        const float2 u2 = cmul(wkL, csub(E, tO));
-        if (k == 0) { X[0] = w0 * u1.x; X[1] = wk * u2.x; }
-        else { X[0] = wk * u1.x; X[1] = -wk * u1.y; X[2] = wk * u2.x; X[3] = -wk * u2.y; }
-      }
+      if (fwd_done) dct2_pair(B[kpa * S2 + sa], B[kpb * S2 + sb], k, pt, wk, w0, X);
       if (kind == MID_MASK) {
         const uint32_t bits = fb[t];
 #pragma unroll
@@ -989,19 +1022,10 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
         }
       }
       if (inv) {
-        float X4[4];
-        if (k == 0) { X4[0] = X[0]; X4[1] = 0.f; X4[2] = X[1]; X4[3] = X[1]; }
-        else if (self) { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[1]; X4[3] = X[0]; }
-        else { X4[0] = X[0]; X4[1] = X[1]; X4[2] = X[2]; X4[3] = X[3]; }
-        // u / L with the 1/w_k and 1/L factors folded: (1/w_k)/L = w_k (k >= 1), 2 w_0 (k = 0)
-        const float2 u1 = make_float2(X4[0] * (k == 0 ? 2.f * w0 : wk), -X4[1] * wk);
-        const float2 u2 = make_float2(X4[2] * wk, -X4[3] * wk);
-        const float2 V1 = cmul(cconj(wk1), u1);
-        const float2 V2 = cmul(cconj(wkL), u2);
-        const float2 E = cscale(cadd(V1, V2), 0.5f);
-        const float2 O = cmul(cscale(csub(V1, V2), 0.5f), cconj(w4k));
-        B[kpa * S2 + sa] = cadd(E, cmuli(O));
-        if (!self) B[kpb * S2 + sb] = cadd(cconj(E), cmuli(cconj(O)));
+        float2 Va, Vb;
+        dct3_pair(X, k, self, pt, wk, w0, Va, Vb);
+        B[kpa * S2 + sa] = Va;
+        if (!self) B[kpb * S2 + sb] = Vb;
       }
     }
   }
@@ -2051,6 +2075,304 @@ int grid_fits(const OpDev& op) {
     return 0;
   }
   return per_sm * sms >= op.G ? 1 : 0;
+}
+
+// ------------------------------------------- streamed batched operator (one CTA per vector)
+// A batch of A x or A^T u with 2^15 <= N <= 2^18: every CTA transforms whole vectors on its
+// own, with L = F P (F = STREAM_F, P = L / F) and the decimation-in-frequency split
+//   m = n1 + F n2,  k = k2 + P k1:
+//   Z[k2 + P k1] = sum_n1 omega_F^{n1 k1} omega_L^{n1 k2} sum_n2 z[n1 + F n2] omega_P^{n2 k2}.
+// Column pass: P-point DFTs over n2 for every n1, times omega_L^{n1 k2}, into rows T[k2][n1]
+// of the CTA's global buffer (written and read back by the same CTA, L2-resident).  Row pass:
+// F-point FFTs of rows k2 and P - k2 in shared memory; together they hold every pair
+// (Z_k, Z_{L-k}) of the DCT step.  A^T runs the same passes in reverse order.
+// Makhoul's reordering puts z[m] and z[L-1-m] in one 16-byte group of x (m < L/2):
+//   x[4m .. 4m+3] = (Re z[m], Im z[L-1-m], Im z[m], Re z[L-1-m])   (times the signs d_n),
+// and L-1-m = (F-1-n1) + F (P-1-n2), so a thread that owns the column pair (n1, F-1-n1)
+// reads or writes x only in whole, coalesced 16-byte groups.
+
+__device__ __forceinline__ float4 sign4(float4 q, uint32_t bits) {
+  q.x = (bits & 1u) ? -q.x : q.x;
+  q.y = (bits & 2u) ? -q.y : q.y;
+  q.z = (bits & 4u) ? -q.z : q.z;
+  q.w = (bits & 8u) ? -q.w : q.w;
+  return q;
+}
+__device__ __forceinline__ uint32_t dbits4(const uint32_t* dbits, int m) {
+  return (__ldg(dbits + (m >> 3)) >> ((4 * m) & 31)) & 0xFu;   // signs of x[4m .. 4m+3]
+}
+
+// Column pass of A x: x (one vector) -> rows T[k2][n1].
+template <int PT>
+__device__ __forceinline__ void stream_cols_fwd(const float4* x4, const uint32_t* dbits, float2* T, const Tw& tw,
+                                                int rot, int c, int nc) {
+  constexpr int F = STREAM_F;
+  const int rs = apad(F);
+  for (int jj = c * NT + threadIdx.x; jj < F / 2; jj += nc * NT) {
+    const int j = (jj + rot) & (F / 2 - 1);
+    const int n1 = j, n1b = F - 1 - j;
+    float2 a[PT], b[PT];   // columns n1 and n1b by n2
+#pragma unroll
+    for (int n2 = 0; n2 < PT / 2; ++n2) {
+      const int m = n1 + F * n2, m2 = n1b + F * n2;
+      const float4 q = sign4(__ldg(x4 + m), dbits4(dbits, m));
+      const float4 q2 = sign4(__ldg(x4 + m2), dbits4(dbits, m2));
+      a[n2] = make_float2(q.x, q.z);
+      b[PT - 1 - n2] = make_float2(q.w, q.y);
+      b[n2] = make_float2(q2.x, q2.z);
+      a[PT - 1 - n2] = make_float2(q2.w, q2.y);
+    }
+    dft<PT, -1>(a);
+    twiddle_powers<PT, -1>(a, tw, 8 * n1);   // a[k2] *= omega_L^{n1 k2}
+    dft<PT, -1>(b);
+    twiddle_powers<PT, -1>(b, tw, 8 * n1b);
+#pragma unroll
+    for (int k2 = 0; k2 < PT; ++k2) {
+      T[k2 * rs + aidx(n1)] = a[k2];
+      T[k2 * rs + aidx(n1b)] = b[k2];
+    }
+  }
+}
+
+// Column pass of A^T: rows T[k2][n1] -> x (one vector).
+template <int PT>
+__device__ __forceinline__ void stream_cols_inv(const float2* T, const uint32_t* dbits, float4* x4, const Tw& tw,
+                                                int rot, int c, int nc) {
+  constexpr int F = STREAM_F;
+  const int rs = apad(F);
+  for (int jj = c * NT + threadIdx.x; jj < F / 2; jj += nc * NT) {
+    const int j = (jj + rot) & (F / 2 - 1);
+    const int n1 = j, n1b = F - 1 - j;
+    float2 a[PT], b[PT];
+#pragma unroll
+    for (int k2 = 0; k2 < PT; ++k2) {
+      a[k2] = T[k2 * rs + aidx(n1)];
+      b[k2] = T[k2 * rs + aidx(n1b)];
+    }
+    twiddle_powers<PT, 1>(a, tw, 8 * n1);   // a[k2] *= conj(omega_L^{n1 k2})
+    dft<PT, 1>(a);                           // a[n2] = z[n1 + F n2]
+    twiddle_powers<PT, 1>(b, tw, 8 * n1b);
+    dft<PT, 1>(b);
+#pragma unroll
+    for (int n2 = 0; n2 < PT / 2; ++n2) {
+      const int m = n1 + F * n2, m2 = n1b + F * n2;
+      const float2 za = a[n2], zam = b[PT - 1 - n2];    // z[m], z[L-1-m]
+      const float2 zb = b[n2], zbm = a[PT - 1 - n2];    // z[m2], z[L-1-m2]
+      x4[m] = sign4(make_float4(za.x, zam.y, za.y, zam.x), dbits4(dbits, m));
+      x4[m2] = sign4(make_float4(zb.x, zbm.y, zb.y, zbm.x), dbits4(dbits, m2));
+    }
+  }
+}
+
+__device__ __forceinline__ void copy_row(float4* dst, const float4* src) {
+  for (int i = threadIdx.x; i < apad(STREAM_F) / 2; i += NT) dst[i] = src[i];
+}
+
+// Row pass of one unit: rows ra and rb = (P - ra) mod P (one row when ra is 0 or P/2).  Every
+// pair (Z_k, Z_{L-k}) with k in row ra and L - k in row rb is visited once: k = ra + P k1 with
+//   ra != 0, P/2:  partner (rb, F-1-k1), k1 in [0, F)
+//   ra == P/2:     partner (ra, F-1-k1), k1 in [0, F/2)
+//   ra == 0:       partner (0, (F-k1) mod F), k1 in [0, F/2]  (k1 = 0 and F/2 pair with themselves)
+// prank holds, in this order, the rank in Omega of each of the pair's outputs (-1: not kept).
+// Forward: y[rank(f)] = X_f.  Inverse: X_f = u[rank(f)] (0 off Omega), and the DCT-III
+// pre-processing writes the pair back into the rows.  Four pairs per thread and step, their
+// global loads issued before any pair's arithmetic.
+__device__ __forceinline__ void stream_pairs(const Geo& g, int ra, float2* R0, float2* R1, const Tw& tw,
+                                             const int4* prank, bool inv, const float* u, float* y, int rot) {
+  constexpr int F = STREAM_F;
+  const int P = g.P;
+  const float wk = sqrtf(2.0f / (float)g.N), w0 = sqrtf(1.0f / (float)g.N);
+  const int npairs = (ra == 0) ? F / 2 + 1 : (2 * ra == P ? F / 2 : F);
+  float2* Rb = (ra == 0 || 2 * ra == P) ? R0 : R1;
+  rot %= npairs;
+  constexpr int U = 4;
+  for (int j0 = threadIdx.x; j0 < npairs; j0 += U * NT) {
+    int rk[U][4];
+    float xin[U][4];
+    int kk[U];
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const int j = j0 + v * NT;
+      kk[v] = j < npairs ? (j + rot < npairs ? j + rot : j + rot - npairs) : -1;
+      const int4 r = kk[v] >= 0 ? __ldg(prank + kk[v]) : make_int4(-1, -1, -1, -1);
+      rk[v][0] = r.x; rk[v][1] = r.y; rk[v][2] = r.z; rk[v][3] = r.w;
+    }
+    if (inv) {
+#pragma unroll
+      for (int v = 0; v < U; ++v)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xin[v][i] = rk[v][i] >= 0 ? __ldg(u + rk[v][i]) : 0.f;
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const int k1 = kk[v];
+      if (k1 < 0) continue;
+      const int kb = ra == 0 ? ((F - k1) & (F - 1)) : F - 1 - k1;
+      const int k = ra + P * k1;
+      const bool self = ra == 0 && (k1 == 0 || 2 * k1 == F);
+      const PairTw pt = pair_tw(tw, k);
+      if (!inv) {
+        float X[4] = {0.f, 0.f, 0.f, 0.f};
+        dct2_pair(R0[aidx(k1)], Rb[aidx(kb)], k, pt, wk, w0, X);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (rk[v][i] >= 0) y[rk[v][i]] = X[i];
+      } else {
+        float2 Va, Vb;
+        dct3_pair(xin[v], k, self, pt, wk, w0, Va, Vb);
+        R0[aidx(k1)] = Va;
+        if (!self) Rb[aidx(kb)] = Vb;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Offset of unit ra's first pair in the pair table (units in order ra = 0, 1, ..., P/2).
+__host__ __device__ inline int stream_pair_base(int ra) { return ra == 0 ? 0 : STREAM_F / 2 + 1 + (ra - 1) * STREAM_F; }
+
+// One unit of the row pass (rows ra and (P - ra) mod P), forward or inverse.
+__device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, int ra, int rot) {
+  constexpr int F = STREAM_F;
+  float2* R0 = reinterpret_cast<float2*>(smem_raw);
+  float2* R1 = R0 + apad(F);
+  float2* TB = R1 + apad(F);
+  const OpDev& op = a.op;
+  const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1};
+  Geo g;
+  g.N = op.N; g.L = op.N >> 1; g.P = op.P; g.F = F; g.c = 0; g.h = 0; g.lh = 0; g.S2 = 0; g.four_n = 4 * op.N;
+  const int rs = apad(F);
+  const int rb = (op.P - ra) & (op.P - 1);
+  if (a.mode == MODE_APPLY) {
+    copy_row(reinterpret_cast<float4*>(R0), reinterpret_cast<const float4*>(T + ra * rs));
+    if (rb != ra) copy_row(reinterpret_cast<float4*>(R1), reinterpret_cast<const float4*>(T + rb * rs));
+    __syncthreads();
+    local_fft<-1>(R0, TB, F, tw, g.four_n);
+    if (rb != ra) local_fft<-1>(R1, TB, F, tw, g.four_n);
+    stream_pairs(g, ra, R0, R1, tw, a.prank + stream_pair_base(ra), false, nullptr, a.out + (size_t)b * op.M, rot);
+  } else {
+    stream_pairs(g, ra, R0, R1, tw, a.prank + stream_pair_base(ra), true, a.in + (size_t)b * op.M, nullptr, rot);
+    local_fft<1>(R0, TB, F, tw, g.four_n);
+    if (rb != ra) local_fft<1>(R1, TB, F, tw, g.four_n);
+    copy_row(reinterpret_cast<float4*>(T + ra * rs), reinterpret_cast<const float4*>(R0));
+    if (rb != ra) copy_row(reinterpret_cast<float4*>(T + rb * rs), reinterpret_cast<const float4*>(R1));
+    __syncthreads();   // R0 / R1 are rewritten by the next unit
+  }
+}
+
+// Row pass share of CTA c of nc: units u = c, c + nc, ... of the P/2 units {rows 0 and P/2},
+// {1, P-1}, ..., {P/2-1, P/2+1} (two rows each).
+__device__ __forceinline__ void stream_rows(const StreamArgs& a, int b, float2* T, int rot, int c, int nc) {
+  const int P = a.op.P;
+  for (int u = c; u < P / 2; u += nc) {
+    if (u == 0) {
+      stream_unit(a, b, T, 0, rot);
+      stream_unit(a, b, T, P / 2, rot);
+    } else {
+      stream_unit(a, b, T, u, rot);
+    }
+  }
+}
+
+template <int PT>
+__device__ __noinline__ void stream_cols(const StreamArgs& a, int b, float2* T, int rot, int c, int nc) {
+  constexpr int F = STREAM_F;
+  const OpDev& op = a.op;
+  float2* TB = reinterpret_cast<float2*>(smem_raw) + 2 * apad(F);
+  const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1};
+  if (a.mode == MODE_APPLY)
+    stream_cols_fwd<PT>(reinterpret_cast<const float4*>(a.in + (size_t)b * op.N), a.dbits, T, tw, rot, c, nc);
+  else
+    stream_cols_inv<PT>(T, a.dbits, reinterpret_cast<float4*>(a.out + (size_t)b * op.N), tw, rot, c, nc);
+}
+
+__device__ __forceinline__ void stream_cols_any(const StreamArgs& a, int b, float2* T, int rot, int c, int nc) {
+  switch (a.op.P) {
+    case 2: stream_cols<2>(a, b, T, rot, c, nc); break;
+    case 4: stream_cols<4>(a, b, T, rot, c, nc); break;
+    case 8: stream_cols<8>(a, b, T, rot, c, nc); break;
+    default: stream_cols<16>(a, b, T, rot, c, nc); break;
+  }
+}
+
+// One cluster of nc CTAs per vector; the intermediate rows T of a vector live in the cluster's
+// global buffer and are shared by its CTAs, with a cluster barrier between the two passes and
+// after each vector (the next vector rewrites T).
+__global__ void __launch_bounds__(NT, 1) stream_kernel(const StreamArgs a) {
+  constexpr int F = STREAM_F;
+  const OpDev& op = a.op;
+  cg::cluster_group cl = cg::this_cluster();
+  const int nc = (int)cl.num_blocks();
+  const int c = (int)cl.block_rank();
+  const int cid = blockIdx.x / nc;
+  const int ncl = gridDim.x / nc;
+  {
+    float2* twlo = reinterpret_cast<float2*>(smem_raw) + 3 * apad(F);
+    float2* twhi = twlo + apad(1 << op.lo_bits);
+    const int nlo = 1 << op.lo_bits, nhi = 1 << op.hi_bits;
+    for (int i = threadIdx.x; i < nlo; i += NT) twlo[aidx(i)] = op.tw[i];
+    for (int i = threadIdx.x; i < nhi; i += NT) twhi[i] = op.tw[nlo + i];
+  }
+  __syncthreads();
+  float2* T = a.T + (size_t)cid * op.P * apad(F);
+  // clusters walk the shared tables (sign bits, pair ranks) from different warp-aligned
+  // offsets, so that concurrent clusters do not all read the same few L2 lines at once
+  const int rot = (int)((cid * 37u * 32u) & (F / 2 - 1));
+  for (int b = cid; b < a.B; b += ncl) {
+    if (a.mode == MODE_APPLY) {
+      stream_cols_any(a, b, T, rot, c, nc);
+      cl.sync();   // every row of T is complete
+      stream_rows(a, b, T, rot, c, nc);
+    } else {
+      stream_rows(a, b, T, rot, c, nc);
+      cl.sync();
+      stream_cols_any(a, b, T, rot, c, nc);
+    }
+    cl.sync();     // nobody reads T any more: the next vector may rewrite it
+  }
+}
+
+size_t stream_row_floats() { return 2 * (size_t)apad(STREAM_F); }
+
+static size_t stream_smem() {
+  // rows R0, R1, the FFT ping-pong buffer, and twiddle levels of up to 1024 entries each
+  return sizeof(float2) * (3 * (size_t)apad(STREAM_F) + apad(1024) + 1024);
+}
+
+static cudaLaunchConfig_t stream_config(int nc, int clusters, cudaStream_t stream, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc * clusters);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = stream_smem();
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+int stream_clusters(int nc) {
+  if (cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stream_smem()) != cudaSuccess)
+    return 0;
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = stream_config(nc, 1, nullptr, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, stream_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_stream(const StreamArgs& a, int nc, int clusters, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stream_smem());
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = stream_config(nc, clusters, stream, attr);
+  return cudaLaunchKernelEx(&cfg, stream_kernel, a);
 }
 
 }  // namespace csg

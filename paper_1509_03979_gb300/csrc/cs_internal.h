@@ -99,6 +99,24 @@ __host__ __device__ constexpr size_t scratch_floats_per_cta(int F_alloc) {
   return (size_t)SCRATCH_ARRAYS * 2 * F_alloc + rank_ints_per_cta(F_alloc);
 }
 
+// Streamed batched operator (A x or A^T u for a batch of vectors, one CTA per vector): rows of
+// STREAM_F points, P = N / (2 STREAM_F) rows, for STREAM_N_MIN <= N <= N_MAX.
+constexpr int STREAM_F = F_MAX;
+constexpr int STREAM_N_MIN = 4 * STREAM_F;   // P >= 2
+struct StreamArgs {
+  OpDev op;                  // N, M, P, twiddles and Omega tables
+  const uint32_t* dbits;     // [N/32] sign bits of d (bit set: d_n = -1)
+  const int4* prank;         // [N/4 + 1] per DCT pair of the row pass: ranks in Omega of its outputs
+  int mode;                  // MODE_APPLY or MODE_APPLY_T
+  int B;                     // vectors
+  const float* in;           // [B][N] (A) or [B][M] (A^T), contiguous
+  float* out;                // [B][M] (A) or [B][N] (A^T)
+  float2* T;                 // per cluster: [P][apad(STREAM_F)] intermediate rows
+};
+size_t stream_row_floats();    // floats of one padded intermediate row
+int stream_clusters(int nc);   // clusters of nc CTAs resident at once (0: cannot launch)
+cudaError_t launch_stream(const StreamArgs& a, int nc, int clusters, cudaStream_t stream);
+
 SmemPlan cluster_plan(int F_alloc);
 SmemPlan grid_plan(const OpDev& op);
 size_t smem_bytes(const SmemPlan& plan);
