@@ -2175,8 +2175,8 @@ __device__ __forceinline__ void copy_row(float4* dst, const float4* src) {
 //   ra == 0:       partner (0, (F-k1) mod F), k1 in [0, F/2]  (k1 = 0 and F/2 pair with themselves)
 // prank holds, in this order, the rank in Omega of each of the pair's outputs (-1: not kept).
 // Forward: y[rank(f)] = X_f.  Inverse: X_f = u[rank(f)] (0 off Omega), and the DCT-III
-// pre-processing writes the pair back into the rows.  Four pairs per thread and step, their
-// global loads issued before any pair's arithmetic.
+// pre-processing writes the pair back into the rows.  The global loads (ranks, and u for the
+// inverse) are software-pipelined one or two steps ahead of the arithmetic.
 __device__ __forceinline__ void stream_pairs(const Geo& g, int ra, float2* R0, float2* R1, const Tw& tw,
                                              const int4* prank, bool inv, const float* u, float* y, int rot) {
   constexpr int F = STREAM_F;
@@ -2185,41 +2185,79 @@ __device__ __forceinline__ void stream_pairs(const Geo& g, int ra, float2* R0, f
   const int npairs = (ra == 0) ? F / 2 + 1 : (2 * ra == P ? F / 2 : F);
   float2* Rb = (ra == 0 || 2 * ra == P) ? R0 : R1;
   rot %= npairs;
-  constexpr int U = 4;
-  for (int j0 = threadIdx.x; j0 < npairs; j0 += U * NT) {
-    int rk[U][4];
-    float xin[U][4];
-    int kk[U];
+  // pair j of this thread's sequence -> k1 (rotated start), -1 past the end
+  auto k1_of = [&](int j) { return j < npairs ? (j + rot < npairs ? j + rot : j + rot - npairs) : -1; };
+  auto ranks = [&](int k1) { return k1 >= 0 ? __ldg(prank + k1) : make_int4(-1, -1, -1, -1); };
+  auto pair_geo = [&](int k1, int& kb, int& k, bool& self) {
+    kb = ra == 0 ? ((F - k1) & (F - 1)) : F - 1 - k1;
+    k = ra + P * k1;
+    self = ra == 0 && (k1 == 0 || 2 * k1 == F);
+  };
+  if (!inv) {
+    // software pipeline: the rank loads of the next U pairs are in flight during this step
+    constexpr int U = 4;
+    int4 rn[U];
 #pragma unroll
-    for (int v = 0; v < U; ++v) {
-      const int j = j0 + v * NT;
-      kk[v] = j < npairs ? (j + rot < npairs ? j + rot : j + rot - npairs) : -1;
-      const int4 r = kk[v] >= 0 ? __ldg(prank + kk[v]) : make_int4(-1, -1, -1, -1);
-      rk[v][0] = r.x; rk[v][1] = r.y; rk[v][2] = r.z; rk[v][3] = r.w;
-    }
-    if (inv) {
+    for (int v = 0; v < U; ++v) rn[v] = ranks(k1_of(threadIdx.x + v * NT));
+    for (int j0 = threadIdx.x; j0 < npairs; j0 += U * NT) {
+      int4 rc[U];
 #pragma unroll
-      for (int v = 0; v < U; ++v)
+      for (int v = 0; v < U; ++v) {
+        rc[v] = rn[v];
+        rn[v] = ranks(k1_of(j0 + (U + v) * NT));
+      }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) xin[v][i] = rk[v][i] >= 0 ? __ldg(u + rk[v][i]) : 0.f;
-    }
-#pragma unroll
-    for (int v = 0; v < U; ++v) {
-      const int k1 = kk[v];
-      if (k1 < 0) continue;
-      const int kb = ra == 0 ? ((F - k1) & (F - 1)) : F - 1 - k1;
-      const int k = ra + P * k1;
-      const bool self = ra == 0 && (k1 == 0 || 2 * k1 == F);
-      const PairTw pt = pair_tw(tw, k);
-      if (!inv) {
+      for (int v = 0; v < U; ++v) {
+        const int k1 = k1_of(j0 + v * NT);
+        if (k1 < 0) continue;
+        int kb, k;
+        bool self;
+        pair_geo(k1, kb, k, self);
         float X[4] = {0.f, 0.f, 0.f, 0.f};
-        dct2_pair(R0[aidx(k1)], Rb[aidx(kb)], k, pt, wk, w0, X);
+        dct2_pair(R0[aidx(k1)], Rb[aidx(kb)], k, pair_tw(tw, k), wk, w0, X);
+        const int r[4] = {rc[v].x, rc[v].y, rc[v].z, rc[v].w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          if (rk[v][i] >= 0) y[rk[v][i]] = X[i];
-      } else {
+          if (r[i] >= 0) y[r[i]] = X[i];
+      }
+    }
+  } else {
+    // three stages: ranks two steps ahead, the u values they address one step ahead
+    constexpr int U = 2;
+    int4 r2[U], r1[U];
+    float x1[U][4];
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      r1[v] = ranks(k1_of(threadIdx.x + v * NT));
+      r2[v] = ranks(k1_of(threadIdx.x + (U + v) * NT));
+    }
+#pragma unroll
+    for (int v = 0; v < U; ++v) {
+      const int r[4] = {r1[v].x, r1[v].y, r1[v].z, r1[v].w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x1[v][i] = r[i] >= 0 ? __ldg(u + r[i]) : 0.f;
+    }
+    for (int j0 = threadIdx.x; j0 < npairs; j0 += U * NT) {
+      float xc[U][4];
+#pragma unroll
+      for (int v = 0; v < U; ++v) {
+        const int r[4] = {r2[v].x, r2[v].y, r2[v].z, r2[v].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          xc[v][i] = x1[v][i];
+          x1[v][i] = r[i] >= 0 ? __ldg(u + r[i]) : 0.f;
+        }
+        r2[v] = ranks(k1_of(j0 + (2 * U + v) * NT));
+      }
+#pragma unroll
+      for (int v = 0; v < U; ++v) {
+        const int k1 = k1_of(j0 + v * NT);
+        if (k1 < 0) continue;
+        int kb, k;
+        bool self;
+        pair_geo(k1, kb, k, self);
         float2 Va, Vb;
-        dct3_pair(xin[v], k, self, pt, wk, w0, Va, Vb);
+        dct3_pair(xc[v], k, self, pair_tw(tw, k), wk, w0, Va, Vb);
         R0[aidx(k1)] = Va;
         if (!self) Rb[aidx(kb)] = Vb;
       }

@@ -2,9 +2,11 @@
 
     python -m paper_1509_03979_gb300.profile_case --case apply --N 262144 --batch 16 --reps 2
     python -m paper_1509_03979_gb300.profile_case --case sp --N 262144 --batch 1
+    python -m paper_1509_03979_gb300.profile_case --case apply --impl streamed --batch 64
 
-Cases: apply / apply_t (batched A or A^T over `batch` random vectors), sp / omp / ompr
-(batched recovery of `batch` synthetic signals with M = N/4, K = M/10).
+Cases: apply / apply_t (batched A or A^T over `batch` random vectors, through the batched
+implementation `impl`: auto, cluster or streamed), sp / omp / ompr (batched recovery of `batch`
+synthetic signals with M = N/4, K = M/10).
 """
 import argparse
 
@@ -20,9 +22,11 @@ def main():
     ap.add_argument("--N", type=int, default=1 << 18)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--impl", default="auto", choices=["auto", "cluster", "streamed"])
     a = ap.parse_args()
     N, M = a.N, a.N // 4
     op = binding.Operator(N, M, 0x0C5002)
+    op.set_batched_impl(a.impl)
     dev = torch.device("cuda")
     g = torch.Generator(device=dev).manual_seed(0)
     if a.case in ("apply", "apply_t"):
