@@ -40,9 +40,11 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="signals per GPU per step (0 = fill the GPU)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-batch", type=int, default=256)
-    ap.add_argument("--workload", default="sp18", choices=["sp18", "batched", "ompr22", "ls16"],
+    ap.add_argument("--workload", default="sp18", choices=["sp18", "batched", "ompr22", "ls16", "paper"],
                     help="sp18: SP at N=2^18 (default); batched: mixed-size batch vs a loop of single "
-                         "calls; ompr22: OMPR at N=2^22; ls16: differentiable LS, 32 signals at N=2^16")
+                         "calls; ompr22: OMPR at N=2^22; ls16: differentiable LS, 32 signals at N=2^16; "
+                         "paper: the paper's own workload and CG precisions over N (Tables II-IV)")
+    ap.add_argument("--paper-max-log2n", type=int, default=22, help="largest log2 N of the paper sweep")
     ap.add_argument("--batched-count", type=int, default=256)
     return ap.parse_args()
 
@@ -487,6 +489,73 @@ def run_single_workload(args, rank, world, local_rank):
     op.close()
 
 
+# Seconds per recovery that the paper reports for its CPU/Matlab runs (Tables II-IV), by
+# log2 N: (exact precision, xi = 1e-10, xi = 1e-5).  Context only: other hardware and FP64.
+PAPER_SECONDS = {
+    "omp": {11: (1.2, 0.6, 0.4), 12: (4.7, 2.3, 1.8), 13: (16.2, 8.7, 7.0), 14: (59.8, 35.5, 26.9),
+            15: (241.0, 131.3, 103.6), 16: (980.3, 564.7, 432.1), 17: (3901.7, 2143.9, 1662.8),
+            18: (15301.4, 8341.3, 6479.2)},
+    "ompr": {11: (0.2, 0.1, 0.06), 12: (0.3, 0.2, 0.09), 13: (0.6, 0.3, 0.2), 14: (1.0, 0.5, 0.3),
+             15: (1.9, 1.0, 0.6), 16: (4.1, 2.2, 1.3), 17: (10.5, 4.8, 2.9), 18: (23.6, 10.1, 6.0),
+             19: (51.8, 23.6, 13.1), 20: (111.3, 49.8, 27.7), 21: (232.1, 113.9, 60.3),
+             22: (495.3, 249.3, 131.3), 23: (1109.1, 532.3, 293.4), 24: (2392.3, 1130.4, 643.6)},
+    "sp": {11: (0.3, 0.2, 0.09), 12: (0.5, 0.3, 0.2), 13: (0.9, 0.5, 0.4), 14: (1.5, 0.8, 0.6),
+           15: (3.0, 1.6, 0.9), 16: (6.2, 3.6, 2.1), 17: (16.6, 7.8, 5.2), 18: (37.9, 17.3, 10.0),
+           19: (79.4, 36.1, 22.5), 20: (173.2, 78.3, 49.1), 21: (359.2, 177.6, 109.2),
+           22: (740.6, 382.9, 241.6), 23: (1581.3, 784.5, 513.2), 24: (3195.4, 1706.3, 1096.8)},
+}
+
+
+def run_paper_sweep(args, rank, local_rank):
+    """The paper's simulation setting (Sec. IV-A: M = N/4, K = N/16, sigma_on = 1, absolute noise
+    sigma_eta = 0.01) with its CG precisions (Sec. IV-C): xi = 1e-5 absolute, and exact precision
+    (xi = 0, at most |S| steps), which in FP32 stops at the floor ||r|| <= 1e-6 ||b|| -- the same
+    computation as xi = 1e-10.  One timed recovery per (decoder, N, precision) after a warm-up on
+    the same input; SNR = 20 log10(||s|| / ||s_hat - s||)."""
+    import torch
+    from paper_1509_03979_gb300 import binding
+
+    torch.cuda.set_device(local_rank)
+    devc = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    rows = []
+    sizes = {"omp": range(11, min(16, args.paper_max_log2n) + 1),
+             "sp": range(11, args.paper_max_log2n + 1), "ompr": range(11, args.paper_max_log2n + 1)}
+    for algo in ("omp", "sp", "ompr"):
+        for e in sizes[algo]:
+            N = 1 << e
+            M, K, s, noise = synth.paper_workload(N, 0x1509 + e)
+            op = binding.Operator(N, M, 0x1509 + e)
+            op.set_cg_tol_mode("absolute")
+            sd = torch.from_numpy(s.astype(np.float32)).to(devc)
+            y = (op.apply(sd) + torch.from_numpy(noise.astype(np.float32)).to(devc)).contiguous()
+            s_out = torch.empty(N, device=devc)
+            k_out = torch.empty(K, dtype=torch.int32, device=devc)
+            for name, xi in (("xi=1e-5", 1e-5), ("exact", 0.0)):
+                op.recover(y, K, algo, xi, 0, s_out, k_out)     # warm-up on the same input
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                op.recover(y, K, algo, xi, 0, s_out, k_out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                st = op.stats()
+                err = float(torch.linalg.norm(s_out - sd))
+                snr = 20.0 * np.log10(float(torch.linalg.norm(sd)) / max(err, 1e-30))
+                paper = PAPER_SECONDS[algo].get(e)
+                rows.append({"algo": algo, "log2N": e, "precision": name, "seconds": e0.elapsed_time(e1) / 1e3,
+                             "snr_db": snr, "outer_iters": st["outer_iters"], "cg_iters": st["cg_iters_total"],
+                             "status": st["status"],
+                             "paper_seconds": None if paper is None else (paper[2] if name == "xi=1e-5" else paper[0])})
+            op.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "paper workload sweep: seconds per recovery and SNR (dB)", "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "M=N/4, K=N/16, sigma_on=1, sigma_eta=0.01 (Sec. IV-A); xi absolute",
+                       "paper_seconds": "Tables II-IV, Matlab on a Core 2 Quad Q6600, FP64 (context)"},
+            "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -506,6 +575,8 @@ def main():
             run_batched(args, rank, world, local_rank)
         elif args.workload in ("ompr22", "ls16"):
             run_single_workload(args, rank, world, local_rank)
+        elif args.workload == "paper":
+            run_paper_sweep(args, rank, local_rank)
         else:
             run_gb300(args, rank, world, local_rank)
     finally:

@@ -28,8 +28,14 @@
  *     (such signals are processed one after another, also inside the batched calls).
  *     A grid-wide wait that does not finish within its iteration limit ends the launch early:
  *     recoveries report CS_ERR_TIMEOUT in cs_stats.status, every call through cs_op_sync.
- *   - cg_tol is RELATIVE: CG stops when ||r_j|| <= cg_tol * ||W A^T y|| (or after cg_maxit
- *     steps; reaching cg_maxit is not an error, it is counted in cs_stats.cg_maxit_hits).
+ *   - cg_tol is RELATIVE by default: CG stops when ||r_j|| <= cg_tol * ||W A^T y|| (or after
+ *     cg_maxit steps; reaching cg_maxit is not an error, it is counted in
+ *     cs_stats.cg_maxit_hits).  cs_op_set_cg_tol_mode(op, CS_CG_TOL_ABSOLUTE) makes it the
+ *     paper's absolute xi on ||r_j|| (Algorithm 1), floored at the FP32 limit: an absolute
+ *     solve also stops once ||r_j|| <= 1e-6 ||W A^T y||, so xi = 0 (the paper's exact
+ *     precision, Sec. IV-C) or xi = 1e-10 yields the LS solution to FP32 precision.
+ *     cg_maxit = 0 means at most |S| steps, the bound of Theorem 5.  A step whose H d
+ *     vanishes in FP32 ends the solve (the residual is at rounding level).
  *   - cs_last_error() returns a thread-local message describing the last failure.
  *   - Operators are not thread-safe: one host thread at a time per cs_op_t.
  */
@@ -101,6 +107,11 @@ cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N);
  * the streamed kernel (2 CTAs per vector) whenever N allows it and B >= 2. */
 cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y);
 cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X);
+
+enum { CS_CG_TOL_RELATIVE = 0, CS_CG_TOL_ABSOLUTE = 1 };
+/* Stopping rule of every CG solve of this op's later recover / LS calls (see the conventions
+ * above): CS_CG_TOL_RELATIVE (default) or CS_CG_TOL_ABSOLUTE (Algorithm 1's ||r_j|| <= xi). */
+cs_status cs_op_set_cg_tol_mode(cs_op_t op, int32_t mode);
 
 enum { CS_BATCHED_AUTO = 0, CS_BATCHED_CLUSTER = 1, CS_BATCHED_STREAMED = 2 };
 /* Choose the implementation of cs_op_apply_batched / cs_op_apply_t_batched for this op.

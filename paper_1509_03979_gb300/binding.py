@@ -41,6 +41,7 @@ SIGNATURES = {
     "cs_op_apply_t_batched": (_I32, [_P, _I32, _P, _P]),
     "cs_op_concurrency": (_I32, [_P]),
     "cs_op_set_batched_impl": (_I32, [_P, _I32]),
+    "cs_op_set_cg_tol_mode": (_I32, [_P, _I32]),
     "cs_op_tune_batched": (_I32, [_P, _I32, _P]),
     "cs_operator_draws": (_I32, [_I64, _I64, _U64, _P, _P]),
     "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
@@ -158,6 +159,10 @@ class Operator:
     def concurrency(self):
         """Signals of this size the GPU runs at once (resident clusters)."""
         return int(lib().cs_op_concurrency(self._h))
+
+    def set_cg_tol_mode(self, mode):
+        """CG stopping rule of later recover / LS calls: 'relative' (to ||b||) or 'absolute'."""
+        _check(lib().cs_op_set_cg_tol_mode(self._h, {"relative": 0, "absolute": 1}[mode]))
 
     BATCHED_IMPLS = {"auto": 0, "cluster": 1, "streamed": 2}
 

@@ -91,6 +91,7 @@ struct cs_op {
   uint32_t* d_dbits = nullptr;  // [N/32] sign bits of d, for the streamed batched operator
   int32_t* d_prank = nullptr;   // [N/4 + 1][4] Omega ranks of the streamed row pass's pair outputs
   int batched_impl = CS_BATCHED_AUTO;
+  int cg_abs = 0;               // CG stopping rule: 0 relative, 1 absolute (cs_op_set_cg_tol_mode)
   int tuned_nc[2] = {0, 0};     // per mode (A, A^T): 0 untuned, -1 cluster engine, else CTAs per vector
 };
 
@@ -120,6 +121,7 @@ Task base_task(const cs_op* op, int mode) {
   t.k_in = 0;
   t.cg_tol = 1e-6f;
   t.cg_maxit = 100;
+  t.cg_abs = op->cg_abs;
   t.outer_max = 0;
   t.stats = op->d_stats;
   t.grid_scratch = op->d_scratch;
@@ -156,7 +158,7 @@ cs_status run_single(cs_op* op, const Task& t) {
 }
 
 cs_status check_cg(float cg_tol, int32_t cg_maxit) {
-  if (!(cg_tol >= 0.f) || cg_maxit < 1) return fail(CS_ERR_INVALID_ARG, "cg_tol must be >= 0 and cg_maxit >= 1");
+  if (!(cg_tol >= 0.f) || cg_maxit < 0) return fail(CS_ERR_INVALID_ARG, "cg_tol must be >= 0 and cg_maxit >= 0");
   return CS_OK;
 }
 
@@ -433,6 +435,13 @@ cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y) {
 
 cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X) {
   return apply_batched(op, MODE_APPLY_T, B, U, X);
+}
+
+cs_status cs_op_set_cg_tol_mode(cs_op_t op, int32_t mode) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  if (mode != CS_CG_TOL_RELATIVE && mode != CS_CG_TOL_ABSOLUTE) return fail(CS_ERR_INVALID_ARG, "unknown CG tolerance mode");
+  op->cg_abs = mode == CS_CG_TOL_ABSOLUTE ? 1 : 0;
+  return CS_OK;
 }
 
 cs_status cs_op_set_batched_impl(cs_op_t op, int32_t impl) {

@@ -459,6 +459,7 @@ struct Ctx {
   OpDev op;           // the operator (grid launches read its streamed geometry and buffers)
   int ring_slot;      // next cluster-reduction slot (all CTAs advance it identically)
   int hist_slot;      // next radix-histogram buffer
+  int cg_abs;         // CG stopping rule of the current task: 1 absolute, 0 relative
   int cg_total;       // statistics (thread 0 only)
   int cg_hits;
   int ntrans;         // N-point DCT applications (forward or inverse)
@@ -1424,6 +1425,7 @@ __device__ __forceinline__ float corr_at(const SigView& sv, const uint32_t* sign
 
 // ------------------------------------------------------------------------------------ CG
 enum R0Src : int { R0_FROM_A = 0, R0_FROM_CY = 1 };
+constexpr float CG_FP32_FLOOR = 1e-6f;   // relative residual FP32 CG reaches reliably
 
 // Algorithm 1's CG on H = W A^T A W restricted to the support in the local list (Theorem 5's
 // |S|-compressed form), b = W A^T y whose by-slot values are in cy.  Start from x0 = xd[wi]
@@ -1439,7 +1441,7 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
   float* cgx = C.cgx;
   float* cgr = C.cgr;
   float* cgp = C.cgp;
-  float v[2] = {0.f, 0.f};
+  float v[3] = {0.f, 0.f, threadIdx.x == 0 ? (float)nloc : 0.f};   // ||r0||^2, ||b||^2, |S|
   for (int i = threadIdx.x; i < nloc; i += NT) {
     const int sg = list[i];
     const float x0 = warm ? xd[sg] : 0.f;
@@ -1451,9 +1453,15 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
     v[0] = fmaf(r0, r0, v[0]);
     v[1] = fmaf(b, b, v[1]);
   }
-  cluster_sum(v, 2);
+  cluster_sum(v, 3);
   float rr = v[0];
-  const float stop2 = tol * tol * v[1];
+  // Algorithm 1's test on ||r_j||: absolute (the paper's xi) or relative to ||b||; maxit = 0
+  // takes Theorem 5's bound of |S| steps.  An absolute xi below what FP32 CG can reach (the
+  // paper's exact precision xi = 0, or xi = 1e-10) stops at the FP32 floor ||r_j|| <=
+  // CG_FP32_FLOOR ||b||: past it the recursive residual no longer tracks b - H x and the
+  // iterate drifts.
+  const float stop2 = C.cg_abs ? fmaxf(tol * tol, CG_FP32_FLOOR * CG_FP32_FLOOR * v[1]) : tol * tol * v[1];
+  if (maxit == 0) maxit = (int)v[2];
   int it = 0;
   while (it < maxit && rr > stop2) {
     transform(SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
@@ -1472,6 +1480,7 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
       pq = fmaf(pp[i], q, pq);
     }
     cluster_sum(&pq, 1);
+    if (!(pq > 0.f)) break;   // H d = 0 in FP32: the residual is at rounding level (uniform: pq is cluster-wide)
     const float alpha = rr / pq;
     float rn = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
@@ -1883,6 +1892,7 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     C.nwords = (2 * op.F + 31) / 32;
     C.omask = op.omask; C.orank = op.orank;
     C.cg_total = 0; C.cg_hits = 0; C.ntrans = 0;
+    C.cg_abs = tp->cg_abs;
     const size_t a = 2 * (size_t)F_alloc;
     C.list = C.glist;
     C.cgx = C.gcg; C.cgr = C.gcg + a; C.cgp = C.gcg + 2 * a; C.cgq = C.gcg + 3 * a;

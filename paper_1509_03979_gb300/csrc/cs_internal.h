@@ -68,7 +68,8 @@ struct Task {
   int K;                     // sparsity (recover)
   int k_in;                  // support length (LS modes)
   float cg_tol;
-  int cg_maxit;
+  int cg_maxit;              // 0: at most |S| steps (Theorem 5)
+  int cg_abs;                // 1: cg_tol bounds ||r_j|| absolutely, 0: relative to ||b||
   int outer_max;             // SP rounds / OMPR swaps cap
   const float* in;
   const int32_t* supp_in;    // [k_in] (LS modes)

@@ -139,3 +139,16 @@ def batched_workload(B=256, seed=0x0B000, e_min=12, e_max=18):
         out.append(Problem(N, M, K, algo, op_seed=base, signal_seed=base + 1,
                            noise_seed=base + 2, noise_rel=1e-3))
     return out
+
+
+PAPER_SIGMA_ETA = 0.01   # Sec. IV-A: sigma_on = 1, sigma_eta = 0.01 (absolute)
+
+
+def paper_workload(N, seed):
+    """The paper's own simulation setting (Sec. IV-A): M = N/4, K = M/4 = N/16 (p = 0.0625),
+    N(0,1) nonzeros at K random positions, and the absolute noise vector sigma_eta * N(0,1) of
+    length M that is added to A s.  Returns (M, K, s, noise)."""
+    M, K = N // 4, N // 16
+    s = sparse_gaussian(N, K, seed)
+    noise = PAPER_SIGMA_ETA * normals(seed ^ 0x40150, M)
+    return M, K, s, noise
