@@ -40,10 +40,11 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="signals per GPU per step (0 = fill the GPU)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-batch", type=int, default=256)
-    ap.add_argument("--workload", default="sp18", choices=["sp18", "batched", "ompr22", "ls16", "paper"],
+    ap.add_argument("--workload", default="sp18", choices=["sp18", "batched", "ompr22", "ls16", "paper", "omp4k"],
                     help="sp18: SP at N=2^18 (default); batched: mixed-size batch vs a loop of single "
                          "calls; ompr22: OMPR at N=2^22; ls16: differentiable LS, 32 signals at N=2^16; "
-                         "paper: the paper's own workload and CG precisions over N (Tables II-IV)")
+                         "paper: the paper's own workload and CG precisions over N (Tables II-IV); "
+                         "omp4k: single-signal OMP at N=4096 with the autotuned cluster size")
     ap.add_argument("--paper-max-log2n", type=int, default=22, help="largest log2 N of the paper sweep")
     ap.add_argument("--batched-count", type=int, default=256)
     return ap.parse_args()
@@ -426,8 +427,9 @@ def run_batched(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------- single-signal workloads
 def run_single_workload(args, rank, world, local_rank):
-    """ompr22: OMPR + CG-LS at N = 2^22, M = 2^20, K = 83886, power-law signal (one recovery per
-    step, the whole GPU per signal).  ls16: forward LS solve + hand-written adjoint for 32
+    """omp4k: OMP + CG-LS at N = 4096, M = 1024, K = 64, one recovery per step on the cluster
+    size the recovery autotuner picks.  ompr22: OMPR + CG-LS at N = 2^22, M = 2^20, K = 83886,
+    power-law signal (one recovery per step, the whole GPU per signal).  ls16: forward LS solve + hand-written adjoint for 32
     signals at N = 2^16, M = 2^14, k = 1024 (one step = both batched launches)."""
     import torch
     from paper_1509_03979_gb300 import binding
@@ -435,7 +437,22 @@ def run_single_workload(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     devc = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    if args.workload == "ompr22":
+    extra = {}
+    if args.workload == "omp4k":
+        p = synth.workload(1)
+        op = binding.Operator(p.N, p.M, p.op_seed)
+        s = torch.from_numpy(p.signal().astype(np.float32)).to(devc)
+        y = op.apply(s).contiguous()
+        s_out = torch.empty(p.N, device=devc)
+        k_out = torch.empty(p.K, dtype=torch.int32, device=devc)
+        extra["tuner_ms_by_cluster_size"] = op.tune_recover(p.K, "omp", CG_TOL, CG_MAXIT)
+        extra["cluster_size"] = op.cluster_size()
+
+        def step():
+            op.recover(y, p.K, "omp", CG_TOL, CG_MAXIT, s_out, k_out)
+        units, unit, metric = 1, "recoveries/s", "recoveries/s (OMP + CG-LS, N=4096, one signal at a time)"
+        cfgname = "OMP+CG-LS N=4096 M=1024 K=64 noiseless, single signal (config 1)"
+    elif args.workload == "ompr22":
         p = synth.workload(3)
         op = binding.Operator(p.N, p.M, p.op_seed)
         s = torch.from_numpy(p.signal().astype(np.float32)).to(devc)
@@ -484,7 +501,7 @@ def run_single_workload(args, rank, world, local_rank):
             "metric": metric, "value": units * args.steps / t, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": cfgname}, "stats_last": stats,
+            "data": "synthetic", "config": dict({"workload": cfgname}, **extra), "stats_last": stats,
         }), flush=True)
     op.close()
 
@@ -573,7 +590,7 @@ def main():
     try:
         if args.workload == "batched":
             run_batched(args, rank, world, local_rank)
-        elif args.workload in ("ompr22", "ls16"):
+        elif args.workload in ("ompr22", "ls16", "omp4k"):
             run_single_workload(args, rank, world, local_rank)
         elif args.workload == "paper":
             run_paper_sweep(args, rank, local_rank)

@@ -108,6 +108,22 @@ cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N);
 cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y);
 cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X);
 
+/* Cluster size P (CTAs per signal) of this op's cluster engine, N <= 2^18 (no counterpart in
+ * the paper).  Default 0 = the smallest that holds the transform on chip (P = max(1, N/2^14)),
+ * which fits the most signals on the GPU at once; a larger P (power of two <= 16, N >= 4 P^2)
+ * spreads one signal over more SMs and lowers its latency.  Waits for the op's stream and
+ * reallocates the op's scratch.  CS_ERR_UNSUPPORTED_N for N > 2^18 (one geometry). */
+cs_status cs_op_set_cluster_size(cs_op_t op, int32_t P);
+int32_t cs_op_cluster_size(cs_op_t op);   /* current P (0 for a NULL op) */
+
+/* Autotuner of the single-signal recovery: times cs_recover(K, algo, cg_tol, cg_maxit) of an
+ * internal K-sparse test signal for every cluster size P in {1, 2, 4, 8, 16} that is valid
+ * for this op, keeps the fastest (cs_op_set_cluster_size), and writes the milliseconds per
+ * recovery to ms_out (HOST [5] or NULL; -1 where P does not apply).  Allocates and frees
+ * 2N + M + K words of device memory, synchronises the op's stream.  No-op for N > 2^18. */
+cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, int32_t cg_maxit,
+                             float* ms_out);
+
 enum { CS_CG_TOL_RELATIVE = 0, CS_CG_TOL_ABSOLUTE = 1 };
 /* Stopping rule of every CG solve of this op's later recover / LS calls (see the conventions
  * above): CS_CG_TOL_RELATIVE (default) or CS_CG_TOL_ABSOLUTE (Algorithm 1's ||r_j|| <= xi). */

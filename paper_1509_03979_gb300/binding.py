@@ -42,6 +42,9 @@ SIGNATURES = {
     "cs_op_concurrency": (_I32, [_P]),
     "cs_op_set_batched_impl": (_I32, [_P, _I32]),
     "cs_op_set_cg_tol_mode": (_I32, [_P, _I32]),
+    "cs_op_set_cluster_size": (_I32, [_P, _I32]),
+    "cs_op_cluster_size": (_I32, [_P]),
+    "cs_op_tune_recover": (_I32, [_P, _I32, _I32, _F32, _I32, _P]),
     "cs_op_tune_batched": (_I32, [_P, _I32, _P]),
     "cs_operator_draws": (_I32, [_I64, _I64, _U64, _P, _P]),
     "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
@@ -163,6 +166,21 @@ class Operator:
     def set_cg_tol_mode(self, mode):
         """CG stopping rule of later recover / LS calls: 'relative' (to ||b||) or 'absolute'."""
         _check(lib().cs_op_set_cg_tol_mode(self._h, {"relative": 0, "absolute": 1}[mode]))
+
+    def set_cluster_size(self, P):
+        """CTAs per signal of the cluster engine (0: the smallest that holds the transform)."""
+        _check(lib().cs_op_set_cluster_size(self._h, int(P)))
+
+    def cluster_size(self):
+        return int(lib().cs_op_cluster_size(self._h))
+
+    def tune_recover(self, K, algo="omp", cg_tol=1e-6, cg_maxit=100):
+        """Time a recovery for every valid cluster size, keep the fastest; returns {P: ms}."""
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        ms = (ctypes.c_float * 5)()
+        self._stream()
+        _check(lib().cs_op_tune_recover(self._h, int(K), a, float(cg_tol), int(cg_maxit), ms))
+        return {1 << i: ms[i] for i in range(5) if ms[i] >= 0}
 
     BATCHED_IMPLS = {"auto": 0, "cluster": 1, "streamed": 2}
 

@@ -437,6 +437,94 @@ cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X)
   return apply_batched(op, MODE_APPLY_T, B, U, X);
 }
 
+cs_status cs_op_set_cluster_size(cs_op_t op, int32_t P) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  if (op->dev.grid) return fail(CS_ERR_UNSUPPORTED_N, "the cluster size applies to N <= 2^18");
+  const int64_t L = op->N / 2;
+  const int Pmin = L > F_MAX ? (int)(L / F_MAX) : 1;
+  if (P == 0) P = Pmin;
+  if (P < Pmin || P > P_MAX || (P & (P - 1)) != 0 || L < 2 * (int64_t)P * P)
+    return fail(CS_ERR_INVALID_ARG, "cluster size must be a power of two with N/(2 F_max) <= P <= 16 and N >= 4 P^2");
+  const int F = (int)(L / P);
+  if (max_active_clusters(P, F) < 1) return fail(CS_ERR_UNSUPPORTED_N, "this cluster size cannot be scheduled on this device");
+  if (P == op->dev.P) return CS_OK;
+  cudaError_t e = cudaStreamSynchronize(op->stream);   // queued work still uses the old scratch
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  const size_t bytes = (size_t)P * scratch_floats_per_cta(F) * sizeof(float);
+  float* scratch = nullptr;
+  if ((e = cudaMalloc(&scratch, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(scratch)");
+  if ((e = cudaMemset(scratch, 0, bytes)) != cudaSuccess) {
+    cudaFree(scratch);
+    return cuda_fail(e, "cudaMemset(scratch)");
+  }
+  cudaFree(op->d_scratch);
+  op->d_scratch = scratch;
+  op->dev.P = P;
+  op->dev.F = F;
+  return CS_OK;
+}
+
+int32_t cs_op_cluster_size(cs_op_t op) { return op ? op->dev.P : 0; }
+
+cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, int32_t cg_maxit, float* ms_out) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  constexpr int NCAND = 5;
+  if (ms_out)
+    for (int i = 0; i < NCAND; ++i) ms_out[i] = -1.f;
+  if (op->dev.grid) return CS_OK;   // one geometry only
+  cs_status st = check_cg(cg_tol, cg_maxit);
+  if (st != CS_OK) return st;
+  if (K < 1 || K > op->M || (algo == CS_SP && 2 * (int64_t)K > op->M) || algo < 0 || algo > 2)
+    return fail(CS_ERR_INVALID_ARG, "K or algo out of range");
+  // a K-sparse test signal: evenly spread positions, values alternating in sign and size
+  std::vector<float> hs((size_t)op->N, 0.f);
+  for (int64_t i = 0; i < K; ++i) hs[(size_t)(i * op->N / K)] = (i & 1) ? -0.5f - 0.25f * (float)(i % 5) : 1.f;
+  float *s = nullptr, *y = nullptr, *so = nullptr;
+  int32_t* supp = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&s, sizeof(float) * (size_t)op->N);
+  if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(float) * (size_t)op->M);
+  if (e == cudaSuccess) e = cudaMalloc(&so, sizeof(float) * (size_t)op->N);
+  if (e == cudaSuccess) e = cudaMalloc(&supp, sizeof(int32_t) * (size_t)K);
+  if (e == cudaSuccess) e = cudaMemcpy(s, hs.data(), sizeof(float) * hs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) st = cuda_fail(e, "tuning buffers");
+  if (st == CS_OK) st = cs_op_apply(op, s, y);
+  const int start_P = op->dev.P;
+  int best_P = start_P;
+  float best = -1.f;
+  for (int ci = 0; ci < NCAND && st == CS_OK; ++ci) {
+    const int P = 1 << ci;
+    if (cs_op_set_cluster_size(op, P) != CS_OK) continue;   // not a valid shape for this N
+    float ms = -1.f;
+    for (int rep = 0; rep < 3 && st == CS_OK; ++rep) {     // one warm-up, then the faster of two
+      if ((e = cudaEventRecord(e0, op->stream)) != cudaSuccess) { st = cuda_fail(e, "event"); break; }
+      st = cs_recover(op, y, K, (cs_algo)algo, cg_tol, cg_maxit, so, supp);
+      if (st != CS_OK) break;
+      if ((e = cudaEventRecord(e1, op->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+        st = cuda_fail(e, "event");
+        break;
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0 && (ms < 0.f || t < ms)) ms = t;
+    }
+    if (st != CS_OK) break;
+    if (ms_out) ms_out[ci] = ms;
+    if (best < 0.f || ms < best) { best = ms; best_P = P; }
+  }
+  const cs_status st2 = cs_op_set_cluster_size(op, st == CS_OK ? best_P : start_P);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(op->stream);
+  cudaFree(s);
+  cudaFree(y);
+  cudaFree(so);
+  cudaFree(supp);
+  return st != CS_OK ? st : st2;
+}
+
 cs_status cs_op_set_cg_tol_mode(cs_op_t op, int32_t mode) {
   if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
   if (mode != CS_CG_TOL_RELATIVE && mode != CS_CG_TOL_ABSOLUTE) return fail(CS_ERR_INVALID_ARG, "unknown CG tolerance mode");
@@ -747,7 +835,8 @@ cs_status cs_op_sync(cs_op_t op) {
 namespace {
 
 constexpr int64_t NOALLOC_N_MAX = 1 << 16;                        // largest supported N
-constexpr size_t NOALLOC_SCRATCH = (size_t)(NOALLOC_N_MAX / 2 / F_MAX) * scratch_floats_per_cta(F_MAX);
+// P CTAs of F = N / 2P points need P (18 F + 128) floats, the most at P = P_MAX
+constexpr size_t NOALLOC_SCRATCH = (size_t)P_MAX * scratch_floats_per_cta(NOALLOC_N_MAX / 2 / P_MAX);
 constexpr size_t NOALLOC_BITS = (size_t)NOALLOC_N_MAX / 32;
 // 2.25 MiB of scratch floats followed by the N-bit support bitmask (8 KiB)
 static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH + NOALLOC_BITS];
@@ -782,6 +871,8 @@ extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, c
   if ((st = check_cg(cg_tol, cg_maxit)) != CS_OK) return st;
   if (op->N > NOALLOC_N_MAX)
     return fail(CS_ERR_INVALID_ARG, "cs_recover_noalloc supports N <= 65536 (fixed scratch size)");
+  if ((size_t)op->dev.P * scratch_floats_per_cta(op->dev.F) > NOALLOC_SCRATCH)
+    return fail(CS_ERR_INVALID_ARG, "cs_recover_noalloc: this cluster size needs more than the fixed scratch");
   if (K == 0) {
     cudaError_t e = cudaMemsetAsync(s_out, 0, sizeof(float) * (size_t)op->N, op->stream);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
