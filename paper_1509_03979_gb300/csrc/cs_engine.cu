@@ -945,6 +945,8 @@ __device__ __forceinline__ void dct3_pair(const float* X, int k, bool self, cons
 
 // Frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, and DCT-III
 // pre-processing back into the pair.  Returns this thread's MID_RESID sum of squares.
+// MASK: the kind is MID_MASK (the H d step), compiled without the y-side state.
+template <bool MASK>
 __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, const int4* rank4, int kind,
                                            bool fwd_done, bool inv, const float* vin, float* vout) {
   const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
@@ -967,7 +969,7 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
         rk[u][i] = -1;
         xin[u][i] = 0.f;
       }
-      if (kind == MID_MASK || t >= nt) continue;
+      if (MASK || t >= nt) continue;
       if (rank4) {
         const int4 r = rank4[t];
         rk[u][0] = r.x; rk[u][1] = r.y; rk[u][2] = r.z; rk[u][3] = r.w;
@@ -985,7 +987,7 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
         }
       }
     }
-    if (kind == MID_RESID || kind == MID_IN) {
+    if (!MASK && (kind == MID_RESID || kind == MID_IN)) {
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -1003,7 +1005,7 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
       const PairTw pt = pair_tw(tw, k);
       float X[4] = {0.f, 0.f, 0.f, 0.f};
       if (fwd_done) dct2_pair(B[kpa * S2 + sa], B[kpb * S2 + sb], k, pt, wk, w0, X);
-      if (kind == MID_MASK) {
+      if (MASK) {
         const uint32_t bits = fb[t];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -1034,9 +1036,14 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
   return acc;
 }
 
-__device__ __noinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
+template <bool MASK>
+__device__ __noinline__ float freq_half_k(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
   const Geo g = C.g;
-  return freq_core(g, shp(C.sm.B), shp(C.sm.fbits), C.rank4, kind, fwd_done, inv, vin, vout);
+  return freq_core<MASK>(g, shp(C.sm.B), shp(C.sm.fbits), C.rank4, kind, fwd_done, inv, vin, vout);
+}
+__device__ __forceinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
+  return kind == MID_MASK ? freq_half_k<true>(kind, fwd_done, inv, vin, vout)
+                          : freq_half_k<false>(kind, fwd_done, inv, vin, vout);
 }
 
 // Inverse exchange: P-point inverse DFT per column, cluster barrier, all-to-all pull back into
@@ -1213,7 +1220,9 @@ __device__ __noinline__ float grid_col_block(int j, int kind, bool fwd_done, boo
     col_fft<-1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
   }
   const int fbstride = (W / 2) * S2 + S2 + 1;
-  const float acc = freq_core(gb, X, shp(C.sm.fbits) + j * fbstride, nullptr, kind, fwd_done, inv, vin, vout);
+  const uint8_t* fbj = shp(C.sm.fbits) + j * fbstride;
+  const float acc = kind == MID_MASK ? freq_core<true>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout)
+                                     : freq_core<false>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout);
   __syncthreads();
   if (inv) {
     col_fft<1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
