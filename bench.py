@@ -528,7 +528,8 @@ def run_paper_sweep(args, rank, local_rank):
     sigma_eta = 0.01) with its CG precisions (Sec. IV-C): xi = 1e-5 absolute, and exact precision
     (xi = 0, at most |S| steps), which in FP32 stops at the floor ||r|| <= 1e-6 ||b|| -- the same
     computation as xi = 1e-10.  One timed recovery per (decoder, N, precision) after a warm-up on
-    the same input; SNR = 20 log10(||s|| / ||s_hat - s||)."""
+    the same input; SNR = 20 log10(||s|| / ||s_hat - s||).  OMPR runs both as the single-swap
+    decoder and as OMPR(l) with l = K/4 replacements per round."""
     import torch
     from paper_1509_03979_gb300 import binding
 
@@ -537,13 +538,17 @@ def run_paper_sweep(args, rank, local_rank):
     stream = torch.cuda.current_stream()
     rows = []
     sizes = {"omp": range(11, min(16, args.paper_max_log2n) + 1),
-             "sp": range(11, args.paper_max_log2n + 1), "ompr": range(11, args.paper_max_log2n + 1)}
-    for algo in ("omp", "sp", "ompr"):
-        for e in sizes[algo]:
+             "sp": range(11, args.paper_max_log2n + 1), "ompr": range(11, args.paper_max_log2n + 1),
+             "ompr(l=K/4)": range(11, args.paper_max_log2n + 1)}
+    for variant in ("omp", "sp", "ompr", "ompr(l=K/4)"):
+        algo = "ompr" if variant.startswith("ompr") else variant
+        for e in sizes[variant]:
             N = 1 << e
             M, K, s, noise = synth.paper_workload(N, 0x1509 + e)
             op = binding.Operator(N, M, 0x1509 + e)
             op.set_cg_tol_mode("absolute")
+            if variant != algo:
+                op.set_ompr_replacements(max(1, K // 4))
             sd = torch.from_numpy(s.astype(np.float32)).to(devc)
             y = (op.apply(sd) + torch.from_numpy(noise.astype(np.float32)).to(devc)).contiguous()
             s_out = torch.empty(N, device=devc)
@@ -559,7 +564,7 @@ def run_paper_sweep(args, rank, local_rank):
                 err = float(torch.linalg.norm(s_out - sd))
                 snr = 20.0 * np.log10(float(torch.linalg.norm(sd)) / max(err, 1e-30))
                 paper = PAPER_SECONDS[algo].get(e)
-                rows.append({"algo": algo, "log2N": e, "precision": name, "seconds": e0.elapsed_time(e1) / 1e3,
+                rows.append({"algo": variant, "log2N": e, "precision": name, "seconds": e0.elapsed_time(e1) / 1e3,
                              "snr_db": snr, "outer_iters": st["outer_iters"], "cg_iters": st["cg_iters_total"],
                              "status": st["status"],
                              "paper_seconds": None if paper is None else (paper[2] if name == "xi=1e-5" else paper[0])})

@@ -124,6 +124,13 @@ int32_t cs_op_cluster_size(cs_op_t op);   /* current P (0 for a NULL op) */
 cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, int32_t cg_maxit,
                              float* ms_out);
 
+/* OMPR replacements per round l for this op's later CS_OMPR recoveries (default 1: one swap
+ * z_j <-> z_i per round, |z_j| > |z_i|).  l > 1 is OMPR(l) (Jain, Tewari & Dhillon 2011, the
+ * generalisation of the OMPR the paper cites): J = the l largest |z| outside S, S' = the K
+ * largest |z| over S u J (ties to the lowest index), stop when S' = S; the swap cap of
+ * cs_recover counts rounds.  l is clamped to N - K. */
+cs_status cs_op_set_ompr_replacements(cs_op_t op, int32_t l);
+
 enum { CS_CG_TOL_RELATIVE = 0, CS_CG_TOL_ABSOLUTE = 1 };
 /* Stopping rule of every CG solve of this op's later recover / LS calls (see the conventions
  * above): CS_CG_TOL_RELATIVE (default) or CS_CG_TOL_ABSOLUTE (Algorithm 1's ||r_j|| <= xi). */

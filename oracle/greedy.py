@@ -14,6 +14,9 @@ relative -- the value the paper's CG approximates (Theorems 1-2).
       (step eta = 1, one replacement per iteration): S <- topK|A^T y|; s <- LS(S); then for at
       most T_max rounds: z = s + A^T r, j = argmax_{not in S}|z_j|, i = argmin_{in S}|z_i|;
       stop if |z_j| <= |z_i|; else S <- S - {i} + {j}, s <- LS(S), r <- y - A s.
+      OMPR(l), l > 1 replacements per round (the generalisation in the same paper): J = the l
+      largest |z_j| outside S, S' = the K largest |z| over S u J; stop if S' = S, else
+      S <- S', s <- LS(S), r <- y - A s.
 
 Ties are broken towards the lowest index everywhere.  Every selection records its margin
 mu = (a_(1) - a_(2)) / a_(1) (argmax, argmin) or (a_(K) - a_(K+1)) / a_(K) (top-K); mu <= 1e-3
@@ -133,8 +136,10 @@ def sp(op, y, K, ls_method="auto", L_max=50):
     return _finish(op, y, S, sS, it, trace)
 
 
-def ompr(op, y, K, ls_method="auto", T_max=100):
-    """OMP with Replacement (eta = 1, one swap per iteration) as stated in the module docstring."""
+def ompr(op, y, K, ls_method="auto", T_max=100, l=1):
+    """OMP with Replacement (eta = 1) as stated in the module docstring: one swap per iteration
+    for l = 1; for l > 1 the OMPR(l) step of Jain, Tewari & Dhillon (2011): J = the l largest
+    |z| outside S, S' = the K largest |z| over S u J, stop when S' = S."""
     y = np.asarray(y, dtype=np.float64)
     trace = []
     S, mu = topk_lowest(np.abs(op.apply_t(y)), np.ones(op.N, dtype=bool), K)
@@ -142,6 +147,26 @@ def ompr(op, y, K, ls_method="auto", T_max=100):
     sS = _ls.ls(op, S, y, ls_method)
     r = y - op.apply_support(S, sS)
     it = 0
+    if l > 1:
+        while it < T_max:
+            z = op.apply_t(r)
+            z[S] += sS
+            a = np.abs(z)
+            inside = np.zeros(op.N, dtype=bool)
+            inside[S] = True
+            J, mu_J = topk_lowest(a, ~inside, min(l, op.N - K))
+            union = inside.copy()
+            union[J] = True
+            S_new, mu_K = topk_lowest(a, union, K)
+            trace.append(("topl", mu_J))
+            trace.append(("topk", mu_K))
+            if np.array_equal(S_new, S):
+                break
+            it += 1
+            S = S_new
+            sS = _ls.ls(op, S, y, ls_method)
+            r = y - op.apply_support(S, sS)
+        return _finish(op, y, S, sS, it, trace)
     while it < T_max:
         z = op.apply_t(r)
         z[S] += sS

@@ -42,6 +42,7 @@ SIGNATURES = {
     "cs_op_concurrency": (_I32, [_P]),
     "cs_op_set_batched_impl": (_I32, [_P, _I32]),
     "cs_op_set_cg_tol_mode": (_I32, [_P, _I32]),
+    "cs_op_set_ompr_replacements": (_I32, [_P, _I32]),
     "cs_op_set_cluster_size": (_I32, [_P, _I32]),
     "cs_op_cluster_size": (_I32, [_P]),
     "cs_op_tune_recover": (_I32, [_P, _I32, _I32, _F32, _I32, _P]),
@@ -162,6 +163,10 @@ class Operator:
     def concurrency(self):
         """Signals of this size the GPU runs at once (resident clusters)."""
         return int(lib().cs_op_concurrency(self._h))
+
+    def set_ompr_replacements(self, l):
+        """Replacements per OMPR round (1: single swap; l > 1: OMPR(l))."""
+        _check(lib().cs_op_set_ompr_replacements(self._h, int(l)))
 
     def set_cg_tol_mode(self, mode):
         """CG stopping rule of later recover / LS calls: 'relative' (to ||b||) or 'absolute'."""

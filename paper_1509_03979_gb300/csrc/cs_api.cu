@@ -92,6 +92,7 @@ struct cs_op {
   int32_t* d_prank = nullptr;   // [N/4 + 1][4] Omega ranks of the streamed row pass's pair outputs
   int batched_impl = CS_BATCHED_AUTO;
   int cg_abs = 0;               // CG stopping rule: 0 relative, 1 absolute (cs_op_set_cg_tol_mode)
+  int ompr_l = 1;               // OMPR replacements per round (cs_op_set_ompr_replacements)
   int tuned_nc[2] = {0, 0};     // per mode (A, A^T): 0 untuned, -1 cluster engine, else CTAs per vector
 };
 
@@ -122,6 +123,7 @@ Task base_task(const cs_op* op, int mode) {
   t.cg_tol = 1e-6f;
   t.cg_maxit = 100;
   t.cg_abs = op->cg_abs;
+  t.ompr_l = op->ompr_l;
   t.outer_max = 0;
   t.stats = op->d_stats;
   t.grid_scratch = op->d_scratch;
@@ -523,6 +525,13 @@ cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, 
   cudaFree(so);
   cudaFree(supp);
   return st != CS_OK ? st : st2;
+}
+
+cs_status cs_op_set_ompr_replacements(cs_op_t op, int32_t l) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  if (l < 1) return fail(CS_ERR_INVALID_ARG, "OMPR replacements per round must be >= 1");
+  op->ompr_l = l;
+  return CS_OK;
 }
 
 cs_status cs_op_set_cg_tol_mode(cs_op_t op, int32_t mode) {

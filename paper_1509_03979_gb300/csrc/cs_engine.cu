@@ -1793,6 +1793,48 @@ __device__ __noinline__ bool ompr_swap() {
   return true;
 }
 
+// OMPR(l) replacement step, l > 1 (Jain, Tewari & Dhillon 2011): z = s + A^T r, J = the l
+// largest |z| outside S (= |A^T r| there), S' = the K largest |z| over S u J, with the
+// lowest-index tie rule of every selection.  If S' != S it becomes the support (mask 0), the
+// warm start keeps s on S' and starts the new entries at 0, and the function returns true.
+__device__ __noinline__ bool ompr_replace(int l, int K) {
+  uint32_t* mA = shp(C.sm.mask[0]);
+  uint32_t* mW = shp(C.sm.mask[1]);
+  for (int w = threadIdx.x; w < C.nwords; w += NT) mW[w] = mA[w];
+  __syncthreads();
+  topk_corr(l, mA, mW);                              // S u J
+  const int nW = build_list(mW);
+  {
+    const SigView A = sigview();
+    const uint32_t* signw = shp(C.sm.signw);
+    const int* list = C.list;
+    const float* xa = C.xd[0];
+    float* z = C.xd[1];
+    for (int i = threadIdx.x; i < nW; i += NT) {
+      const int sg = list[i];
+      z[sg] = (mask_bit(mA, sg) ? xa[sg] : 0.f) + corr_at(A, signw, sg);
+    }
+  }
+  __syncthreads();
+  sp_prune(1, nW, K, mW);                            // S' = topK |z| over S u J
+  if (mask_diff(1, 0) == 0.f) return false;
+  {
+    float* xa = C.xd[0];
+    for (int w = threadIdx.x; w < C.nwords; w += NT) {
+      uint32_t fresh = mW[w] & ~mA[w];
+      while (fresh) {
+        const int b = __ffs(fresh) - 1;
+        fresh &= fresh - 1;
+        xa[32 * w + b] = 0.f;
+      }
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < C.nwords; w += NT) mA[w] = mW[w];
+  }
+  __syncthreads();
+  return true;
+}
+
 __device__ __noinline__ void run_ompr(const Task& t) {
   init_correlation(t.in);
   zero_mask(shp(C.sm.mask[0]));
@@ -1801,14 +1843,17 @@ __device__ __noinline__ void run_ompr(const Task& t) {
   cg_solve(0, nloc, false, R0_FROM_CY, t.cg_tol, t.cg_maxit);
   float rn2 = resid_corr(0, nloc, t.in);
   int swaps = 0;
+  const int l = t.ompr_l < t.op.N - t.K ? t.ompr_l : t.op.N - t.K;
   while (swaps < t.outer_max) {
-    if (!ompr_swap()) break;
+    if (!(l > 1 ? ompr_replace(l, t.K) : ompr_swap())) break;
     ++swaps;
     nloc = build_list(shp(C.sm.mask[0]));
     resid_corr(0, nloc, t.in);   // r0 for x0 = s without i, 0 at j
     cg_solve(0, nloc, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
     rn2 = resid_corr(0, nloc, t.in);
   }
+  // a rejected OMPR(l) step leaves the working list of S u J behind: rebuild the list of S
+  if (l > 1) nloc = build_list(shp(C.sm.mask[0]));
   write_recovery(t, 0, nloc, rn2, swaps);
 }
 

@@ -71,6 +71,7 @@ struct Task {
   int cg_maxit;              // 0: at most |S| steps (Theorem 5)
   int cg_abs;                // 1: cg_tol bounds ||r_j|| absolutely, 0: relative to ||b||
   int outer_max;             // SP rounds / OMPR swaps cap
+  int ompr_l;                // OMPR replacements per round (1: one swap)
   const float* in;
   const int32_t* supp_in;    // [k_in] (LS modes)
   float* out;

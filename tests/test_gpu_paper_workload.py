@@ -73,3 +73,28 @@ def test_cg_tol_mode_rejects_unknown(B):
         op.set_cg_tol_mode("sloppy")
     from paper_1509_03979_gb300 import binding
     assert binding.lib().cs_op_set_cg_tol_mode(op._h, 7) != 0
+
+
+@pytest.mark.parametrize("N,M,K,l", [(4096, 1024, 64, 16), (1 << 12, 1 << 10, 1 << 8, 64), (1 << 15, 4000, 300, 300)])
+def test_ompr_l_matches_oracle(B, N, M, K, l):
+    """OMPR(l): same supports and rounds as the FP64 oracle's OMPR(l), s_hat within 1e-4."""
+    seed = 0x0A11 + N + l
+    p = synth.Problem(N=N, M=M, K=K, algo="ompr", op_seed=seed, signal_seed=seed + 1, noise_seed=seed + 2,
+                      noise_rel=1e-3)
+    ref = oracle.Operator(N, M, seed)
+    y = p.add_noise(ref.apply(p.signal())).astype(np.float32)
+    op = B.Operator(N, M, seed)
+    op.set_ompr_replacements(l)
+    s_hat, supp = op.recover(to_dev(y), K, "ompr", 1e-6, 200)
+    st = op.stats()
+    want = greedy.ompr(ref, y.astype(np.float64), K, l=l)
+    if want["near_ties"] == 0:
+        assert np.array_equal(np.sort(supp.cpu().numpy()), want["S"])
+        assert st["outer_iters"] == want["iters"]
+    assert rel(s_hat.cpu().numpy(), want["s"]) <= SHAT_TOL
+
+
+def test_ompr_replacements_rejects_zero(B):
+    op = B.Operator(1024, 256, 1)
+    with pytest.raises(RuntimeError):
+        op.set_ompr_replacements(0)

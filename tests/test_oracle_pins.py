@@ -281,3 +281,41 @@ def test_adjoint_cg_route_matches_pinv():
     dense = np.linalg.pinv(op.columns(S)).T @ cot               # (A_S^+)^T g
     assert np.allclose(adjoint.ls_backward(op, S, cot), dense, atol=1e-10)
     assert np.allclose(adjoint.ls_backward_cg(op, S, cot), dense, atol=1e-9)
+
+
+# ------------------------------------------------------------------ OMPR(l), l > 1
+def test_ompr_l_recovers_noiseless_and_ends_at_a_fixed_point():
+    """OMPR(l) recovers a noiseless K-sparse signal at M >> K log(N/K), and its final support is
+    a fixed point of the OMPR(l) step (recomputing z there selects the same S)."""
+    N, M, K = 512, 160, 12
+    op = oracle.Operator(N, M, 21)
+    s = synth.sparse_gaussian(N, K, 22)
+    y = op.apply(s)
+    out = greedy.ompr(op, y, K, l=4)
+    assert np.array_equal(out["S"], np.flatnonzero(s))
+    assert np.linalg.norm(out["s"] - s) <= 1e-9 * np.linalg.norm(s)
+    S = out["S"]
+    z = op.apply_t(y - op.apply(out["s"]))
+    z[S] += out["s"][S]
+    a = np.abs(z)
+    inside = np.zeros(N, dtype=bool)
+    inside[S] = True
+    J, _ = greedy.topk_lowest(a, ~inside, 4)
+    union = inside.copy()
+    union[J] = True
+    S2, _ = greedy.topk_lowest(a, union, K)
+    assert np.array_equal(S2, S)
+
+
+def test_ompr_l_fixes_several_wrong_indices_per_round():
+    """Starting from topK|A^T y| with several wrong indices, OMPR(l) with l = K needs fewer
+    rounds than single-swap OMPR on the same input, and both end at the true support."""
+    N, M, K = 1024, 256, 40
+    op = oracle.Operator(N, M, 31)
+    s = synth.sparse_gaussian(N, K, 32)
+    y = op.apply(s)
+    one = greedy.ompr(op, y, K, T_max=400)
+    many = greedy.ompr(op, y, K, T_max=400, l=K)
+    truth = np.flatnonzero(s)
+    assert np.array_equal(one["S"], truth) and np.array_equal(many["S"], truth)
+    assert many["iters"] < one["iters"]
