@@ -229,8 +229,9 @@ cs_status cs_ls_backward_batched(cs_op_t op, int32_t B, const int32_t* support, 
 cs_status cs_get_stats(cs_op_t op, cs_stats* out);
 
 /* Wait for the op's stream and report how its last launch ended: CS_ERR_CUDA if the stream
- * holds a CUDA error, CS_ERR_TIMEOUT if the op runs on the streamed path (N > 2^18) and a
- * grid-wide wait of its last launch gave up (its outputs are then undefined), else CS_OK.
+ * holds a CUDA error, CS_ERR_TIMEOUT if a bounded device wait gave up (a grid-wide barrier of
+ * the streamed path, N > 2^18, or a bulk-copy completion of the last streamed batched A / A^T;
+ * the outputs are then undefined), else CS_OK.
  * Apply and LS calls have no cs_stats; this is how their callers see a timeout. */
 cs_status cs_op_sync(cs_op_t op);
 

@@ -90,6 +90,7 @@ struct cs_op {
   void* d_grid = nullptr;       // streamed geometry: rows, signal rows, barrier and reduction state
   uint32_t* d_dbits = nullptr;  // [N/32] sign bits of d, for the streamed batched operator
   int32_t* d_prank = nullptr;   // [N/4 + 1][4] Omega ranks of the streamed row pass's pair outputs
+  int* d_stream_err = nullptr;  // status word of the last streamed batched launch
   int batched_impl = CS_BATCHED_AUTO;
   int cg_abs = 0;               // CG stopping rule: 0 relative, 1 absolute (cs_op_set_cg_tol_mode)
   int ompr_l = 1;               // OMPR replacements per round (cs_op_set_ompr_replacements)
@@ -110,6 +111,7 @@ void free_op(cs_op* op) {
   cudaFree(op->d_grid);
   cudaFree(op->d_dbits);
   cudaFree(op->d_prank);
+  cudaFree(op->d_stream_err);
   delete op;
 }
 
@@ -293,6 +295,8 @@ cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) {
       free_op(op);
       return nullptr;
     }
+    CSG_TRY(cudaMalloc(&op->d_stream_err, sizeof(int)));
+    CSG_TRY(cudaMemset(op->d_stream_err, 0, sizeof(int)));
     CSG_TRY(cudaMalloc(&op->d_prank, sizeof(int32_t) * prank.size()));
     CSG_TRY(cudaMemcpy(op->d_prank, prank.data(), sizeof(int32_t) * prank.size(), cudaMemcpyHostToDevice));
   }
@@ -389,7 +393,9 @@ static cs_status stream_apply(cs_op_t op, int mode, int32_t B, const float* in, 
   a.B = B;
   a.in = in;
   a.out = out;
+  a.err = op->d_stream_err;
   cudaError_t e;
+  if ((e = cudaMemsetAsync(op->d_stream_err, 0, sizeof(int), op->stream)) != cudaSuccess) return cuda_fail(e, "memset");
   const size_t bytes = sizeof(float) * stream_row_floats() * (size_t)op->dev.P * (size_t)clusters;
   if ((e = cudaMallocAsync(&a.T, bytes, op->stream)) != cudaSuccess) return cuda_fail(e, "alloc stream rows");
   e = launch_stream(a, nc, clusters, op->stream);
@@ -821,8 +827,13 @@ cs_status cs_op_sync(cs_op_t op) {
   if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
   cudaError_t e = cudaStreamSynchronize(op->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sync");
-  if (!op->dev.grid) return CS_OK;
   int err = 0;
+  if (op->d_stream_err) {
+    if ((e = cudaMemcpy(&err, op->d_stream_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "status copy");
+    if (err != 0) return fail(CS_ERR_TIMEOUT, "a bulk-copy wait of the last streamed batched launch gave up");
+  }
+  if (!op->dev.grid) return CS_OK;
   e = cudaMemcpy(&err, op->dev.gerr, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "status copy");
   if (err != 0) return fail(CS_ERR_TIMEOUT, "a grid-wide wait of the last streamed launch gave up");

@@ -116,7 +116,7 @@ __device__ __forceinline__ T* shp(T* p) {
 // Padded index into the local FFT buffer (one spare element every 16 keeps the strided
 // Stockham stores of the early passes free of shared-memory bank conflicts).
 __device__ __forceinline__ int aidx(int q) { return q + (q >> 4); }
-__host__ __device__ inline int apad(int F) { return F + F / 16; }
+__host__ __device__ constexpr int apad(int F) { return F + F / 16; }
 
 // Two-level twiddle table: omega_{4N}^j = exp(-2 pi i j / 4N) = lo[j & m] * hi[j >> lo_bits];
 // lo is stored with the same one-in-16 padding as the FFT buffer, which keeps the strided
@@ -2167,6 +2167,36 @@ __device__ __forceinline__ uint32_t dbits4(const uint32_t* dbits, int m) {
 }
 
 // Column pass of A x: x (one vector) -> rows T[k2][n1].
+// Bulk copies (TMA) of the intermediate rows from global memory into the row buffers in shared
+// memory.  A load completes on an mbarrier with a transaction count; the wait is bounded: one
+// that runs out sets the status word and the pass continues, so the launch always ends (the
+// caller reports the status).
+constexpr long STREAM_TMA_POLLS = 1L << 20;
+constexpr size_t STREAM_MBAR_OFF = sizeof(float2) * (3 * (size_t)apad(STREAM_F) + apad(1024) + 1024);
+constexpr uint32_t STREAM_ROW_BYTES = sizeof(float2) * apad(STREAM_F);   // one padded row, 69 632 B
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  for (long i = 0; i < STREAM_TMA_POLLS; ++i) {
+    uint32_t done;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 template <int PT>
 __device__ __forceinline__ void stream_cols_fwd(const float4* x4, const uint32_t* dbits, float2* T, const Tw& tw,
                                                 int rot, int c, int nc) {
@@ -2227,6 +2257,7 @@ __device__ __forceinline__ void stream_cols_inv(const float2* T, const uint32_t*
     }
   }
 }
+
 
 __device__ __forceinline__ void copy_row(float4* dst, const float4* src) {
   for (int i = threadIdx.x; i < apad(STREAM_F) / 2; i += NT) dst[i] = src[i];
@@ -2334,7 +2365,7 @@ __device__ __forceinline__ void stream_pairs(const Geo& g, int ra, float2* R0, f
 __host__ __device__ inline int stream_pair_base(int ra) { return ra == 0 ? 0 : STREAM_F / 2 + 1 + (ra - 1) * STREAM_F; }
 
 // One unit of the row pass (rows ra and (P - ra) mod P), forward or inverse.
-__device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, int ra, int rot) {
+__device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, int ra, int rot, uint32_t* phase) {
   constexpr int F = STREAM_F;
   float2* R0 = reinterpret_cast<float2*>(smem_raw);
   float2* R1 = R0 + apad(F);
@@ -2345,10 +2376,18 @@ __device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, 
   g.N = op.N; g.L = op.N >> 1; g.P = op.P; g.F = F; g.c = 0; g.h = 0; g.lh = 0; g.S2 = 0; g.four_n = 4 * op.N;
   const int rs = apad(F);
   const int rb = (op.P - ra) & (op.P - 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + STREAM_MBAR_OFF);
   if (a.mode == MODE_APPLY) {
-    copy_row(reinterpret_cast<float4*>(R0), reinterpret_cast<const float4*>(T + ra * rs));
-    if (rb != ra) copy_row(reinterpret_cast<float4*>(R1), reinterpret_cast<const float4*>(T + rb * rs));
-    __syncthreads();
+    // rows ra (and rb) by bulk copy; R0 / R1 were last accessed by generic loads and stores
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      mbar_expect(mbar, (rb != ra ? 2u : 1u) * STREAM_ROW_BYTES);
+      bulk_g2s(R0, T + ra * rs, STREAM_ROW_BYTES, mbar);
+      if (rb != ra) bulk_g2s(R1, T + rb * rs, STREAM_ROW_BYTES, mbar);
+    }
+    if (!mbar_wait(mbar, *phase & 1u)) atomicExch(a.err, CS_ERR_TIMEOUT);
+    *phase ^= 1u;
     local_fft<-1>(R0, TB, F, tw, g.four_n);
     if (rb != ra) local_fft<-1>(R1, TB, F, tw, g.four_n);
     stream_pairs(g, ra, R0, R1, tw, a.prank + stream_pair_base(ra), false, nullptr, a.out + (size_t)b * op.M, rot);
@@ -2356,6 +2395,8 @@ __device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, 
     stream_pairs(g, ra, R0, R1, tw, a.prank + stream_pair_base(ra), true, a.in + (size_t)b * op.M, nullptr, rot);
     local_fft<1>(R0, TB, F, tw, g.four_n);
     if (rb != ra) local_fft<1>(R1, TB, F, tw, g.four_n);
+    // rows back with plain coalesced stores (a bulk store measured no faster here: R0 / R1 are
+    // rewritten by the next unit right away, so its source read must be waited for at once)
     copy_row(reinterpret_cast<float4*>(T + ra * rs), reinterpret_cast<const float4*>(R0));
     if (rb != ra) copy_row(reinterpret_cast<float4*>(T + rb * rs), reinterpret_cast<const float4*>(R1));
     __syncthreads();   // R0 / R1 are rewritten by the next unit
@@ -2364,14 +2405,15 @@ __device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, 
 
 // Row pass share of CTA c of nc: units u = c, c + nc, ... of the P/2 units {rows 0 and P/2},
 // {1, P-1}, ..., {P/2-1, P/2+1} (two rows each).
-__device__ __forceinline__ void stream_rows(const StreamArgs& a, int b, float2* T, int rot, int c, int nc) {
+__device__ __forceinline__ void stream_rows(const StreamArgs& a, int b, float2* T, int rot, int c, int nc,
+                                            uint32_t* phase) {
   const int P = a.op.P;
   for (int u = c; u < P / 2; u += nc) {
     if (u == 0) {
-      stream_unit(a, b, T, 0, rot);
-      stream_unit(a, b, T, P / 2, rot);
+      stream_unit(a, b, T, 0, rot, phase);
+      stream_unit(a, b, T, P / 2, rot, phase);
     } else {
-      stream_unit(a, b, T, u, rot);
+      stream_unit(a, b, T, u, rot, phase);
     }
   }
 }
@@ -2415,7 +2457,13 @@ __global__ void __launch_bounds__(NT, 1) stream_kernel(const StreamArgs a) {
     for (int i = threadIdx.x; i < nlo; i += NT) twlo[aidx(i)] = op.tw[i];
     for (int i = threadIdx.x; i < nhi; i += NT) twhi[i] = op.tw[nlo + i];
   }
+  if (threadIdx.x == 0) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + STREAM_MBAR_OFF);
+    mbar_init(&mbar[0]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
+  uint32_t phase = 0;   // parity of the row loads' mbarrier
   float2* T = a.T + (size_t)cid * op.P * apad(F);
   // clusters walk the shared tables (sign bits, pair ranks) from different warp-aligned
   // offsets, so that concurrent clusters do not all read the same few L2 lines at once
@@ -2423,10 +2471,11 @@ __global__ void __launch_bounds__(NT, 1) stream_kernel(const StreamArgs a) {
   for (int b = cid; b < a.B; b += ncl) {
     if (a.mode == MODE_APPLY) {
       stream_cols_any(a, b, T, rot, c, nc);
+      asm volatile("fence.proxy.async.global;" ::: "memory");   // the rows are read by bulk copies
       cl.sync();   // every row of T is complete
-      stream_rows(a, b, T, rot, c, nc);
+      stream_rows(a, b, T, rot, c, nc, &phase);
     } else {
-      stream_rows(a, b, T, rot, c, nc);
+      stream_rows(a, b, T, rot, c, nc, &phase);
       cl.sync();
       stream_cols_any(a, b, T, rot, c, nc);
     }
@@ -2437,8 +2486,9 @@ __global__ void __launch_bounds__(NT, 1) stream_kernel(const StreamArgs a) {
 size_t stream_row_floats() { return 2 * (size_t)apad(STREAM_F); }
 
 static size_t stream_smem() {
-  // rows R0, R1, the FFT ping-pong buffer, and twiddle levels of up to 1024 entries each
-  return sizeof(float2) * (3 * (size_t)apad(STREAM_F) + apad(1024) + 1024);
+  // rows R0, R1, the FFT ping-pong buffer, twiddle levels of up to 1024 entries each, and the
+  // two mbarriers of the column pass's staging buffers (which overlay R0 and R1)
+  return STREAM_MBAR_OFF + 16;
 }
 
 static cudaLaunchConfig_t stream_config(int nc, int clusters, cudaStream_t stream, cudaLaunchAttribute* attr) {

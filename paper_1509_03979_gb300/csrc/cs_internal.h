@@ -114,6 +114,7 @@ struct StreamArgs {
   const float* in;           // [B][N] (A) or [B][M] (A^T), contiguous
   float* out;                // [B][M] (A) or [B][N] (A^T)
   float2* T;                 // per cluster: [P][apad(STREAM_F)] intermediate rows
+  int* err;                  // status word: CS_ERR_TIMEOUT if a bulk-copy wait ran out
 };
 size_t stream_row_floats();    // floats of one padded intermediate row
 int stream_clusters(int nc);   // clusters of nc CTAs resident at once (0: cannot launch)
