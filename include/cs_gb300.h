@@ -78,6 +78,22 @@ typedef struct {
  * Returns NULL on failure (see cs_last_error()).  Owns all its device memory. */
 cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed);
 
+/* The operator with a chosen randomiser R of the SRM (Sec. III-A): CS_RANDOMIZER_SIGNS is
+ * diag(d) as in cs_op_create; CS_RANDOMIZER_PERMUTATION is the paper's uniform random
+ * permutation, A = P_Omega C_N Pi with (Pi x)_n = x_{perm[n]} and no sign flips, perm drawn by a
+ * full Fisher-Yates shuffle: for i = 0 .. N-2, j = i + (mix((seed ^ 0xA0761D6478BD642F) +
+ * (i+1) gamma) mod (N-i)), swap.  Every entry point works with both; the streamed batched
+ * operator is not used for permutation operators (their x gather is not contiguous).
+ * Returns NULL on failure. */
+enum { CS_RANDOMIZER_SIGNS = 0, CS_RANDOMIZER_PERMUTATION = 1 };
+cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer);
+
+/* Host-only draw of the permutation randomiser for (N, seed) into perm_N_host [N] HOST. */
+cs_status cs_operator_perm(int64_t N, uint64_t seed, int32_t* perm_N_host);
+
+/* Copy a permutation operator's perm to perm_N_host [N] HOST (CS_ERR_INVALID_ARG otherwise). */
+cs_status cs_op_export_perm(cs_op_t op, int32_t* perm_N_host);
+
 /* Free the operator and every buffer it owns.  Waits for its stream first. */
 void cs_op_destroy(cs_op_t op);
 
@@ -156,7 +172,8 @@ cs_status cs_op_tune_batched(cs_op_t op, int32_t B, float* ms_out);
 int32_t cs_op_concurrency(cs_op_t op);
 
 /* Copy the operator's random draws to HOST memory for cross-checking: omega_M_host [M]
- * (sorted row indices) and d_N_host [N] (+1/-1).  Either pointer may be NULL. */
+ * (sorted row indices) and d_N_host [N] (+1/-1; all +1 for a permutation operator).  Either
+ * pointer may be NULL. */
 cs_status cs_op_export(cs_op_t op, int32_t* omega_M_host, int8_t* d_N_host);
 
 /* Host-only: the same random draws cs_op_create(N, M, seed) uses, without touching a GPU.

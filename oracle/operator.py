@@ -18,13 +18,23 @@ from . import rng as _rng
 class Operator:
     """A in R^{M x N}; `fast=True` applies C_N via FFT (O-fast), else by the O(N^2) sum."""
 
-    def __init__(self, N, M, seed, fast=True):
+    def __init__(self, N, M, seed, fast=True, randomizer="signs"):
+        """randomizer 'signs': R = diag(d) (A = P_Omega C_N diag(d)); 'perm': R the paper's random
+        permutation, (R x)_n = x[perm[n]], no signs (A = P_Omega C_N Pi)."""
         if N < 2 or (N & (N - 1)):
             raise ValueError("N must be a power of two >= 2")
         self.N, self.M, self.seed = int(N), int(M), int(seed)
         self.omega = _rng.omega(N, M, seed)
-        self.d = _rng.signs(N, seed)
         self.fast = fast
+        if randomizer == "perm":
+            self.d = np.ones(N)
+            self.perm = _rng.perm(N, seed)
+            self.iperm = np.empty(N, dtype=np.int64)
+            self.iperm[self.perm] = np.arange(N)
+        else:
+            self.d = _rng.signs(N, seed)
+            self.perm = None
+            self.iperm = None
 
     # --- transforms -------------------------------------------------------------------
     def _c(self, x):
@@ -35,21 +45,30 @@ class Operator:
 
     # --- A and A^T (Sec. III-D operator list) --------------------------------------------
     def apply(self, x):
-        """A x = (C_N (d * x))[Omega]."""
-        return self._c(self.d * np.asarray(x, dtype=np.float64))[..., self.omega]
+        """A x = (C_N (d * x))[Omega], or (C_N x[perm])[Omega] for the permutation randomiser."""
+        x = np.asarray(x, dtype=np.float64)
+        if self.perm is not None:
+            return self._c(x[..., self.perm])[..., self.omega]
+        return self._c(self.d * x)[..., self.omega]
 
     def apply_t(self, u):
         """A^T u = d * C_N^T (P_Omega^T u)."""
         u = np.asarray(u, dtype=np.float64)
         full = np.zeros(u.shape[:-1] + (self.N,))
         full[..., self.omega] = u
-        return self.d * self._ct(full)
+        w = self._ct(full)
+        if self.perm is not None:
+            out = np.empty_like(w)
+            out[..., self.perm] = w
+            return out
+        return self.d * w
 
     def columns(self, S):
         """Dense A_S (M x |S|) from the closed form A[m, j] = d_j w_{Omega_m} cos(pi (2j+1) Omega_m / (2N))."""
         S = np.asarray(S, dtype=np.int64)
         k = self.omega[:, None].astype(np.float64)
-        j = S[None, :].astype(np.float64)
+        pos = S if self.perm is None else self.iperm[S]   # DCT input index of each column
+        j = pos[None, :].astype(np.float64)
         w = _dct.weights(self.N)[self.omega][:, None]
         return self.d[S][None, :] * w * np.cos(np.pi * (2.0 * j + 1.0) * k / (2.0 * self.N))
 

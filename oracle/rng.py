@@ -78,3 +78,20 @@ def omega(N, M, seed):
         j = i + int(jump[i])
         perm[i], perm[j] = perm[j], perm[i]
     return np.sort(perm[:M])
+
+
+PERM_SALT = 0xA0761D6478BD642F
+
+
+def perm(N, seed):
+    """The permutation randomiser R of the SRM (Sec. III-A: a uniform random permutation): a full
+    Fisher-Yates shuffle of [0, N) with j = i + (u_{i+1} mod (N - i)), u the SplitMix64 stream
+    seeded with seed ^ PERM_SALT; (R x)_n = x[perm[n]]."""
+    u = stream((seed ^ PERM_SALT) & _M64, max(N - 1, 0))
+    p = np.arange(N, dtype=np.int64)
+    span = (N - np.arange(max(N - 1, 0), dtype=np.uint64)).astype(np.uint64)
+    jump = (u % span).astype(np.int64)
+    for i in range(N - 1):
+        j = i + int(jump[i])
+        p[i], p[j] = p[j], p[i]
+    return p

@@ -32,6 +32,9 @@ _P = ctypes.c_void_p
 _I64, _U64, _I32, _F32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_float
 SIGNATURES = {
     "cs_op_create": (_P, [_I64, _I64, _U64]),
+    "cs_op_create_ex": (_P, [_I64, _I64, _U64, _I32]),
+    "cs_operator_perm": (_I32, [_I64, _U64, _P]),
+    "cs_op_export_perm": (_I32, [_P, _P]),
     "cs_op_destroy": (None, [_P]),
     "cs_op_set_stream": (_I32, [_P, _P]),
     "cs_op_apply": (_I32, [_P, _P, _P]),
@@ -105,12 +108,22 @@ def operator_draws(N, M, seed):
 class Operator:
     """A = P_Omega C_N diag(d) on the current CUDA device (Sec. III-A, Eq. 7)."""
 
-    def __init__(self, N, M, seed):
+    RANDOMIZERS = {"signs": 0, "perm": 1}
+
+    def __init__(self, N, M, seed, randomizer="signs"):
+        """randomizer: 'signs' (R = diag(d), the default) or 'perm' (R a random permutation)."""
         self.N, self.M, self.seed = int(N), int(M), int(seed)
-        h = lib().cs_op_create(self.N, self.M, self.seed)
+        self.randomizer = randomizer
+        h = lib().cs_op_create_ex(self.N, self.M, self.seed, self.RANDOMIZERS[randomizer])
         if not h:
             raise RuntimeError(f"cs_op_create failed: {lib().cs_last_error().decode()}")
         self._h = ctypes.c_void_p(h)
+
+    def export_perm(self):
+        import numpy as np
+        p = np.zeros(self.N, dtype=np.int32)
+        _check(lib().cs_op_export_perm(self._h, p.ctypes.data_as(ctypes.c_void_p)))
+        return p
 
     def close(self):
         if getattr(self, "_h", None):

@@ -59,6 +59,23 @@ std::vector<int32_t> draw_omega(int64_t N, int64_t M, uint64_t seed) {
   return om;
 }
 
+// Permutation randomiser R: a full Fisher-Yates shuffle of [0, N) driven by the SplitMix64
+// stream seeded with seed ^ PERM_SALT, j = i + (u_{i+1} mod (N - i)) for i < N - 1; the DCT
+// input n holds x[perm[n]].
+constexpr uint64_t PERM_SALT = 0xA0761D6478BD642Full;
+std::vector<int32_t> draw_perm(int64_t N, uint64_t seed) {
+  std::vector<int32_t> perm((size_t)N);
+  std::iota(perm.begin(), perm.end(), 0);
+  uint64_t st = seed ^ PERM_SALT;
+  for (int64_t i = 0; i + 1 < N; ++i) {
+    st += GAMMA;
+    const uint64_t u = mix64(st);
+    const int64_t j = i + (int64_t)(u % (uint64_t)(N - i));
+    std::swap(perm[(size_t)i], perm[(size_t)j]);
+  }
+  return perm;
+}
+
 // d_n = -1 iff the top bit of mix((seed ^ salt) + n + gamma) is set.
 int8_t draw_sign(uint64_t sign_key, int64_t n) {
   return (mix64(sign_key + (uint64_t)n + GAMMA) >> 63) ? (int8_t)-1 : (int8_t)1;
@@ -90,6 +107,8 @@ struct cs_op {
   void* d_grid = nullptr;       // streamed geometry: rows, signal rows, barrier and reduction state
   uint32_t* d_dbits = nullptr;  // [N/32] sign bits of d, for the streamed batched operator
   int32_t* d_prank = nullptr;   // [N/4 + 1][4] Omega ranks of the streamed row pass's pair outputs
+  int32_t* d_perm = nullptr;    // permutation randomiser: [N] perm then [N] its inverse
+  int randomizer = CS_RANDOMIZER_SIGNS;
   int* d_stream_err = nullptr;  // status word of the last streamed batched launch
   int batched_impl = CS_BATCHED_AUTO;
   int cg_abs = 0;               // CG stopping rule: 0 relative, 1 absolute (cs_op_set_cg_tol_mode)
@@ -111,6 +130,7 @@ void free_op(cs_op* op) {
   cudaFree(op->d_grid);
   cudaFree(op->d_dbits);
   cudaFree(op->d_prank);
+  cudaFree(op->d_perm);
   cudaFree(op->d_stream_err);
   delete op;
 }
@@ -188,12 +208,28 @@ cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_
   return CS_OK;
 }
 
-cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) {
+cs_status cs_operator_perm(int64_t N, uint64_t seed, int32_t* perm_N_host) {
+  const cs_status st = check_nm(N, 1);
+  if (st != CS_OK) return st;
+  if (!perm_N_host) return fail(CS_ERR_INVALID_ARG, "null argument");
+  const std::vector<int32_t> p = draw_perm(N, seed);
+  std::memcpy(perm_N_host, p.data(), sizeof(int32_t) * (size_t)N);
+  return CS_OK;
+}
+
+cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) { return cs_op_create_ex(N, M, seed, CS_RANDOMIZER_SIGNS); }
+
+cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer) {
   if (check_nm(N, M) != CS_OK) return nullptr;
+  if (randomizer != CS_RANDOMIZER_SIGNS && randomizer != CS_RANDOMIZER_PERMUTATION) {
+    fail(CS_ERR_INVALID_ARG, "unknown randomiser");
+    return nullptr;
+  }
   cs_op* op = new cs_op();
   op->N = N;
   op->M = M;
   op->seed = seed;
+  op->randomizer = randomizer;
   op->h_omega = draw_omega(N, M, seed);
   const int64_t W = (N + 31) / 32;
   std::vector<uint32_t> omask((size_t)W, 0u);
@@ -261,7 +297,19 @@ cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) {
   CSG_TRY(cudaMemcpy(op->d_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
   CSG_TRY(cudaMemset(op->d_scratch, 0, scratch));
   CSG_TRY(cudaMemset(op->d_stats, 0, sizeof(cs_stats)));
-  if (!d.grid && N >= STREAM_N_MIN) {
+  if (randomizer == CS_RANDOMIZER_PERMUTATION) {
+    const std::vector<int32_t> perm = draw_perm(N, seed);
+    std::vector<int32_t> both((size_t)(2 * N));
+    for (int64_t n = 0; n < N; ++n) {
+      both[(size_t)n] = perm[(size_t)n];
+      both[(size_t)(N + perm[(size_t)n])] = (int32_t)n;
+    }
+    CSG_TRY(cudaMalloc(&op->d_perm, sizeof(int32_t) * both.size()));
+    CSG_TRY(cudaMemcpy(op->d_perm, both.data(), sizeof(int32_t) * both.size(), cudaMemcpyHostToDevice));
+    d.perm = op->d_perm;
+    d.iperm = op->d_perm + N;
+  }
+  if (!d.grid && N >= STREAM_N_MIN && randomizer == CS_RANDOMIZER_SIGNS) {
     std::vector<uint32_t> dbits((size_t)W, 0u);
     for (int64_t n = 0; n < N; ++n)
       if (draw_sign(d.sign_key, n) < 0) dbits[(size_t)(n >> 5)] |= 1u << (n & 31);
@@ -620,7 +668,16 @@ cs_status cs_op_export(cs_op_t op, int32_t* omega_M_host, int8_t* d_N_host) {
   if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
   if (omega_M_host) std::memcpy(omega_M_host, op->h_omega.data(), sizeof(int32_t) * (size_t)op->M);
   if (d_N_host)
-    for (int64_t n = 0; n < op->N; ++n) d_N_host[n] = draw_sign(op->dev.sign_key, n);
+    for (int64_t n = 0; n < op->N; ++n)
+      d_N_host[n] = op->randomizer == CS_RANDOMIZER_SIGNS ? draw_sign(op->dev.sign_key, n) : (int8_t)1;
+  return CS_OK;
+}
+
+cs_status cs_op_export_perm(cs_op_t op, int32_t* perm_N_host) {
+  if (!op || !perm_N_host) return fail(CS_ERR_INVALID_ARG, "null argument");
+  if (op->randomizer != CS_RANDOMIZER_PERMUTATION) return fail(CS_ERR_INVALID_ARG, "the operator has no permutation");
+  cudaError_t e = cudaMemcpy(perm_N_host, op->d_perm, sizeof(int32_t) * (size_t)op->N, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "perm copy");
   return CS_OK;
 }
 

@@ -543,6 +543,18 @@ __device__ __forceinline__ void slot_of_n(const Geo& g, int n, int& owner, int& 
 __device__ __forceinline__ float sgn_bits(const uint32_t* signw, int sigma) {
   return (signw[sigma >> 5] >> (sigma & 31)) & 1u ? -1.0f : 1.0f;
 }
+// Index of x (the signal) held by slot sigma: the DCT input index itself under the sign
+// randomiser, perm[n] under the permutation randomiser R (Sec. III-A), whose DCT input n is
+// x[perm[n]].  slot_of_sig inverts it.
+__device__ __forceinline__ int sig_of_slot(const Geo& g, int sigma) {
+  const int n = n_of_slot(g, sigma);
+  const int32_t* perm = C.op.perm;
+  return perm ? __ldg(perm + n) : n;
+}
+__device__ __forceinline__ void slot_of_sig(const Geo& g, int j, int& owner, int& sigma) {
+  const int32_t* iperm = C.op.iperm;
+  slot_of_n(g, iperm ? __ldg(iperm + j) : j, owner, sigma);
+}
 __device__ __forceinline__ bool mask_bit(const uint32_t* m, int sigma) { return (m[sigma >> 5] >> (sigma & 31)) & 1u; }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -848,7 +860,7 @@ __device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, 
 #pragma unroll
       for (int e = 0; e < U; ++e) {
         const int sg = s0 + e * NT;
-        v[e] = sg < 2 * F ? __ldg(gin + n_of_slot(g, sg)) : 0.f;
+        v[e] = sg < 2 * F ? __ldg(gin + sig_of_slot(g, sg)) : 0.f;
       }
 #pragma unroll
       for (int e = 0; e < U; ++e) {
@@ -1171,8 +1183,8 @@ __device__ __noinline__ void grid_row_forward(int lr, int src, int nloc, const f
   if (src == SRC_GLOBAL_N) {
     for (int n1 = threadIdx.x; n1 < S1; n1 += NT) {
       const int q = n1 * R + lr;
-      X[aidx(n1)] = make_float2(gin[n_of_slot(g, 2 * q)] * sgn_bits(signw, 2 * q),
-                                gin[n_of_slot(g, 2 * q + 1)] * sgn_bits(signw, 2 * q + 1));
+      X[aidx(n1)] = make_float2(gin[sig_of_slot(g, 2 * q)] * sgn_bits(signw, 2 * q),
+                                gin[sig_of_slot(g, 2 * q + 1)] * sgn_bits(signw, 2 * q + 1));
     }
   } else {
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1543,7 +1555,7 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
     const float* xd = C.xd[wi];
     for (int i = threadIdx.x; i < nloc; i += NT) {
       const int sg = list[i];
-      const int n = n_of_slot(g, sg);
+      const int n = sig_of_slot(g, sg);
       t.out[n] = xd[sg];
       atomicOr(&C.bits[n >> 5], 1u << (n & 31));
     }
@@ -1639,7 +1651,7 @@ __device__ __noinline__ void topk_corr(int K, const uint32_t* excl, uint32_t* ds
         if (excl && mask_bit(excl, sg)) return 0u;
         return abs_key(A.at(sg));
       },
-      [&](int sg) { return n_of_slot(g, sg); },
+      [&](int sg) { return sig_of_slot(g, sg); },
       [&](int sg) { atomicOr(&dst[sg >> 5], 1u << (sg & 31)); });
 }
 
@@ -1653,14 +1665,14 @@ __device__ __noinline__ int omp_select(uint32_t* mA) {
   for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
     if (mask_bit(mA, sg)) continue;
     const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) |
-                                  (0xffffffffu - (uint32_t)n_of_slot(g, sg));
+                                  (0xffffffffu - (uint32_t)sig_of_slot(g, sg));
     key = kk > key ? kk : key;
   }
   cluster_max64(&key, 1);
   if (key == 0ull) return -1;   // no candidate left (uniform: key is cluster-reduced)
   const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
   int owner, sg;
-  slot_of_n(C.g, n, owner, sg);
+  slot_of_sig(C.g, n, owner, sg);
   if (owner == C.g.c && threadIdx.x == 0) {
     mA[sg >> 5] |= 1u << (sg & 31);
     C.xd[0][sg] = 0.f;
@@ -1691,7 +1703,7 @@ __device__ __noinline__ void sp_prune(int wi, int nW, int K, uint32_t* mW) {
   const float* xw = C.xd[wi];
   select_topk(
       nW, K, [&](int i) -> uint32_t { return abs_key(xw[list[i]]); },
-      [&](int i) { return n_of_slot(g, list[i]); },
+      [&](int i) { return sig_of_slot(g, list[i]); },
       [&](int i) { const int sg = list[i]; atomicOr(&mW[sg >> 5], 1u << (sg & 31)); });
 }
 
@@ -1765,7 +1777,7 @@ __device__ __noinline__ bool ompr_swap() {
   unsigned long long key[2] = {0ull, 0ull};
   const float* xd = C.xd[0];
   for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
-    const uint32_t lo = 0xffffffffu - (uint32_t)n_of_slot(g, sg);
+    const uint32_t lo = 0xffffffffu - (uint32_t)sig_of_slot(g, sg);
     if (mask_bit(mA, sg)) {
       const float z = xd[sg] + corr_at(A, signw, sg);
       const unsigned long long kk =
@@ -1783,8 +1795,8 @@ __device__ __noinline__ bool ompr_swap() {
   const int nj = (int)(0xffffffffu - (uint32_t)(key[0] & 0xffffffffu));
   const int ni = (int)(0xffffffffu - (uint32_t)(key[1] & 0xffffffffu));
   int oj, sj, oi, si;
-  slot_of_n(g, nj, oj, sj);
-  slot_of_n(g, ni, oi, si);
+  slot_of_sig(g, nj, oj, sj);
+  slot_of_sig(g, ni, oi, si);
   if (threadIdx.x == 0) {
     if (oi == g.c) { mA[si >> 5] &= ~(1u << (si & 31)); C.xd[0][si] = 0.f; }
     if (oj == g.c) { mA[sj >> 5] |= 1u << (sj & 31); C.xd[0][sj] = 0.f; }
@@ -1865,7 +1877,7 @@ __device__ __noinline__ void mask_from_support(const int32_t* supp, int k, uint3
     const int n = supp[i];
     if (n < 0 || n >= g.N) continue;
     int owner, sg;
-    slot_of_n(g, n, owner, sg);
+    slot_of_sig(g, n, owner, sg);
     if (owner == g.c) atomicOr(&m[sg >> 5], 1u << (sg & 31));
   }
   __syncthreads();
@@ -1882,7 +1894,7 @@ __device__ __noinline__ void run_ls_solve(const Task& t) {
     const int n = t.supp_in[i];
     if (n < 0 || n >= g.N) continue;
     int owner, sg;
-    slot_of_n(g, n, owner, sg);
+    slot_of_sig(g, n, owner, sg);
     if (owner == g.c) t.out[i] = C.xd[0][sg];
   }
   if (g.c == 0 && threadIdx.x == 0 && t.stats) {
@@ -1900,7 +1912,7 @@ __device__ __noinline__ void run_ls_backward(const Task& t) {
     const int n = t.supp_in[i];
     if (n < 0 || n >= g.N) continue;
     int owner, sg;
-    slot_of_n(g, n, owner, sg);
+    slot_of_sig(g, n, owner, sg);
     if (owner == g.c) C.cy[sg] = t.in[i];
   }
   __syncthreads();
@@ -1969,7 +1981,7 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
         const int sg = 32 * w + b;
         if (sg < 2 * op.F) {
           const uint64_t hsh = mix64(op.sign_key + (uint64_t)n_of_slot(gg, sg) + 0x9E3779B97F4A7C15ull);
-          bitsw |= (uint32_t)(hsh >> 63) << b;
+          if (!op.perm) bitsw |= (uint32_t)(hsh >> 63) << b;   // the permutation randomiser has no signs
         }
       }
       signw[w] = bitsw;
@@ -1988,7 +2000,7 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
       const SigView A = sigview();
       const uint32_t* signw = shp(C.sm.signw);
       const Geo gg = C.g;
-      for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[n_of_slot(gg, sg)] = corr_at(A, signw, sg);
+      for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[sig_of_slot(gg, sg)] = corr_at(A, signw, sg);
       break;
     }
     case MODE_RECOVER:

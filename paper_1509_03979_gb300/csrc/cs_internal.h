@@ -49,6 +49,8 @@ struct OpDev {
   const uint32_t* omask;     // [N/32] bitmask of Omega
   const int32_t* orank;      // [N/32] number of Omega members below word w
   const float2* tw;          // [2^lo_bits] then [2^hi_bits]: omega_{4N}^j = lo[j & m] * hi[j >> lo]
+  const int32_t* perm;       // permutation randomiser: DCT input n holds x[perm[n]] (null: signs d)
+  const int32_t* iperm;      // its inverse
   // streamed geometry (grid != 0 only)
   int grid;
   int S1, S2, G, R, W, NB, bpc;  // row length, rows, CTAs, rows per CTA, block width, blocks, blocks per CTA

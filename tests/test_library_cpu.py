@@ -52,3 +52,10 @@ def test_invalid_sizes_rejected_without_gpu(lib, N, M, code):
     st = lib.cs_operator_draws(N, M, 1, om.ctypes.data_as(ctypes.c_void_p), None)
     assert st == code
     assert len(lib.cs_last_error()) > 0
+
+
+@pytest.mark.parametrize("N,seed", [(16, 1), (4096, 0x0C5001), (1 << 16, 77)])
+def test_permutation_draw_matches_oracle(lib, N, seed):
+    p = np.zeros(N, dtype=np.int32)
+    assert lib.cs_operator_perm(N, seed, p.ctypes.data_as(ctypes.c_void_p)) == 0
+    assert np.array_equal(p.astype(np.int64), rng.perm(N, seed))

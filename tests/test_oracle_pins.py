@@ -319,3 +319,33 @@ def test_ompr_l_fixes_several_wrong_indices_per_round():
     truth = np.flatnonzero(s)
     assert np.array_equal(one["S"], truth) and np.array_equal(many["S"], truth)
     assert many["iters"] < one["iters"]
+
+
+# ------------------------------------------------------------ permutation randomiser R
+def test_perm_is_a_permutation_and_the_operator_is_the_permuted_dct():
+    """Sec. III-A's R as a uniform random permutation: A = P_Omega C_N Pi equals the orthonormal
+    DCT matrix (scipy) restricted to Omega, with its columns permuted by perm."""
+    N, M = 256, 70
+    op = oracle.Operator(N, M, 5, randomizer="perm")
+    assert np.array_equal(np.sort(op.perm), np.arange(N))
+    assert not np.array_equal(op.perm, np.arange(N))
+    C = sfft.dct(np.eye(N), axis=0, norm="ortho")
+    want = np.empty((M, N))
+    want[:, op.perm] = C[op.omega, :]          # column perm[n] of A is column n of C
+    assert np.allclose(op.dense(), want, atol=1e-12)
+    g = np.random.default_rng(1)
+    x = g.standard_normal(N)
+    u = g.standard_normal(M)
+    assert np.allclose(op.apply(x), want @ x, atol=1e-12)
+    assert np.allclose(op.apply_t(u), want.T @ u, atol=1e-12)
+    assert np.allclose(op.apply(op.apply_t(u)), u, atol=1e-12)   # A A^T = I_M
+
+
+def test_perm_operator_recovers_noiseless_sparse():
+    N, M, K = 1024, 256, 20
+    op = oracle.Operator(N, M, 9, randomizer="perm")
+    s = synth.sparse_gaussian(N, K, 10)
+    for algo in ("omp", "sp", "ompr"):
+        out = greedy.recover(op, op.apply(s), K, algo)
+        assert np.array_equal(out["S"], np.flatnonzero(s)), algo
+        assert np.linalg.norm(out["s"] - s) <= 1e-9 * np.linalg.norm(s)
