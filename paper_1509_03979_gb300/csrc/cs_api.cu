@@ -716,36 +716,40 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
 // stream-ordered allocator and are released on the same stream.
 static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
   std::map<int, std::vector<Task>> groups;
+  std::vector<Task> grid_tasks;
   for (const Task& t : tasks) {
-    if (t.op.grid) {   // streamed geometry: the whole GPU per signal, one launch each
-      Launch L{};
-      L.tasks = nullptr;
-      L.single = t;
-      L.ntasks = 1;
-      L.F_alloc = t.op.F;
-      L.plan = grid_plan(t.op);
-      L.scratch = t.grid_scratch;
-      L.scratch_per_cluster = 0;
-      L.bits = t.grid_bits;
-      L.bits_per_cluster = 0;
-      cudaError_t e;
-      if ((e = cudaMemsetAsync(t.op.gerr, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "memset");
-      if ((e = launch_grid(L, t.op.G, stream)) != cudaSuccess) return cuda_fail(e, "grid launch");
-      continue;
-    }
-    groups[t.op.P].push_back(t);
+    if (t.op.grid) grid_tasks.push_back(t);
+    else groups[t.op.P].push_back(t);
   }
+  // One persistent launch per cluster size.  With several sizes the launches run concurrently on
+  // forked streams (joined back into `stream`), so a long signal of one size does not hold the
+  // others back; clusters claim tasks dynamically, largest work first.
+  const bool fork = groups.size() > 1;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> evs;
+  cudaError_t e;
+  cudaEvent_t start = nullptr;
+  if (fork) {
+    if ((e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = cudaEventRecord(start, stream)) != cudaSuccess) return cuda_fail(e, "event record");
+  }
+  cs_status st = CS_OK;
   for (auto& kv : groups) {
     const int P = kv.first;
     std::vector<Task>& g = kv.second;
-    // largest work first (a static round-robin over clusters then balances reasonably)
+    cudaStream_t s = stream;
+    if (fork) {
+      if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) { st = cuda_fail(e, "stream"); break; }
+      aux.push_back(s);
+      if ((e = cudaStreamWaitEvent(s, start, 0)) != cudaSuccess) { st = cuda_fail(e, "stream wait"); break; }
+    }
     std::stable_sort(g.begin(), g.end(), [](const Task& a, const Task& b) {
       return (int64_t)a.op.N * std::max(a.K, a.k_in) > (int64_t)b.op.N * std::max(b.K, b.k_in);
     });
     int F_alloc = 0, Nmax = 0;
     for (const Task& t : g) { F_alloc = std::max(F_alloc, t.op.F); Nmax = std::max(Nmax, t.op.N); }
     const int maxc = max_active_clusters(P, F_alloc);
-    if (maxc < 1) return fail(CS_ERR_UNSUPPORTED_N, "cluster configuration cannot be scheduled");
+    if (maxc < 1) { st = fail(CS_ERR_UNSUPPORTED_N, "cluster configuration cannot be scheduled"); break; }
     const int G = std::min<int>((int)g.size(), maxc);
     Launch L{};
     L.ntasks = (int)g.size();
@@ -754,19 +758,53 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     L.scratch_per_cluster = (size_t)P * scratch_floats_per_cta(F_alloc);
     L.bits_per_cluster = (size_t)(Nmax + 31) / 32;
     Task* d_tasks = nullptr;
-    cudaError_t e;
-    if ((e = cudaMallocAsync(&d_tasks, sizeof(Task) * g.size(), stream)) != cudaSuccess) return cuda_fail(e, "alloc tasks");
-    if ((e = cudaMallocAsync(&L.scratch, sizeof(float) * L.scratch_per_cluster * G, stream)) != cudaSuccess)
-      return cuda_fail(e, "alloc scratch");
-    if ((e = cudaMallocAsync(&L.bits, sizeof(uint32_t) * L.bits_per_cluster * G, stream)) != cudaSuccess)
-      return cuda_fail(e, "alloc bits");
-    if ((e = cudaMemcpyAsync(d_tasks, g.data(), sizeof(Task) * g.size(), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-      return cuda_fail(e, "upload tasks");
+    if ((e = cudaMallocAsync(&d_tasks, sizeof(Task) * g.size() + 16, s)) != cudaSuccess) { st = cuda_fail(e, "alloc tasks"); break; }
+    if ((e = cudaMallocAsync(&L.scratch, sizeof(float) * L.scratch_per_cluster * G, s)) != cudaSuccess) {
+      st = cuda_fail(e, "alloc scratch");
+      break;
+    }
+    if ((e = cudaMallocAsync(&L.bits, sizeof(uint32_t) * L.bits_per_cluster * G, s)) != cudaSuccess) {
+      st = cuda_fail(e, "alloc bits");
+      break;
+    }
+    if ((e = cudaMemcpyAsync(d_tasks, g.data(), sizeof(Task) * g.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+      st = cuda_fail(e, "upload tasks");
+      break;
+    }
+    L.claim = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(d_tasks) + sizeof(Task) * g.size());
+    if ((e = cudaMemsetAsync(L.claim, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
     L.tasks = d_tasks;
-    if ((e = launch_engine(L, P, G, stream)) != cudaSuccess) return cuda_fail(e, "engine launch");
-    cudaFreeAsync(d_tasks, stream);
-    cudaFreeAsync(L.scratch, stream);
-    cudaFreeAsync(L.bits, stream);
+    if ((e = launch_engine(L, P, G, s)) != cudaSuccess) { st = cuda_fail(e, "engine launch"); break; }
+    cudaFreeAsync(d_tasks, s);
+    cudaFreeAsync(L.scratch, s);
+    cudaFreeAsync(L.bits, s);
+    if (fork) {
+      cudaEvent_t ev = nullptr;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { st = cuda_fail(e, "event"); break; }
+      evs.push_back(ev);
+      if ((e = cudaEventRecord(ev, s)) != cudaSuccess) { st = cuda_fail(e, "event record"); break; }
+      if ((e = cudaStreamWaitEvent(stream, ev, 0)) != cudaSuccess) { st = cuda_fail(e, "stream wait"); break; }
+    }
+  }
+  // streams and events are released once their work completes
+  for (cudaStream_t s : aux) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  if (start) cudaEventDestroy(start);
+  if (st != CS_OK) return st;
+  // streamed geometry: the whole GPU per signal, one cooperative launch each, after the rest
+  for (const Task& t : grid_tasks) {
+    Launch L{};
+    L.tasks = nullptr;
+    L.single = t;
+    L.ntasks = 1;
+    L.F_alloc = t.op.F;
+    L.plan = grid_plan(t.op);
+    L.scratch = t.grid_scratch;
+    L.scratch_per_cluster = 0;
+    L.bits = t.grid_bits;
+    L.bits_per_cluster = 0;
+    if ((e = cudaMemsetAsync(t.op.gerr, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = launch_grid(L, t.op.G, stream)) != cudaSuccess) return cuda_fail(e, "grid launch");
   }
   return CS_OK;
 }

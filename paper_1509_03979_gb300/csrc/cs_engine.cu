@@ -463,6 +463,7 @@ struct Ctx {
   int cg_total;       // statistics (thread 0 only)
   int cg_hits;
   int ntrans;         // N-point DCT applications (forward or inverse)
+  int next_task;      // cluster rank 0: the task index it claimed for the cluster
 };
 __shared__ Ctx C;
 
@@ -2038,8 +2039,24 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
     C.bits = lp.bits + (size_t)cid * lp.bits_per_cluster;
   }
   __syncthreads();
-  for (int ti = cid; ti < lp.ntasks; ti += ncl) {
-    run_task(lp.tasks ? lp.tasks + ti : &lp.single, P, c, lp.F_alloc);
+  if (!lp.claim) {
+    for (int ti = cid; ti < lp.ntasks; ti += ncl) {
+      run_task(lp.tasks ? lp.tasks + ti : &lp.single, P, c, lp.F_alloc);
+      cl.sync();
+    }
+    return;
+  }
+  // dynamic claiming: rank 0 takes the next task index and every CTA reads it through DSMEM
+  // between two cluster barriers (the task list is sorted by work, largest first).  The second
+  // barrier also keeps rank 0 resident until every CTA has read its claim: no CTA may exit, or
+  // overwrite the claim, while another still reads its shared memory.
+  for (;;) {
+    if (c == 0 && threadIdx.x == 0) C.next_task = atomicAdd(lp.claim, 1);
+    cl.sync();
+    const int ti = *cl_map(&C.next_task, 0);
+    cl.sync();
+    if (ti >= lp.ntasks) break;
+    run_task(lp.tasks + ti, P, c, lp.F_alloc);
     cl.sync();
   }
 }

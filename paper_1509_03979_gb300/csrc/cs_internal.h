@@ -94,6 +94,7 @@ struct Launch {
   size_t scratch_per_cluster;   // floats
   uint32_t* bits;            // per cluster: N_MAX/32 words for the sorted support output
   size_t bits_per_cluster;   // words
+  int* claim;                // task counter for dynamic claiming (zeroed), or null: static round robin
 };
 
 // Per-CTA global scratch: SCRATCH_ARRAYS arrays of 2*F_alloc 32-bit words, then the rank
