@@ -252,6 +252,13 @@ cs_status cs_get_stats(cs_op_t op, cs_stats* out);
  * Apply and LS calls have no cs_stats; this is how their callers see a timeout. */
 cs_status cs_op_sync(cs_op_t op);
 
+/* Failure-path self test (no counterpart in the paper): runs, in a one-CTA kernel, the bounded
+ * poll that the streamed path's grid barrier uses, on a device flag that is already set
+ * (set_flag != 0: returns CS_OK at once) or that nothing sets (set_flag = 0: gives up after
+ * `polls` polls, about 100 ns apart, and returns the CS_ERR_TIMEOUT the kernel reports).
+ * 1 <= polls <= 2^24.  Synchronises the device. */
+cs_status cs_probe_bounded_wait(uint64_t polls, int32_t set_flag);
+
 /* Thread-local description of the last error (never NULL). */
 const char* cs_last_error(void);
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "cs_ls_backward_batched": (_I32, [_P, _I32, _P, _I32, _P, _F32, _I32, _P]),
     "cs_get_stats": (_I32, [_P, _P]),
     "cs_op_sync": (_I32, [_P]),
+    "cs_probe_bounded_wait": (_I32, [_U64, _I32]),
     "cs_last_error": (ctypes.c_char_p, []),
 }
 

@@ -658,6 +658,23 @@ cs_status cs_op_tune_batched(cs_op_t op, int32_t B, float* ms_out) {
   return st;
 }
 
+cs_status cs_probe_bounded_wait(uint64_t polls, int32_t set_flag) {
+  if (polls < 1 || polls > (1ull << 24)) return fail(CS_ERR_INVALID_ARG, "polls must be in [1, 2^24]");
+  unsigned* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 2 * sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(probe)");
+  const unsigned init[2] = {set_flag ? 1u : 0u, 0xffffffffu};
+  int status = -1;
+  e = cudaMemcpy(buf, init, sizeof(init), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_wait_probe(buf, polls, reinterpret_cast<int*>(buf + 1), nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&status, buf + 1, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "probe");
+  if (status == CS_ERR_TIMEOUT) return fail(CS_ERR_TIMEOUT, "the bounded wait ran out (as the probe intends when the flag is never set)");
+  return (cs_status)status;
+}
+
 int32_t cs_op_concurrency(cs_op_t op) {
   if (!op) return 1;
   if (op->dev.grid) return 1;

@@ -476,6 +476,18 @@ __device__ __forceinline__ T* cl_map(T* p, int rank) { return cg::this_cluster()
 // op's status word and continues, and later barriers stop waiting once the status is set, so
 // the launch always ends.
 constexpr unsigned long long GRID_SPIN_LIMIT = 1ull << 26;
+
+// Poll *word until it differs from `from`, at most `limit` times about 100 ns apart; false when
+// the limit ran out.
+__device__ __forceinline__ bool spin_until_changed(volatile unsigned* word, unsigned from, unsigned long long limit) {
+  unsigned long long spins = 0;
+  while (*word == from) {
+    if (++spins > limit) return false;
+    __nanosleep(100);
+  }
+  return true;
+}
+
 __device__ __noinline__ void grid_sync() {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -489,14 +501,7 @@ __device__ __noinline__ void grid_sync() {
       __threadfence();
       atomicAdd(const_cast<unsigned*>(gen), 1u);
     } else if (*err == 0) {
-      unsigned long long spins = 0;
-      while (*gen == g0) {
-        if (++spins > GRID_SPIN_LIMIT) {
-          atomicExch(const_cast<int*>(err), (int)CS_ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(100);
-      }
+      if (!spin_until_changed(gen, g0, GRID_SPIN_LIMIT)) atomicExch(const_cast<int*>(err), (int)CS_ERR_TIMEOUT);
     }
     __threadfence();
   }
@@ -2554,6 +2559,17 @@ cudaError_t launch_stream(const StreamArgs& a, int nc, int clusters, cudaStream_
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = stream_config(nc, clusters, stream, attr);
   return cudaLaunchKernelEx(&cfg, stream_kernel, a);
+}
+
+// Failure-path probe: the grid barrier's bounded wait on a flag that is set (returns at once)
+// or that nothing sets (runs out after `limit` polls and reports CS_ERR_TIMEOUT).
+__global__ void wait_probe_kernel(volatile unsigned* flag, unsigned long long limit, int* status) {
+  if (threadIdx.x == 0) *status = spin_until_changed(flag, 0u, limit) ? (int)CS_OK : (int)CS_ERR_TIMEOUT;
+}
+
+cudaError_t launch_wait_probe(unsigned* flag, unsigned long long limit, int* status, cudaStream_t stream) {
+  wait_probe_kernel<<<1, 32, 0, stream>>>(flag, limit, status);
+  return cudaGetLastError();
 }
 
 }  // namespace csg

@@ -123,6 +123,8 @@ size_t stream_row_floats();    // floats of one padded intermediate row
 int stream_clusters(int nc);   // clusters of nc CTAs resident at once (0: cannot launch)
 cudaError_t launch_stream(const StreamArgs& a, int nc, int clusters, cudaStream_t stream);
 
+cudaError_t launch_wait_probe(unsigned* flag, unsigned long long limit, int* status, cudaStream_t stream);
+
 SmemPlan cluster_plan(int F_alloc);
 SmemPlan grid_plan(const OpDev& op);
 size_t smem_bytes(const SmemPlan& plan);
