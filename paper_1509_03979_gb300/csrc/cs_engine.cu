@@ -314,9 +314,10 @@ __device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
 
 // ------------------------------------------------------------------------- shared layout
 
-constexpr int CG_CAP_MAX = 0;      // support entries per CTA whose CG vectors live in shared memory
-                                   // (0: global, L1-cached; a larger L1 share measured faster)
-__host__ __device__ inline int cg_cap(int F_alloc) { return 2 * F_alloc < CG_CAP_MAX ? 2 * F_alloc : CG_CAP_MAX; }
+// Support entries per CTA whose list and CG vectors live in shared memory: up to 4096 when the
+// transform is at most 4096 points per CTA (the rest of the plan is small); none for the
+// 8192-point CTAs, where the L1 share left by a larger carve-out measured faster.
+__host__ __device__ inline int cluster_cg_cap(int F_alloc) { return F_alloc <= 4096 ? (2 * F_alloc < 4096 ? 2 * F_alloc : 4096) : 0; }
 
 struct Smem {
   float2* A;          // local FFT buffer (padded), signal-domain slots between transforms
@@ -351,7 +352,7 @@ struct Bump {
 
 __host__ __device__ inline void layout(const SmemPlan& pl, Bump& take, Smem* s) {
   const int nw = pl.slot_words;
-  const int cap = cg_cap(pl.fft_n);
+  const int cap = pl.cg_cap;
   unsigned char* A = take(sizeof(float2) * apad(pl.fft_n));
   unsigned char* B = take(sizeof(float2) * apad(pl.fft_n));   // also the FFT ping-pong buffer (padded)
   unsigned char* tl = take(sizeof(float2) * apad(pl.tw_lo_n));
@@ -395,6 +396,7 @@ SmemPlan cluster_plan(int F_alloc) {
   p.tw_hi_n = 1024;
   p.slot_words = (2 * F_alloc + 31) / 32;
   p.fb_bytes = F_alloc / 2 + P_MAX + 16;
+  p.cg_cap = cluster_cg_cap(F_alloc);
   return p;
 }
 
@@ -407,6 +409,7 @@ SmemPlan grid_plan(const OpDev& op) {
   p.tw_hi_n = 1 << op.hi_bits;
   p.slot_words = (2 * op.R * op.S1 + 31) / 32;
   p.fb_bytes = op.bpc * ((op.W / 2) * op.S2 + op.S2 + 1) + 16;
+  p.cg_cap = 0;
   return p;
 }
 
@@ -2031,7 +2034,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
     C.grid = 0;
     C.ring_slot = 0;
     C.hist_slot = 0;
-    C.cap = cg_cap(lp.F_alloc);
+    C.cap = lp.plan.cg_cap;
     float* base = lp.scratch + (size_t)cid * lp.scratch_per_cluster + (size_t)c * scratch_floats_per_cta(lp.F_alloc);
     const size_t a = 2 * (size_t)lp.F_alloc;
     C.xd[0] = base;
@@ -2076,7 +2079,7 @@ __global__ void __launch_bounds__(NT, 1) grid_kernel(const Launch lp) {
     C.grid = 1;
     C.ring_slot = 0;
     C.hist_slot = 0;
-    C.cap = cg_cap(lp.F_alloc);
+    C.cap = lp.plan.cg_cap;
     float* base = lp.scratch + (size_t)c * scratch_floats_per_cta(lp.F_alloc);
     const size_t a = 2 * (size_t)lp.F_alloc;
     C.xd[0] = base;

@@ -30,6 +30,7 @@ struct SmemPlan {
   int tw_hi_n;      // entries of the high twiddle table
   int slot_words;   // 32-bit words of each per-slot bitmask (2F slots)
   int fb_bytes;     // Omega bits of the CTA's frequency tasks
+  int cg_cap;       // support entries per CTA whose list and CG vectors live in shared memory
 };
 
 enum Mode : int {
