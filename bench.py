@@ -269,6 +269,10 @@ def run_gb300(args, rank, world, local_rank):
                 "frac": achieved / peak_alu, "traffic": traffic,
                 "kernel": "engine_kernel (SP recovery, one launch per step)",
                 "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
+    # the same step seen as HBM work: 8N bytes per N-point transform that does not fit on chip
+    # (read and write N floats), although this engine keeps every transform on chip
+    hbm_view = {"algorithmic_GBs": transforms * 8.0 * p.N / (ms_per_step / 1e3) / 1e9,
+                "bytes_per_transform": 8 * p.N, "transforms_per_step": transforms}
 
     # ---- A / A^T apply bandwidth over a batch larger than L2, both batched implementations
     hbm_peak, peak_kind = peaks()
@@ -355,7 +359,7 @@ def run_gb300(args, rank, world, local_rank):
                        "l2": "256 MiB buffer written between timed steps",
                        "parallelism": f"signals sharded over {world} GPU(s), no collective"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
-            "apply_roofline": apply, "cpu_baseline": cpu,
+            "apply_roofline": apply, "hbm_view": hbm_view, "cpu_baseline": cpu,
             "quality": {"support_recall_vs_truth": recall, "rel_err_vs_truth": err_truth,
                         "sp_rounds": rounds, "cg_iters_total": cg_iters, "status": status,
                         "transforms_per_step": transforms},
