@@ -100,12 +100,13 @@ void cs_op_destroy(cs_op_t op);
 /* Launch all further work of `op` on `cuda_stream` (a cudaStream_t; NULL = legacy default). */
 cs_status cs_op_set_stream(cs_op_t op, void* cuda_stream);
 
-/* y_M = A x_N: sign flip, orthonormal DCT-II, keep rows Omega (Sec. III-D operator list).
+/* y_M = A x_N: randomiser (sign flip or permutation), orthonormal DCT-II, keep rows Omega
+ * (Sec. III-D operator list).
  * x_N: [N] device, y_M: [M] device (written).  Buffers must not overlap. */
 cs_status cs_op_apply(cs_op_t op, const float* x_N, float* y_M);
 
-/* x_N = A^T y_M: scatter onto Omega, orthonormal DCT-III, sign flip (the correlation A^T r of
- * Eq. 6).  y_M: [M] device; x_N: [N] device (written).  Buffers must not overlap. */
+/* x_N = A^T y_M: scatter onto Omega, orthonormal DCT-III, randomiser transposed (the
+ * correlation A^T r of Eq. 6).  y_M: [M] device; x_N: [N] device (written).  Buffers must not overlap. */
 cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N);
 
 /* Batched A / A^T: B independent vectors through the same operator, one persistent launch.
@@ -186,7 +187,8 @@ cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_
  *   y           [M] device measurements
  *   K           sparsity (number of support entries returned)
  *   algo        CS_OMP, CS_SP or CS_OMPR
- *   cg_tol      relative CG tolerance (see conventions); cg_maxit >= 1
+ *   cg_tol      CG tolerance, relative or absolute (see conventions); cg_maxit >= 0 (0: at most
+ *               |S| steps, Theorem 5)
  *   s_out       [N] device, dense estimate, zeros off the support
  *   support_out [K] device, selected indices sorted ascending
  * One kernel launch on the op's stream; the whole greedy + CG loop runs on the device
@@ -211,7 +213,10 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
 cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, cs_algo algo, float cg_tol,
                              int32_t cg_maxit, float* s_out, int32_t* support_out);
 
-/* Batched recovery of B independent signals in one persistent launch per cluster size.
+/* Batched recovery of B independent signals in one persistent launch per cluster size; the
+ * launches of different sizes run concurrently on streams forked from (and joined back into)
+ * ops[0]'s stream, and the clusters of each launch claim signals largest-work first.  Signals
+ * with N > 2^18 run one cooperative launch each, after the rest.
  * ops[b], y[b], K[b], algo[b], s_out[b], support_out[b] describe signal b (HOST arrays of
  * handles/device pointers).  All ops must share one stream (taken from ops[0]).
  * stats_host [B] HOST (may be NULL): filled after the work completes -- a non-NULL
