@@ -1233,10 +1233,17 @@ __device__ __noinline__ float grid_col_block(int j, int kind, bool fwd_done, boo
   const int S1 = op.S1, S2 = op.S2, W = op.W, lw = __ffs(W) - 1;
   float2* X = shp(C.sm.A);
   if (fwd_done) {
-    for (int idx = threadIdx.x; idx < (S2 << lw); idx += NT) {
+    // S2 W = GRID_BLOCK entries, all loads of a thread in flight before any store
+    constexpr int EPT = GRID_BLOCK / NT;
+    float2 v[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int idx = threadIdx.x + e * NT;
       const int n2 = idx >> lw, sidx = idx & (W - 1);
-      X[idx] = __ldcg(op.gY + (size_t)n2 * S1 + kq_of(gb, sidx));
+      v[e] = __ldcg(op.gY + (size_t)n2 * S1 + kq_of(gb, sidx));
     }
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) X[threadIdx.x + e * NT] = v[e];
     __syncthreads();
     col_fft<-1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
   }
@@ -1267,8 +1274,13 @@ __device__ __noinline__ void grid_row_inverse(int lr) {
     const float2* row = C.op.gY + (size_t)n2 * S1;
     float2 w = tw.get<1>(8 * n2 * (int)threadIdx.x);
     const float2 step = tw.get<1>(8 * n2 * NT);
-    for (int k1 = threadIdx.x; k1 < S1; k1 += NT) {
-      X[aidx(k1)] = cmul(__ldcg(row + k1), w);
+    constexpr int EPT = GRID_S1 / NT;   // S1 = GRID_S1; all loads in flight before any use
+    float2 v[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) v[e] = __ldcg(row + threadIdx.x + e * NT);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      X[aidx(threadIdx.x + e * NT)] = cmul(v[e], w);
       w = cmul(w, step);
     }
   }
