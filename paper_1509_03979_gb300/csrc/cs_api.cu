@@ -743,7 +743,6 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
   // others back; clusters claim tasks dynamically, largest work first.
   const bool fork = groups.size() > 1;
   std::vector<cudaStream_t> aux;
-  std::vector<cudaEvent_t> evs;
   cudaError_t e;
   cudaEvent_t start = nullptr;
   if (fork) {
@@ -795,17 +794,21 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     cudaFreeAsync(d_tasks, s);
     cudaFreeAsync(L.scratch, s);
     cudaFreeAsync(L.bits, s);
-    if (fork) {
-      cudaEvent_t ev = nullptr;
-      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { st = cuda_fail(e, "event"); break; }
-      evs.push_back(ev);
-      if ((e = cudaEventRecord(ev, s)) != cudaSuccess) { st = cuda_fail(e, "event record"); break; }
-      if ((e = cudaStreamWaitEvent(stream, ev, 0)) != cudaSuccess) { st = cuda_fail(e, "stream wait"); break; }
-    }
   }
-  // streams and events are released once their work completes
-  for (cudaStream_t s : aux) cudaStreamDestroy(s);
-  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  // join every forked stream back into `stream` (also after an error, so that the caller's
+  // stream never runs ahead of work already queued); streams and events are released once
+  // their work completes
+  for (cudaStream_t s : aux) {
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) == cudaSuccess && (e = cudaEventRecord(ev, s)) == cudaSuccess)
+      e = cudaStreamWaitEvent(stream, ev, 0);
+    if (e != cudaSuccess) {
+      if (st == CS_OK) st = cuda_fail(e, "stream join");
+      cudaStreamSynchronize(s);   // the join failed: wait for the work instead
+    }
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(s);
+  }
   if (start) cudaEventDestroy(start);
   if (st != CS_OK) return st;
   // streamed geometry: the whole GPU per signal, one cooperative launch each, after the rest
