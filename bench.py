@@ -26,7 +26,11 @@ sys.path.insert(0, ROOT)
 from paper_1509_03979_gb300 import shard, synth  # noqa: E402
 
 WORKLOAD = synth.workload(2)
-CG_TOL, CG_MAXIT = 1e-6, 100
+# The metric counts recoveries within rel-err 1e-4 of the FP64 oracle.  On the N = 2^18 SP
+# workload the GPU error is set by the near-ties in the support (7-10 per signal), not by the
+# CG tolerance: measured max rel-err over the 7 signals 2.3e-5 at cg_tol 1e-6, 3.4e-5 at 5e-6,
+# 4.4e-5 at 2e-5.  5e-6 keeps a 3x margin to the bound (the CPU-baseline leg re-checks it).
+CG_TOL, CG_MAXIT = 5e-6, 100
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 SMSPs x 32)
 METRIC = "recoveries/s (SP + CG-LS, N=2^18)"
 
