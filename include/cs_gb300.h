@@ -121,7 +121,7 @@ cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N);
  *                        ordered temporary device memory per resident cluster, allocated and
  *                        freed on the op's stream per call.
  * CS_BATCHED_AUTO (the default) takes the choice of cs_op_tune_batched when it has run, else
- * the streamed kernel (2 CTAs per vector) whenever N allows it and B >= 2. */
+ * the streamed kernel (4 CTAs per vector, at most N/2^15) whenever N allows it and B >= 2. */
 cs_status cs_op_apply_batched(cs_op_t op, int32_t B, const float* X, float* Y);
 cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X);
 

@@ -187,7 +187,7 @@ cs_status check_cg(float cg_tol, int32_t cg_maxit) {
 }
 
 constexpr int SP_ROUNDS = 50;     // SP outer-iteration cap
-constexpr int STREAM_CLUSTER = 2;  // default CTAs per vector of the streamed batched operator
+constexpr int STREAM_CLUSTER = 4;  // default CTAs per vector of the streamed batched operator (fastest untuned at 256 vectors)
 constexpr int OMPR_SWAPS = 100;   // OMPR replacement cap
 
 }  // namespace
