@@ -1,0 +1,38 @@
+"""GPU parity at the benchmark's full size and launch configuration: SP + CG-LS at N = 2^18,
+M = 65 536, K = 6 554 with 1e-3 noise, one batched launch over as many signals as the GPU runs
+at once (the configuration bench.py times, same seeds and CG settings), two of them checked
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import greedy
+from paper_1509_03979_gb300 import synth
+from tests.gpu_common import SHAT_TOL, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CG_TOL, CG_MAXIT = 5e-6, 100   # the benchmark's settings for this workload
+
+
+def test_sp_full_size_batched_matches_oracle():
+    from paper_1509_03979_gb300 import binding
+    p = synth.workload(2)
+    op = binding.Operator(p.N, p.M, p.op_seed)
+    B = op.concurrency()
+    S = np.stack([synth.sparse_gaussian(p.N, p.K, p.signal_seed + 7919 * i) for i in range(B)]).astype(np.float32)
+    noise = np.stack([synth.normals(p.noise_seed + 7919 * i, p.M) for i in range(B)]).astype(np.float32)
+    Yc = op.apply_batched(torch.from_numpy(S).cuda())
+    sigma = p.noise_rel * torch.linalg.vector_norm(Yc, dim=1, keepdim=True) / np.sqrt(p.M)
+    Y = (Yc + sigma * torch.from_numpy(noise).cuda()).contiguous()
+    s_b, k_b, st = binding.recover_batched([op] * B, [Y[b] for b in range(B)], [p.K] * B, ["sp"] * B,
+                                           CG_TOL, CG_MAXIT, want_stats=True)
+    assert all(x["status"] == 0 for x in st)
+    ref = oracle.Operator(p.N, p.M, p.op_seed)
+    for b in (0, B - 1):
+        want = greedy.sp(ref, Y[b].cpu().numpy().astype(np.float64), p.K)
+        assert rel(s_b[b].cpu().numpy(), want["s"]) <= SHAT_TOL, b
+        got = set(k_b[b].cpu().numpy().tolist())
+        # supports differ only at the oracle's near-ties: at most that many entries
+        assert len(got ^ set(want["S"].tolist())) <= 2 * want["near_ties"], b
