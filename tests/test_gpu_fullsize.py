@@ -36,3 +36,30 @@ def test_sp_full_size_batched_matches_oracle():
         got = set(k_b[b].cpu().numpy().tolist())
         # supports differ only at the oracle's near-ties: at most that many entries
         assert len(got ^ set(want["S"].tolist())) <= 2 * want["near_ties"], b
+
+
+def test_mixed_batch_full_size_sampled_against_oracle():
+    """The full 256-signal mixed batch in one call, as bench.py --workload batched runs it;
+    sampled outputs the oracle can recompute quickly: the four smallest-work signals and the
+    largest-N SP signal."""
+    from paper_1509_03979_gb300 import binding
+    probs = synth.batched_workload(B=256)
+    ops, ys = [], []
+    for p in probs:
+        op = binding.Operator(p.N, p.M, p.op_seed)
+        yc = op.apply(torch.from_numpy(p.signal().astype(np.float32)).cuda())
+        sig = p.noise_rel * torch.linalg.vector_norm(yc) / np.sqrt(p.M)
+        ys.append((yc + sig * torch.from_numpy(p.noise_unit().astype(np.float32)).cuda()).contiguous())
+        ops.append(op)
+    s_b, k_b, st = binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs],
+                                           CG_TOL, CG_MAXIT, want_stats=True)
+    assert all(x["status"] == 0 for x in st)
+    work = [p.N * p.K for p in probs]
+    sample = list(np.argsort(work)[:4])
+    sp_big = [i for i, p in enumerate(probs) if p.algo == "sp"]
+    sample.append(max(sp_big, key=lambda i: (probs[i].N, -probs[i].K)))
+    for i in sample:
+        p = probs[i]
+        ref = oracle.Operator(p.N, p.M, p.op_seed)
+        want = greedy.recover(ref, ys[i].cpu().numpy().astype(np.float64), p.K, p.algo)
+        assert rel(s_b[i].cpu().numpy(), want["s"]) <= SHAT_TOL, (i, p)
