@@ -38,6 +38,14 @@
  *     vanishes in FP32 ends the solve (the residual is at rounding level).
  *   - cs_last_error() returns a thread-local message describing the last failure.
  *   - Operators are not thread-safe: one host thread at a time per cs_op_t.
+ *   - CUDA graphs: cs_op_apply(_t)(_batched), cs_recover, cs_recover_batched (stats_host
+ *     NULL), cs_ls_* and cs_recover_noalloc may be captured into a graph on the op's stream
+ *     once the same call has run uncaptured (first calls set kernel attributes and look up
+ *     device addresses); every launch carries its tables in its own parameters, so a replay
+ *     needs no host memory of the capturing call.  Under capture, cs_recover_batched runs
+ *     its cluster sizes one after another instead of on forked streams.  The autotuners,
+ *     cs_get_stats, cs_op_sync and a non-NULL stats_host wait on the host and cannot be
+ *     captured.
  */
 #ifndef CS_GB300_H
 #define CS_GB300_H
@@ -263,6 +271,12 @@ cs_status cs_op_sync(cs_op_t op);
  * `polls` polls, about 100 ns apart, and returns the CS_ERR_TIMEOUT the kernel reports).
  * 1 <= polls <= 2^24.  Synchronises the device. */
 cs_status cs_probe_bounded_wait(uint64_t polls, int32_t set_flag);
+
+/* Kernel launches this library has issued in this process, over all devices and operators:
+ * every engine, grid, streamed-operator, task-table-upload and probe launch that was accepted
+ * by the runtime (launches captured into a graph count once, at capture; replays do not).
+ * The difference of two readings counts the launches of the calls made between them. */
+int64_t cs_launch_count(void);
 
 /* Thread-local description of the last error (never NULL). */
 const char* cs_last_error(void);

@@ -62,6 +62,7 @@ SIGNATURES = {
     "cs_op_sync": (_I32, [_P]),
     "cs_probe_bounded_wait": (_I32, [_U64, _I32]),
     "cs_last_error": (ctypes.c_char_p, []),
+    "cs_launch_count": (ctypes.c_int64, []),
 }
 
 
@@ -95,6 +96,11 @@ def _dev(t, dtype, n=None, name="tensor"):
     if n is not None and t.numel() != n:
         raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def launch_count():
+    """Kernel launches this library has issued in this process (cs_launch_count)."""
+    return int(lib().cs_launch_count())
 
 
 def operator_draws(N, M, seed):

@@ -1,12 +1,15 @@
 // cs_api.cu -- host side of the C ABI declared in include/cs_gb300.h.
 //
 // Builds the operator's random draws and tables (Sec. III-A, Eq. 7), validates arguments,
-// packs tasks and launches the cluster engine of cs_engine.cu.  No compute happens here.
+// packs tasks and launches the cluster engine of cs_engine.cu.  No compute happens here; the
+// one kernel defined in this file copies task tables from its launch parameters to the device.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -26,6 +29,13 @@ cs_status fail(cs_status st, const std::string& msg) {
 }
 cs_status cuda_fail(cudaError_t e, const char* what) {
   return fail(CS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Kernel launches issued by this library in this process (cs_launch_count).
+std::atomic<int64_t> g_launches{0};
+cudaError_t counted(cudaError_t e) {
+  if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
 }
 
 constexpr uint64_t GAMMA = 0x9E3779B97F4A7C15ull;
@@ -172,11 +182,11 @@ cs_status run_single(cs_op* op, const Task& t) {
   cudaError_t e;
   if (op->dev.grid) {
     if ((e = cudaMemsetAsync(op->dev.gerr, 0, sizeof(int), op->stream)) != cudaSuccess) return cuda_fail(e, "memset");
-    e = launch_grid(L, op->dev.G, op->stream);
+    e = counted(launch_grid(L, op->dev.G, op->stream));
     if (e != cudaSuccess) return cuda_fail(e, "grid launch");
     return CS_OK;
   }
-  e = launch_engine(L, op->dev.P, 1, op->stream);
+  e = counted(launch_engine(L, op->dev.P, 1, op->stream));
   if (e != cudaSuccess) return cuda_fail(e, "engine launch");
   return CS_OK;
 }
@@ -195,6 +205,8 @@ constexpr int OMPR_SWAPS = 100;   // OMPR replacement cap
 extern "C" {
 
 const char* cs_last_error(void) { return g_err.c_str(); }
+
+int64_t cs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_M_host, int8_t* d_N_host) {
   const cs_status st = check_nm(N, M);
@@ -446,7 +458,7 @@ static cs_status stream_apply(cs_op_t op, int mode, int32_t B, const float* in, 
   if ((e = cudaMemsetAsync(op->d_stream_err, 0, sizeof(int), op->stream)) != cudaSuccess) return cuda_fail(e, "memset");
   const size_t bytes = sizeof(float) * stream_row_floats() * (size_t)op->dev.P * (size_t)clusters;
   if ((e = cudaMallocAsync(&a.T, bytes, op->stream)) != cudaSuccess) return cuda_fail(e, "alloc stream rows");
-  e = launch_stream(a, nc, clusters, op->stream);
+  e = counted(launch_stream(a, nc, clusters, op->stream));
   cudaFreeAsync(a.T, op->stream);
   if (e != cudaSuccess) return cuda_fail(e, "stream launch");
   return CS_OK;
@@ -666,7 +678,7 @@ cs_status cs_probe_bounded_wait(uint64_t polls, int32_t set_flag) {
   const unsigned init[2] = {set_flag ? 1u : 0u, 0xffffffffu};
   int status = -1;
   e = cudaMemcpy(buf, init, sizeof(init), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = launch_wait_probe(buf, polls, reinterpret_cast<int*>(buf + 1), nullptr);
+  if (e == cudaSuccess) e = counted(launch_wait_probe(buf, polls, reinterpret_cast<int*>(buf + 1), nullptr));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&status, buf + 1, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(buf);
@@ -729,6 +741,43 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
   return run_single(op, t);
 }
 
+// Task tables reach the device inside kernel launch parameters, TASK_CHUNK tasks per launch of
+// task_upload_kernel, instead of a copy from host memory: parameter values are copied when the
+// launch is issued, so the call can return (and its host vector die) at once, and a launch
+// captured into a CUDA graph carries its own tables rather than a pointer into freed host
+// memory.  The first chunk also zeroes the dynamic-claim counter that follows the table.
+constexpr int TASK_CHUNK = 120;
+struct TaskChunk {
+  Task t[TASK_CHUNK];
+  int n;                     // tasks in this chunk
+  int first;                 // index of t[0] in the device table
+};
+static_assert(sizeof(TaskChunk) <= 32000, "task chunk must fit the 32 KB kernel-parameter limit");
+static_assert(sizeof(Task) % 4 == 0, "tasks are copied as 32-bit words");
+
+__global__ void task_upload_kernel(const __grid_constant__ TaskChunk c, Task* dst, int* claim) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(c.t);
+  uint32_t* out = reinterpret_cast<uint32_t*>(dst + c.first);
+  const int words = c.n * (int)(sizeof(Task) / 4);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) out[i] = src[i];
+  if (c.first == 0 && claim && blockIdx.x == 0 && threadIdx.x == 0) *claim = 0;
+}
+
+static cudaError_t upload_tasks(const std::vector<Task>& g, Task* dst, int* claim, cudaStream_t s) {
+  auto chunk = std::make_unique<TaskChunk>();   // staging only: each launch copies it
+  TaskChunk& c = *chunk;
+  for (size_t first = 0; first < g.size(); first += TASK_CHUNK) {
+    c.n = (int)std::min<size_t>(TASK_CHUNK, g.size() - first);
+    c.first = (int)first;
+    std::memcpy(c.t, g.data() + first, sizeof(Task) * (size_t)c.n);
+    const int words = c.n * (int)(sizeof(Task) / 4);
+    task_upload_kernel<<<(words + 255) / 256, 256, 0, s>>>(c, dst, claim);
+    const cudaError_t e = counted(cudaGetLastError());
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Launch a list of tasks grouped by cluster size; scratch and task arrays come from the
 // stream-ordered allocator and are released on the same stream.
 static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
@@ -741,7 +790,10 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
   // One persistent launch per cluster size.  With several sizes the launches run concurrently on
   // forked streams (joined back into `stream`), so a long signal of one size does not hold the
   // others back; clusters claim tasks dynamically, largest work first.
-  const bool fork = groups.size() > 1;
+  // (While the stream is being captured into a CUDA graph the sizes run one after another on it.)
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &capturing) != cudaSuccess) return fail(CS_ERR_CUDA, "stream capture query failed");
+  const bool fork = groups.size() > 1 && capturing == cudaStreamCaptureStatusNone;
   std::vector<cudaStream_t> aux;
   cudaError_t e;
   cudaEvent_t start = nullptr;
@@ -774,26 +826,31 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     L.scratch_per_cluster = (size_t)P * scratch_floats_per_cta(F_alloc);
     L.bits_per_cluster = (size_t)(Nmax + 31) / 32;
     Task* d_tasks = nullptr;
-    if ((e = cudaMallocAsync(&d_tasks, sizeof(Task) * g.size() + 16, s)) != cudaSuccess) { st = cuda_fail(e, "alloc tasks"); break; }
     if ((e = cudaMallocAsync(&L.scratch, sizeof(float) * L.scratch_per_cluster * G, s)) != cudaSuccess) {
       st = cuda_fail(e, "alloc scratch");
       break;
     }
     if ((e = cudaMallocAsync(&L.bits, sizeof(uint32_t) * L.bits_per_cluster * G, s)) != cudaSuccess) {
+      cudaFreeAsync(L.scratch, s);
       st = cuda_fail(e, "alloc bits");
       break;
     }
-    if ((e = cudaMemcpyAsync(d_tasks, g.data(), sizeof(Task) * g.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
-      st = cuda_fail(e, "upload tasks");
-      break;
+    if (g.size() == 1) {
+      L.single = g[0];   // one task travels in the engine's own launch parameters
+      e = cudaSuccess;
+    } else {
+      if ((e = cudaMallocAsync(&d_tasks, sizeof(Task) * g.size() + 16, s)) == cudaSuccess) {
+        L.claim = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(d_tasks) + sizeof(Task) * g.size());
+        e = upload_tasks(g, d_tasks, L.claim, s);
+      }
+      L.tasks = d_tasks;
     }
-    L.claim = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(d_tasks) + sizeof(Task) * g.size());
-    if ((e = cudaMemsetAsync(L.claim, 0, sizeof(int), s)) != cudaSuccess) { st = cuda_fail(e, "memset"); break; }
-    L.tasks = d_tasks;
-    if ((e = launch_engine(L, P, G, s)) != cudaSuccess) { st = cuda_fail(e, "engine launch"); break; }
-    cudaFreeAsync(d_tasks, s);
+    if (e == cudaSuccess && (e = counted(launch_engine(L, P, G, s))) != cudaSuccess) st = cuda_fail(e, "engine launch");
+    else if (e != cudaSuccess) st = cuda_fail(e, "upload tasks");
+    if (d_tasks) cudaFreeAsync(d_tasks, s);
     cudaFreeAsync(L.scratch, s);
     cudaFreeAsync(L.bits, s);
+    if (st != CS_OK) break;
   }
   // join every forked stream back into `stream` (also after an error, so that the caller's
   // stream never runs ahead of work already queued); streams and events are released once
@@ -824,7 +881,7 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     L.bits = t.grid_bits;
     L.bits_per_cluster = 0;
     if ((e = cudaMemsetAsync(t.op.gerr, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "memset");
-    if ((e = launch_grid(L, t.op.G, stream)) != cudaSuccess) return cuda_fail(e, "grid launch");
+    if ((e = counted(launch_grid(L, t.op.G, stream))) != cudaSuccess) return cuda_fail(e, "grid launch");
   }
   return CS_OK;
 }
@@ -840,6 +897,12 @@ cs_status cs_recover_batched(int32_t B, const cs_op_t* ops, const float* const* 
   cudaStream_t stream = ops[0] ? ops[0]->stream : nullptr;
   cs_stats* d_stats = nullptr;
   cudaError_t e;
+  if (stats_host) {   // the statistics are read back synchronously: not inside a graph capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(stream, &cap)) != cudaSuccess) return cuda_fail(e, "stream capture query");
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(CS_ERR_INVALID_ARG, "stats_host must be null while the stream is captured into a graph");
+  }
   if ((e = cudaMallocAsync(&d_stats, sizeof(cs_stats) * (size_t)B, stream)) != cudaSuccess) return cuda_fail(e, "alloc stats");
   if ((e = cudaMemsetAsync(d_stats, 0, sizeof(cs_stats) * (size_t)B, stream)) != cudaSuccess) return cuda_fail(e, "memset");
   std::vector<Task> tasks;
@@ -1037,7 +1100,7 @@ extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, c
   L.bits_per_cluster = (size_t)(op->N + 31) / 32;
   // every scratch word the engine reads is written earlier in the same launch, so nothing
   // needs clearing between calls
-  const cudaError_t e = launch_engine(L, op->dev.P, 1, op->stream);
+  const cudaError_t e = counted(launch_engine(L, op->dev.P, 1, op->stream));
   if (e != cudaSuccess) return cuda_fail(e, "engine launch");
   return CS_OK;
 }

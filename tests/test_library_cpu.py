@@ -59,3 +59,8 @@ def test_permutation_draw_matches_oracle(lib, N, seed):
     p = np.zeros(N, dtype=np.int32)
     assert lib.cs_operator_perm(N, seed, p.ctypes.data_as(ctypes.c_void_p)) == 0
     assert np.array_equal(p.astype(np.int64), rng.perm(N, seed))
+
+
+def test_launch_counter_starts_at_zero_without_a_gpu(lib):
+    # nothing can launch on a machine without a GPU; the counter is process-wide
+    assert lib.cs_launch_count() == 0
