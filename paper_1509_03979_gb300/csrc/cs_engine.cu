@@ -315,9 +315,10 @@ __device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
 // ------------------------------------------------------------------------- shared layout
 
 // Support entries per CTA whose list and CG vectors live in shared memory: up to 4096 when the
-// transform is at most 4096 points per CTA (the rest of the plan is small); none for the
-// 8192-point CTAs, where the L1 share left by a larger carve-out measured faster.
-__host__ __device__ inline int cluster_cg_cap(int F_alloc) { return F_alloc <= 4096 ? (2 * F_alloc < 4096 ? 2 * F_alloc : 4096) : 0; }
+// transform is at most 4096 points per CTA (the rest of the plan is small); 1024 (20 KB) for
+// the 8192-point CTAs, where a larger share costs more in L1 than it saves (SP at N = 2^18:
+// 1024 measured 5 % faster than none, 2048 4 %; its merged support puts ~820 entries per CTA).
+__host__ __device__ inline int cluster_cg_cap(int F_alloc) { return F_alloc <= 4096 ? (2 * F_alloc < 4096 ? 2 * F_alloc : 4096) : 1024; }
 
 struct Smem {
   float2* A;          // local FFT buffer (padded), signal-domain slots between transforms
@@ -1067,10 +1068,13 @@ __device__ __forceinline__ float freq_half(int kind, bool fwd_done, bool inv, co
                           : freq_half_k<false>(kind, fwd_done, inv, vin, vout);
 }
 
-// Inverse exchange: P-point inverse DFT per column, cluster barrier, all-to-all pull back into
-// the stride-P layout with conj(omega_L^{c k}).  The twiddle of element
-// k = k0 + e NT is conj(omega_L^{c k0}) * conj(omega_L^{c NT})^e: one strided lookup per
-// thread and broadcast powers.
+// Inverse exchange: P-point inverse DFT per column, then an all-to-all PUSH back into the
+// stride-P layout: row p of this CTA's columns goes to CTA p's A at k = k_q(s), times
+// conj(omega_L^{p k}).  Remote stores do not stall the issuing warp the way remote loads do,
+// and no barrier is needed before them: CTA p's A is the source of the forward pull, and the
+// only slots written here (this CTA's own k_q) are the ones this CTA already pulled.  The
+// caller's cluster barrier after this function makes every push visible before the inverse
+// FFT reads A.
 __device__ __noinline__ void exchange_inv() {
   const Geo g = C.g;
   const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
@@ -1078,37 +1082,22 @@ __device__ __noinline__ void exchange_inv() {
   float2* B = shp(C.sm.B);
   const int F = g.F, S2 = g.S2;
   pstep<1>(B, g.P, S2);
-  cl_sync();                                      // every CTA's B is final
   {
     constexpr int EPT = F_MAX / NT;
-    float2 v[EPT];
+    const int ls2 = g.lh + 1;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      const int k = threadIdx.x + e * NT;
-      if (k < F) {
-        int cc, s;
-        owner_of_kq(g, k, cc, s);
-        v[e] = cl_map(B, cc)[g.c * S2 + s];
-      }
-    }
-    if (g.c == 0) {
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int k = threadIdx.x + e * NT;
-        if (k < F) A[aidx(k)] = v[e];
-      }
-    } else {
-      float2 w = tw.get<1>(8 * g.c * (int)threadIdx.x);
-      const float2 step = tw.get<1>(8 * g.c * NT);
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int k = threadIdx.x + e * NT;
-        if (k < F) A[aidx(k)] = cmul(v[e], w);
-        w = cmul(w, step);
+      const int idx = threadIdx.x + e * NT;
+      if (idx < F) {
+        const int p = idx >> ls2;
+        const int s = idx & (S2 - 1);
+        const int k = kq_of(g, s);
+        float2 v = B[idx];
+        if (p != 0) v = cmul(v, tw.get<1>(8 * p * k));
+        cl_map(A, p)[aidx(k)] = v;
       }
     }
   }
-  __syncthreads();
 }
 
 // ------------------------------------------------------ streamed transform (grid launches)
@@ -1333,7 +1322,7 @@ __device__ __noinline__ float transform(int src, int nloc, const float* dense, c
   const float acc = freq_half(kind, src != SRC_NONE, inv, vin, vout);
   if (inv) {
     exchange_inv();
-    cl_sync();                                    // every pull from B is done: B is scratch again
+    cl_sync();                                    // every push into A has landed; B is scratch again
     local_fft<1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
   } else {
     cl_sync();                                    // nobody still reads this CTA's A
