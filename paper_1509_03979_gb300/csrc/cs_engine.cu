@@ -272,6 +272,18 @@ __device__ __noinline__ void local_fft(float2* X, float2* Y, int F, Tw tw, int f
   }
 }
 
+// The F_MAX = 2^13 plan after its leading radix-2 pass, for input already in that pass's
+// output layout in Y: three radix-16 passes, Y -> X -> Y -> X.
+static_assert(F_MAX == 8192, "fft_after_radix2 follows the 2^13 plan");
+template <int DIR>
+__device__ __noinline__ void fft_after_radix2(float2* X, float2* Y, Tw tw, int four_n) {
+  X = shp(X);
+  Y = shp(Y);
+  tw.lo = shp(tw.lo);
+  tw.hi = shp(tw.hi);
+  fft_rest<13, DIR, 1, false>(X, Y, tw, four_n);
+}
+
 // P-point DFT across CTAs, one frequency slot column per thread; B is laid out [p][s].
 template <int R, int DIR>
 __device__ __forceinline__ void pcol(float2* B, int s, int S2) {
@@ -857,7 +869,7 @@ __device__ __forceinline__ void pull_fwd(const Geo& g, const Tw& tw, float2* A, 
   }
 }
 
-__device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, const float* gin) {
+__device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, const float* gin, bool pre2) {
   const Geo g = C.g;
   float2* A = shp(C.sm.A);
   const uint32_t* signw = shp(C.sm.signw);
@@ -879,21 +891,28 @@ __device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, 
       }
     }
   } else {
+    // sparse sources: zero the buffer, then place the support values.  With pre2 the values go
+    // straight into B in the layout after the FFT's leading radix-2 pass (F = 2^13 plans start
+    // with one), Y[2j] = X[j] + X[j + F/2] and Y[2j+1] = X[j] - X[j + F/2], accumulated by
+    // shared-memory atomics: an output has two terms at most, so the order cannot change it.
+    float2* D = pre2 ? shp(C.sm.B) : A;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4* A4 = reinterpret_cast<float4*>(A);
-    for (int q = threadIdx.x; q < apad(F) / 2; q += NT) A4[q] = z4;
+    float4* D4 = reinterpret_cast<float4*>(D);
+    for (int q = threadIdx.x; q < apad(F) / 2; q += NT) D4[q] = z4;
     __syncthreads();
     const int* list = C.list;
-    if (src == SRC_CG) {
-      const float* vals = C.cgp;
-      for (int i = threadIdx.x; i < nloc; i += NT) {
-        const int sg = list[i];
-        slot_ref(A, sg) = vals[i] * sgn_bits(signw, sg);
-      }
-    } else {
-      for (int i = threadIdx.x; i < nloc; i += NT) {
-        const int sg = list[i];
-        slot_ref(A, sg) = dense[sg] * sgn_bits(signw, sg);
+    const float* vals = C.cgp;
+    float* Df = reinterpret_cast<float*>(D);
+    const int half = F >> 1;
+    for (int i = threadIdx.x; i < nloc; i += NT) {
+      const int sg = list[i];
+      const float v = (src == SRC_CG ? vals[i] : dense[sg]) * sgn_bits(signw, sg);
+      if (pre2) {
+        const int q = sg >> 1, b = sg & 1, j = q & (half - 1);
+        atomicAdd(Df + 2 * aidx(2 * j) + b, v);
+        atomicAdd(Df + 2 * aidx(2 * j + 1) + b, q < half ? v : -v);
+      } else {
+        slot_ref(A, sg) = v;
       }
     }
   }
@@ -1309,15 +1328,17 @@ __device__ __noinline__ float transform(int src, int nloc, const float* dense, c
   // Each step is its own call and this function holds almost nothing live across them, so
   // every step gets the full register budget (ptxas allocates registers across calls).
   if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
-  // B is free at the start of every transform: each transform ends with (or is followed by)
-  // a cluster barrier after the last remote read of B, so the forward FFT may use B as its
-  // ping-pong buffer.
+  // B is free at the start of every transform: no other CTA reads it (both exchanges move A),
+  // and this CTA's last use of it, the inverse FFT, is over; so the scatter of a sparse source
+  // and the forward FFT may use it.
   if (src != SRC_NONE) {
-    scatter_fwd(src, nloc, dense, gin);
-    local_fft<-1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
+    const bool pre2 = src != SRC_GLOBAL_N && C.g.F == F_MAX;
+    scatter_fwd(src, nloc, dense, gin, pre2);
+    if (pre2) fft_after_radix2<-1>(C.sm.A, C.sm.B, C.tw, C.g.four_n);
+    else local_fft<-1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
     exchange_fwd();
   } else {
-    cl_sync();                                    // nobody still reads this CTA's B
+    cl_sync();                                    // every CTA is done with its A before any push
   }
   const float acc = freq_half(kind, src != SRC_NONE, inv, vin, vout);
   if (inv) {
