@@ -42,8 +42,9 @@
  *     NULL), cs_ls_* and cs_recover_noalloc may be captured into a graph on the op's stream
  *     once the same call has run uncaptured (first calls set kernel attributes and look up
  *     device addresses); every launch carries its tables in its own parameters, so a replay
- *     needs no host memory of the capturing call.  Under capture, cs_recover_batched runs
- *     its cluster sizes one after another instead of on forked streams.  The autotuners,
+ *     needs no host memory of the capturing call.  The concurrent launches of
+ *     cs_recover_batched (one per cluster size) run on streams that ops[0] keeps for the
+ *     purpose, so under capture they become parallel branches of the graph.  The autotuners,
  *     cs_get_stats, cs_op_sync and a non-NULL stats_host wait on the host and cannot be
  *     captured.
  */

@@ -124,6 +124,7 @@ struct cs_op {
   int cg_abs = 0;               // CG stopping rule: 0 relative, 1 absolute (cs_op_set_cg_tol_mode)
   int ompr_l = 1;               // OMPR replacements per round (cs_op_set_ompr_replacements)
   int tuned_nc[2] = {0, 0};     // per mode (A, A^T): 0 untuned, -1 cluster engine, else CTAs per vector
+  std::vector<cudaStream_t> fork_streams;   // created on first use, kept until cs_op_destroy
 };
 
 namespace {
@@ -142,6 +143,7 @@ void free_op(cs_op* op) {
   cudaFree(op->d_prank);
   cudaFree(op->d_perm);
   cudaFree(op->d_stream_err);
+  for (cudaStream_t s : op->fork_streams) cudaStreamDestroy(s);
   delete op;
 }
 
@@ -436,7 +438,7 @@ cs_status cs_op_apply_t(cs_op_t op, const float* y_M, float* x_N) {
   return run_single(op, t);
 }
 
-static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream);
+static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream, cs_op* owner);
 
 // Streamed batched operator: one cluster of nc CTAs per vector, a per-cluster intermediate
 // freed after the launch.
@@ -488,7 +490,7 @@ static cs_status apply_with(cs_op_t op, int mode, int32_t B, const float* in, fl
     tasks.push_back(t);
   }
   if (B == 1) return run_single(op, tasks[0]);
-  return launch_tasks(tasks, op->stream);
+  return launch_tasks(tasks, op->stream, op);
 }
 
 static cs_status apply_batched(cs_op_t op, int mode, int32_t B, const float* in, float* out) {
@@ -780,7 +782,7 @@ static cudaError_t upload_tasks(const std::vector<Task>& g, Task* dst, int* clai
 
 // Launch a list of tasks grouped by cluster size; scratch and task arrays come from the
 // stream-ordered allocator and are released on the same stream.
-static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
+static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream, cs_op* owner) {
   std::map<int, std::vector<Task>> groups;
   std::vector<Task> grid_tasks;
   for (const Task& t : tasks) {
@@ -788,12 +790,12 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     else groups[t.op.P].push_back(t);
   }
   // One persistent launch per cluster size.  With several sizes the launches run concurrently on
-  // forked streams (joined back into `stream`), so a long signal of one size does not hold the
-  // others back; clusters claim tasks dynamically, largest work first.
-  // (While the stream is being captured into a CUDA graph the sizes run one after another on it.)
-  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(stream, &capturing) != cudaSuccess) return fail(CS_ERR_CUDA, "stream capture query failed");
-  const bool fork = groups.size() > 1 && capturing == cudaStreamCaptureStatusNone;
+  // streams forked from `stream` (event record + wait) and joined back into it, so a long signal
+  // of one size does not hold the others back; clusters claim tasks dynamically, largest work
+  // first.  The forked streams belong to the owning operator and outlive the call, so the same
+  // fork and join also work while `stream` is being captured into a CUDA graph (they become
+  // parallel branches of the graph).
+  const bool fork = groups.size() > 1;
   std::vector<cudaStream_t> aux;
   cudaError_t e;
   cudaEvent_t start = nullptr;
@@ -807,7 +809,12 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     std::vector<Task>& g = kv.second;
     cudaStream_t s = stream;
     if (fork) {
-      if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) { st = cuda_fail(e, "stream"); break; }
+      const size_t i = aux.size();
+      if (i >= owner->fork_streams.size()) {
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) { st = cuda_fail(e, "stream"); break; }
+        owner->fork_streams.push_back(s);
+      }
+      s = owner->fork_streams[i];
       aux.push_back(s);
       if ((e = cudaStreamWaitEvent(s, start, 0)) != cudaSuccess) { st = cuda_fail(e, "stream wait"); break; }
     }
@@ -853,8 +860,8 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
     if (st != CS_OK) break;
   }
   // join every forked stream back into `stream` (also after an error, so that the caller's
-  // stream never runs ahead of work already queued); streams and events are released once
-  // their work completes
+  // stream never runs ahead of work already queued); events are released once their work
+  // completes, the streams stay with the operator
   for (cudaStream_t s : aux) {
     cudaEvent_t ev = nullptr;
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) == cudaSuccess && (e = cudaEventRecord(ev, s)) == cudaSuccess)
@@ -864,7 +871,6 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream) {
       cudaStreamSynchronize(s);   // the join failed: wait for the work instead
     }
     if (ev) cudaEventDestroy(ev);
-    cudaStreamDestroy(s);
   }
   if (start) cudaEventDestroy(start);
   if (st != CS_OK) return st;
@@ -928,7 +934,7 @@ cs_status cs_recover_batched(int32_t B, const cs_op_t* ops, const float* const* 
     t.stats = d_stats + b;
     tasks.push_back(t);
   }
-  st = launch_tasks(tasks, stream);
+  st = launch_tasks(tasks, stream, ops[0]);
   if (st == CS_OK && stats_host) {
     if ((e = cudaMemcpyAsync(stats_host, d_stats, sizeof(cs_stats) * (size_t)B, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
       st = cuda_fail(e, "stats copy");
@@ -969,7 +975,7 @@ static cs_status ls_batched(cs_op_t op, int mode, int32_t B, const int32_t* supp
   }
   if (B == 1) return run_single(op, tasks[0]);
   for (Task& t : tasks) t.stats = nullptr;
-  return launch_tasks(tasks, op->stream);
+  return launch_tasks(tasks, op->stream, op);
 }
 
 cs_status cs_ls_solve(cs_op_t op, const int32_t* support, int32_t k, const float* y, float cg_tol, int32_t cg_maxit,
