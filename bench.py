@@ -55,7 +55,7 @@ def parse():
                          "calls; ompr22: OMPR at N=2^22; ls16: differentiable LS, 32 signals at N=2^16; "
                          "paper: the paper's own workload and CG precisions over N (Tables II-IV); "
                          "omp4k: single-signal OMP at N=4096 with the autotuned cluster size")
-    ap.add_argument("--paper-max-log2n", type=int, default=22, help="largest log2 N of the paper sweep")
+    ap.add_argument("--paper-max-log2n", type=int, default=23, help="largest log2 N of the paper sweep")
     ap.add_argument("--batched-count", type=int, default=256)
     return ap.parse_args()
 

@@ -21,9 +21,9 @@
  *     FP32 values and int32 indices, contiguous, unless a comment says "host".
  *   - Calls are asynchronous on the operator's stream (cs_op_set_stream); they return after
  *     the launch.  Argument errors are returned synchronously and nothing is launched.
- *   - N must be a power of two with 16 <= N <= 2^22 (else CS_ERR_UNSUPPORTED_N);
+ *   - N must be a power of two with 16 <= N <= 2^23 (else CS_ERR_UNSUPPORTED_N);
  *     1 <= M <= N; 0 <= K <= M; for SP also 2K <= M (else CS_ERR_INVALID_ARG).
- *     N <= 2^18 runs on one thread-block cluster per signal; 2^18 < N <= 2^22 runs on a
+ *     N <= 2^18 runs on one thread-block cluster per signal; 2^18 < N <= 2^23 runs on a
  *     cooperative grid of up to 128 CTAs per signal that streams the transform through L2
  *     (such signals are processed one after another, also inside the batched calls).
  *     A grid-wide wait that does not finish within its iteration limit ends the launch early:

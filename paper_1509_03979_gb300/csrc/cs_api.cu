@@ -93,7 +93,7 @@ int8_t draw_sign(uint64_t sign_key, int64_t n) {
 
 cs_status check_nm(int64_t N, int64_t M) {
   if (!is_pow2(N) || N < N_MIN || N > N_MAX_GRID)
-    return fail(CS_ERR_UNSUPPORTED_N, "N must be a power of two in [16, 2^22], got " + std::to_string(N));
+    return fail(CS_ERR_UNSUPPORTED_N, "N must be a power of two in [16, 2^23], got " + std::to_string(N));
   if (M < 1 || M > N) return fail(CS_ERR_INVALID_ARG, "M must satisfy 1 <= M <= N");
   return CS_OK;
 }

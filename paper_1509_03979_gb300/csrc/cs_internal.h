@@ -21,7 +21,7 @@ constexpr int SCRATCH_ARRAYS = 8;   // per-CTA global arrays of 2F words (see Sc
 constexpr int GRID_S1 = 4096;
 constexpr int GRID_G_MAX = 128;
 constexpr int GRID_BLOCK = 4096;    // complex points per column block (W = GRID_BLOCK / S2)
-constexpr int N_MAX_GRID = 1 << 22;
+constexpr int N_MAX_GRID = 1 << 23;   // 2^23: the streamed plan's 225 KB of shared memory per CTA
 
 // Shared-memory sizing of one launch.
 struct SmemPlan {

@@ -19,7 +19,8 @@ def B():
     return binding
 
 
-@pytest.mark.parametrize("N,M", [(1 << 19, 1 << 17), (1 << 20, 300000), (1 << 21, 1 << 19), (1 << 22, 1 << 20)])
+@pytest.mark.parametrize("N,M", [(1 << 19, 1 << 17), (1 << 20, 300000), (1 << 21, 1 << 19), (1 << 22, 1 << 20),
+                                 (1 << 23, 1 << 21)])
 def test_streamed_apply_and_transpose(B, N, M):
     op = B.Operator(N, M, 91)
     ref = oracle.Operator(N, M, 91)
@@ -90,3 +91,24 @@ def test_ompr_workload3_full_size_properties(B):
         out[S] = False
         zj, zi = np.abs(z[out]).max(), np.abs(z[S]).min()
         assert zj <= zi * (1 + 1e-3), (zj, zi)
+
+
+@pytest.mark.parametrize("algo,K", [("sp", 2000), ("ompr", 600)])
+def test_n23_recovery_properties(B, algo, K):
+    """N = 2^23 (the largest streamed size; 225 KB of shared memory per CTA), M = N/4, noiseless
+    K-sparse Gaussian signal: the decoders recover it exactly (K << M), the returned support is
+    the true one, and the coefficients are the FP64 least-squares solution on that support."""
+    N, M = 1 << 23, 1 << 21
+    ref_op = oracle.Operator(N, M, 0x23001)
+    s_true = synth.sparse_gaussian(N, K, 0x23002)
+    y = ref_op.apply(s_true).astype(np.float32)
+    op = B.Operator(N, M, 0x23001)
+    s, supp = op.recover(to_dev(y), K, algo, 1e-6, 200)
+    st = op.stats()
+    assert st["status"] == 0
+    S = supp.cpu().numpy().astype(np.int64)
+    assert np.array_equal(S, np.flatnonzero(s_true))
+    s = s.cpu().numpy().astype(np.float64)
+    assert rel(s, s_true) <= SHAT_TOL
+    sS = ls.ls_cg(ref_op, S, y.astype(np.float64), tol=1e-12)
+    assert rel(s[S], sS) <= SHAT_TOL

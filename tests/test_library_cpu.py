@@ -46,7 +46,7 @@ def test_operator_draws_match_oracle(lib, N, M, seed):
     assert np.array_equal(d.astype(np.float64), rng.signs(N, seed))
 
 
-@pytest.mark.parametrize("N,M,code", [(24, 8, 2), (8, 4, 2), (1 << 23, 8, 2), (64, 0, 1), (64, 65, 1)])
+@pytest.mark.parametrize("N,M,code", [(24, 8, 2), (8, 4, 2), (1 << 24, 8, 2), (64, 0, 1), (64, 65, 1)])
 def test_invalid_sizes_rejected_without_gpu(lib, N, M, code):
     om = np.zeros(max(M, 1), dtype=np.int32)
     st = lib.cs_operator_draws(N, M, 1, om.ctypes.data_as(ctypes.c_void_p), None)
