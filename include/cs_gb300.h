@@ -22,7 +22,8 @@
  *   - Calls are asynchronous on the operator's stream (cs_op_set_stream); they return after
  *     the launch.  Argument errors are returned synchronously and nothing is launched.
  *   - N must be a power of two with 16 <= N <= 2^23 (else CS_ERR_UNSUPPORTED_N);
- *     1 <= M <= N; 0 <= K <= M; for SP also 2K <= M (else CS_ERR_INVALID_ARG).
+ *     1 <= M <= N; 0 <= K <= M; for SP also 2K <= M, for CoSaMP 3K <= M (else
+ *     CS_ERR_INVALID_ARG).
  *     N <= 2^18 runs on one thread-block cluster per signal; 2^18 < N <= 2^23 runs on a
  *     cooperative grid of up to 128 CTAs per signal that streams the transform through L2
  *     (such signals are processed one after another, also inside the batched calls).
@@ -59,7 +60,7 @@ extern "C" {
 
 typedef struct cs_op* cs_op_t;
 
-typedef enum { CS_OMP = 0, CS_SP = 1, CS_OMPR = 2 } cs_algo;
+typedef enum { CS_OMP = 0, CS_SP = 1, CS_OMPR = 2, CS_COSAMP = 3 } cs_algo;
 
 typedef enum {
   CS_OK = 0,
@@ -195,7 +196,9 @@ cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_
  * Sec. IV) with the CG weighted LS step (Eq. 8-10, the CG function of Algorithm 1).
  *   y           [M] device measurements
  *   K           sparsity (number of support entries returned)
- *   algo        CS_OMP, CS_SP or CS_OMPR
+ *   algo        CS_OMP, CS_SP, CS_OMPR, or CS_COSAMP (CoSaMP, Needell & Tropp 2009, which the paper
+ *               does not treat: T = S u {2K largest |A^T r|}, LS on T, keep the K largest of
+ *               that solution without a second solve, SP's stopping rule, <= 50 rounds)
  *   cg_tol      CG tolerance, relative or absolute (see conventions); cg_maxit >= 0 (0: at most
  *               |S| steps, Theorem 5)
  *   s_out       [N] device, dense estimate, zeros off the support

@@ -1,4 +1,4 @@
-"""Oracle greedy decoders OMP, SP and OMPR in FP64 (test infrastructure only).
+"""Oracle greedy decoders OMP, SP, OMPR and CoSaMP in FP64 (test infrastructure only).
 
 Each decoder alternates support detection (a correlation A^T r and a selection over |.|) with
 the least-squares sub-problem on the current support (Sec. II).  The oracle solves every LS
@@ -17,6 +17,11 @@ relative -- the value the paper's CG approximates (Theorems 1-2).
       OMPR(l), l > 1 replacements per round (the generalisation in the same paper): J = the l
       largest |z_j| outside S, S' = the K largest |z| over S u J; stop if S' = S, else
       S <- S', s <- LS(S), r <- y - A s.
+  * CoSaMP (Needell & Tropp 2009), a relative of SP that the paper does not treat.  Reading used
+      (with SP's stopping rule): S <- {}, s <- 0, r <- y; then repeat: T = S u top2K|A^T r|
+      (the 2K largest over all indices), b <- LS(T), S' <- topK_{j in T}|b_j|, s' <- b on S'
+      (no second LS), r' <- y - A s'; stop and keep (s, S) if S' = S or ||r'|| >= ||r||, else
+      accept.  At most L_max rounds.  Needs 3K <= M.
 
 Ties are broken towards the lowest index everywhere.  Every selection records its margin
 mu = (a_(1) - a_(2)) / a_(1) (argmax, argmin) or (a_(K) - a_(K+1)) / a_(K) (top-K); mu <= 1e-3
@@ -189,5 +194,36 @@ def ompr(op, y, K, ls_method="auto", T_max=100, l=1):
     return _finish(op, y, S, sS, it, trace)
 
 
+def cosamp(op, y, K, ls_method="auto", L_max=50):
+    """CoSaMP with the reading stated in the module docstring."""
+    y = np.asarray(y, dtype=np.float64)
+    trace = []
+    everything = np.ones(op.N, dtype=bool)
+    S = np.zeros(0, dtype=np.int64)
+    sS = np.zeros(0)
+    r = y.copy()
+    rn = float(np.linalg.norm(r))
+    it = 0
+    while it < L_max:
+        it += 1
+        Om, mu = topk_lowest(np.abs(op.apply_t(r)), everything, 2 * K)
+        trace.append(("topk", mu))
+        T = np.union1d(S, Om)
+        b = _ls.ls(op, T, y, ls_method)
+        ba = np.zeros(op.N)
+        ba[T] = np.abs(b)
+        inside = np.zeros(op.N, dtype=bool)
+        inside[T] = True
+        Sp, mu = topk_lowest(ba, inside, K)
+        trace.append(("topk", mu))
+        sp_ = b[np.searchsorted(T, Sp)]
+        rp = y - op.apply_support(Sp, sp_)
+        rpn = float(np.linalg.norm(rp))
+        if np.array_equal(Sp, S) or rpn >= rn:
+            break
+        S, sS, r, rn = Sp, sp_, rp, rpn
+    return _finish(op, y, S, sS, it, trace)
+
+
 def recover(op, y, K, algo, **kw):
-    return {"omp": omp, "sp": sp, "ompr": ompr}[algo](op, y, K, **kw)
+    return {"omp": omp, "sp": sp, "ompr": ompr, "cosamp": cosamp}[algo](op, y, K, **kw)

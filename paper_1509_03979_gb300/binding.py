@@ -13,8 +13,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcs_gb300.so")
 
-OMP, SP, OMPR = 0, 1, 2
-ALGOS = {"omp": OMP, "sp": SP, "ompr": OMPR}
+OMP, SP, OMPR, COSAMP = 0, 1, 2, 3
+ALGOS = {"omp": OMP, "sp": SP, "ompr": OMPR, "cosamp": COSAMP}
 
 
 class CsStats(ctypes.Structure):

@@ -198,7 +198,7 @@ cs_status check_cg(float cg_tol, int32_t cg_maxit) {
   return CS_OK;
 }
 
-constexpr int SP_ROUNDS = 50;     // SP outer-iteration cap
+constexpr int SP_ROUNDS = 50;     // SP / CoSaMP outer-iteration cap
 constexpr int STREAM_CLUSTER = 4;  // default CTAs per vector of the streamed batched operator (fastest untuned at 256 vectors)
 constexpr int OMPR_SWAPS = 100;   // OMPR replacement cap
 
@@ -544,7 +544,8 @@ cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, 
   if (op->dev.grid) return CS_OK;   // one geometry only
   cs_status st = check_cg(cg_tol, cg_maxit);
   if (st != CS_OK) return st;
-  if (K < 1 || K > op->M || (algo == CS_SP && 2 * (int64_t)K > op->M) || algo < 0 || algo > 2)
+  if (K < 1 || K > op->M || algo < CS_OMP || algo > CS_COSAMP || (algo == CS_SP && 2 * (int64_t)K > op->M) ||
+      (algo == CS_COSAMP && 3 * (int64_t)K > op->M))
     return fail(CS_ERR_INVALID_ARG, "K or algo out of range");
   // a K-sparse test signal: evenly spread positions, values alternating in sign and size
   std::vector<float> hs((size_t)op->N, 0.f);
@@ -715,9 +716,10 @@ cs_status cs_op_export_perm(cs_op_t op, int32_t* perm_N_host) {
 static cs_status check_recover(const cs_op* op, const float* y, int32_t K, int algo, float* s_out,
                                int32_t* support_out) {
   if (!op || !y || !s_out || (K > 0 && !support_out)) return fail(CS_ERR_INVALID_ARG, "null argument");
-  if (algo < CS_OMP || algo > CS_OMPR) return fail(CS_ERR_INVALID_ARG, "unknown algo");
+  if (algo < CS_OMP || algo > CS_COSAMP) return fail(CS_ERR_INVALID_ARG, "unknown algo");
   if (K < 0 || K > op->M) return fail(CS_ERR_INVALID_ARG, "K must satisfy 0 <= K <= M");
   if (algo == CS_SP && 2 * (int64_t)K > op->M) return fail(CS_ERR_INVALID_ARG, "SP needs 2K <= M");
+  if (algo == CS_COSAMP && 3 * (int64_t)K > op->M) return fail(CS_ERR_INVALID_ARG, "CoSaMP needs 3K <= M");
   return CS_OK;
 }
 
@@ -736,7 +738,7 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
   t.K = K;
   t.cg_tol = cg_tol;
   t.cg_maxit = cg_maxit;
-  t.outer_max = algo == CS_SP ? SP_ROUNDS : OMPR_SWAPS;
+  t.outer_max = (algo == CS_SP || algo == CS_COSAMP) ? SP_ROUNDS : OMPR_SWAPS;
   t.in = y;
   t.out = s_out;
   t.supp_out = support_out;
@@ -927,7 +929,7 @@ cs_status cs_recover_batched(int32_t B, const cs_op_t* ops, const float* const* 
     t.K = K[b];
     t.cg_tol = cg_tol;
     t.cg_maxit = cg_maxit;
-    t.outer_max = algo[b] == CS_SP ? SP_ROUNDS : OMPR_SWAPS;
+    t.outer_max = (algo[b] == CS_SP || algo[b] == CS_COSAMP) ? SP_ROUNDS : OMPR_SWAPS;
     t.in = y[b];
     t.out = s_out[b];
     t.supp_out = support_out[b];
@@ -1089,7 +1091,7 @@ extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, c
   t.K = K;
   t.cg_tol = cg_tol;
   t.cg_maxit = cg_maxit;
-  t.outer_max = algo == CS_SP ? SP_ROUNDS : OMPR_SWAPS;
+  t.outer_max = (algo == CS_SP || algo == CS_COSAMP) ? SP_ROUNDS : OMPR_SWAPS;
   t.in = y;
   t.out = s_out;
   t.supp_out = support_out;

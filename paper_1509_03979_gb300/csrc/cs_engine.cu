@@ -1797,6 +1797,48 @@ __device__ __noinline__ void run_sp(const Task& t) {
   write_recovery(t, acc, nloc, rn2, rounds);
 }
 
+// CoSaMP (Needell & Tropp 2009; not treated by the paper, built on the SP machinery):
+// S = {}, s = 0, r = y; each round T = S u {the 2K largest |A^T r| over all indices}, b = LS(T)
+// (warm-started from s), S' = the K largest |b| on T, s' = b on S' with no second solve,
+// r' = y - A s'; SP's stopping rule (S' = S or ||r'|| >= ||r||) keeps (S, s).
+__device__ __noinline__ void run_cosamp(const Task& t) {
+  init_correlation(t.in);
+  int acc = 0;
+  zero_mask(shp(C.sm.mask[0]));
+  float rn2 = resid_corr(acc, 0, t.in);              // ||y||^2; the A buffer holds A^T y
+  int rounds = 0;
+  while (rounds < t.outer_max) {
+    ++rounds;
+    const int wi = acc ^ 1;
+    uint32_t* mW = shp(C.sm.mask[wi]);
+    const uint32_t* mA = shp(C.sm.mask[acc]);
+    for (int w = threadIdx.x; w < C.nwords; w += NT) mW[w] = mA[w];
+    __syncthreads();
+    topk_corr(2 * t.K, nullptr, mW);                 // T = S u top-2K |A^T r|
+    int nW = build_list(mW);
+    {
+      const int* list = C.list;
+      float* xw = C.xd[wi];
+      const float* xa = C.xd[acc];
+      for (int i = threadIdx.x; i < nW; i += NT) {
+        const int sg = list[i];
+        xw[sg] = mask_bit(mA, sg) ? xa[sg] : 0.f;    // warm start: s on S, 0 on the new entries
+      }
+      __syncthreads();
+    }
+    cg_solve(wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);   // the A buffer holds A^T r
+    sp_prune(wi, nW, t.K, mW);                        // S'
+    nW = build_list(mW);
+    const float rn2_new = resid_corr(wi, nW, t.in);
+    const float diff = mask_diff(wi, acc);
+    if (diff == 0.f || rn2_new >= rn2) break;
+    acc = wi;
+    rn2 = rn2_new;
+  }
+  const int nloc = build_list(shp(C.sm.mask[acc]));
+  write_recovery(t, acc, nloc, rn2, rounds);
+}
+
 // OMPR replacement step: z = s + A^T r, j = argmax_{not in S} |z|, i = argmin_{in S} |z|
 // (lowest index on ties).  If |z_j| > |z_i| swaps them in the support (owner CTAs), zeroes both
 // slots of the warm-start vector and returns true; otherwise returns false.
@@ -2037,6 +2079,7 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     case MODE_RECOVER:
       if (t.algo == CS_OMP) run_omp(t);
       else if (t.algo == CS_SP) run_sp(t);
+      else if (t.algo == CS_COSAMP) run_cosamp(t);
       else run_ompr(t);
       break;
     case MODE_LS_SOLVE: run_ls_solve(t); break;

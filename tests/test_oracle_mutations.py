@@ -155,3 +155,13 @@ def test_wrong_sign_salt_is_caught_by_the_host_draw_cross_check(monkeypatch):
     d = np.zeros(N, dtype=np.int8)
     assert lib.cs_operator_draws(N, M, seed, None, d.ctypes.data_as(ctypes.c_void_p)) == 0
     assert not np.array_equal(d.astype(np.float64), rng.signs(N, seed))
+
+
+def test_cosamp_merging_k_instead_of_2k_is_caught(monkeypatch):
+    orig = greedy.topk_lowest
+
+    def half(a, allowed, K):
+        # the first selection of each CoSaMP round is the only one over all indices
+        return orig(a, allowed, K // 2 if allowed.all() and K % 2 == 0 else K)
+    monkeypatch.setattr(greedy, "topk_lowest", half)
+    caught(pins.test_cosamp_orthonormal_operator_and_2k_merge_finish_in_one_round)

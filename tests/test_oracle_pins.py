@@ -230,6 +230,50 @@ def test_sp_and_ompr_recover_truth_noiseless():
         assert np.abs(res["s"] - s).max() < 1e-9, algo
 
 
+def test_cosamp_recovers_truth_noiseless():
+    N, M, K = 2048, 512, 40                  # 3K <= M
+    op = oracle.Operator(N, M, 21)
+    s = synth.sparse_gaussian(N, K, 22)
+    res = greedy.cosamp(op, op.apply(s), K)
+    assert np.array_equal(res["S"], np.flatnonzero(s))
+    assert np.abs(res["s"] - s).max() < 1e-9
+
+
+def test_cosamp_orthonormal_operator_and_2k_merge_finish_in_one_round():
+    """Two closed-form cases of the first CoSaMP round on noiseless data: (1) M = N makes A
+    orthonormal, so A^T y = s and LS(T) = s on any T containing the support; (2) a signal whose
+    support lies within the 2K largest |A^T y| but not within the K largest: the 2K merge puts the
+    whole support into T, so LS(T) = s exactly after round 1 (a K merge could not).  Either way
+    round 1 returns s and round 2 sees the same support and stops."""
+    opf = oracle.Operator(256, 256, 62)
+    s = synth.sparse_gaussian(256, 12, 5)
+    res = greedy.cosamp(opf, opf.apply(s), 12)
+    assert res["iters"] == 2 and np.abs(res["s"] - s).max() < 1e-12
+    N, M, K = 1024, 256, 10
+    op = oracle.Operator(N, M, 61)
+    for seed in range(1000, 1200):
+        s = synth.sparse_gaussian(N, K, seed)
+        c = np.abs(op.apply_t(op.apply(s)))
+        order = np.lexsort((np.arange(N), -c))
+        sup = set(np.flatnonzero(s).tolist())
+        if sup <= set(order[:2 * K].tolist()) and not sup <= set(order[:K].tolist()):
+            break
+    else:
+        pytest.fail("no signal with its support between the K and 2K largest correlations")
+    res = greedy.cosamp(op, op.apply(s), K)
+    assert res["iters"] == 2 and np.abs(res["s"] - s).max() < 1e-12
+
+
+def test_cosamp_noisy_support_and_noise_level_error():
+    N, M, K = 1 << 13, 1 << 11, 160
+    p = synth.Problem(N, M, K, "cosamp", 31, 32, 33, 1e-3)
+    op = oracle.Operator(N, M, p.op_seed)
+    s = p.signal()
+    res = greedy.cosamp(op, p.add_noise(op.apply(s)), K)
+    assert np.array_equal(res["S"], np.flatnonzero(s))
+    assert np.linalg.norm(res["s"] - s) < 1e-2 * np.linalg.norm(s)
+
+
 def test_sp_noisy_support_and_noise_level_error():
     N, M, K = 1 << 13, 1 << 11, 160
     p = synth.Problem(N, M, K, "sp", 31, 32, 33, 1e-3)
