@@ -243,8 +243,8 @@ def test_cosamp_orthonormal_operator_and_2k_merge_finish_in_one_round():
     """Two closed-form cases of the first CoSaMP round on noiseless data: (1) M = N makes A
     orthonormal, so A^T y = s and LS(T) = s on any T containing the support; (2) a signal whose
     support lies within the 2K largest |A^T y| but not within the K largest: the 2K merge puts the
-    whole support into T, so LS(T) = s exactly after round 1 (a K merge could not).  Either way
-    round 1 returns s and round 2 sees the same support and stops."""
+    whole support into T, so LS(T) = s exactly after the first round (a K merge could not).
+    Either way the first round returns s and the second sees the same support and stops."""
     opf = oracle.Operator(256, 256, 62)
     s = synth.sparse_gaussian(256, 12, 5)
     res = greedy.cosamp(opf, opf.apply(s), 12)
