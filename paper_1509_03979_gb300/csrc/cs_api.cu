@@ -805,10 +805,21 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream, cs_
     if ((e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
     if ((e = cudaEventRecord(start, stream)) != cudaSuccess) return cuda_fail(e, "event record");
   }
+  // Launch the group holding the largest single task first: the makespan is set by the
+  // longest recoveries, and a group launched later finds the SMs taken by the earlier ones.
+  auto work = [](const Task& t) { return (int64_t)t.op.N * std::max(t.K, t.k_in); };
+  std::vector<std::pair<int, std::vector<Task>*>> order;
+  for (auto& kv : groups) order.emplace_back(kv.first, &kv.second);
+  std::stable_sort(order.begin(), order.end(), [&](const auto& a, const auto& b) {
+    int64_t wa = 0, wb = 0;
+    for (const Task& t : *a.second) wa = std::max(wa, work(t));
+    for (const Task& t : *b.second) wb = std::max(wb, work(t));
+    return wa > wb;
+  });
   cs_status st = CS_OK;
-  for (auto& kv : groups) {
-    const int P = kv.first;
-    std::vector<Task>& g = kv.second;
+  for (auto& og : order) {
+    const int P = og.first;
+    std::vector<Task>& g = *og.second;
     cudaStream_t s = stream;
     if (fork) {
       const size_t i = aux.size();
