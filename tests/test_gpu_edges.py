@@ -67,3 +67,34 @@ def test_non_default_stream_and_two_operators_concurrently(B):
         got = y.cpu().numpy()
         for b in (0, 17, 39):
             assert rel(got[b], ref.apply(x[b].astype(np.float64))) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("algo", ["omp", "sp", "ompr", "cosamp"])
+def test_full_sampling_m_equals_n(B, algo):
+    """M = N keeps every DCT row: A is orthonormal, so every decoder recovers a noiseless
+    K-sparse signal exactly."""
+    N = M = 1024
+    K = 50
+    ref = oracle.Operator(N, M, 31)
+    s = synth.sparse_gaussian(N, K, 32)
+    y = ref.apply(s).astype(np.float32)
+    op = B.Operator(N, M, 31)
+    s_hat, supp = op.recover(to_dev(y), K, algo, 1e-6, 100)
+    assert op.stats()["status"] == 0
+    assert np.array_equal(supp.cpu().numpy(), np.flatnonzero(s))
+    assert rel(s_hat.cpu().numpy(), s) <= SHAT_TOL
+
+
+def test_single_measurement(B):
+    """M = 1: one DCT row; A, A^T and a one-entry OMP recovery against the oracle."""
+    N, M = 64, 1
+    ref = oracle.Operator(N, M, 41)
+    op = B.Operator(N, M, 41)
+    x = np.random.default_rng(2).standard_normal(N).astype(np.float32)
+    u = np.array([0.75], dtype=np.float32)
+    assert rel(op.apply(to_dev(x)).cpu().numpy(), ref.apply(x.astype(np.float64))) <= APPLY_TOL
+    assert rel(op.apply_t(to_dev(u)).cpu().numpy(), ref.apply_t(u.astype(np.float64))) <= APPLY_TOL
+    s_hat, supp = op.recover(to_dev(u), 1, "omp", 1e-6, 10)
+    want = greedy.recover(ref, u.astype(np.float64), 1, "omp")
+    assert int(supp.cpu().numpy()[0]) == int(want["S"][0]) or want["near_ties"] > 0
+    assert rel(s_hat.cpu().numpy(), want["s"]) <= SHAT_TOL or want["near_ties"] > 0
