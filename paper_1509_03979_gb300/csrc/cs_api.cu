@@ -184,6 +184,7 @@ cs_status run_single(cs_op* op, const Task& t) {
   cudaError_t e;
   if (op->dev.grid) {
     if ((e = cudaMemsetAsync(op->dev.gerr, 0, sizeof(int), op->stream)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(op->dev.gbar, 0, 2 * sizeof(unsigned), op->stream)) != cudaSuccess) return cuda_fail(e, "memset");
     e = counted(launch_grid(L, op->dev.G, op->stream));
     if (e != cudaSuccess) return cuda_fail(e, "grid launch");
     return CS_OK;
@@ -900,6 +901,7 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream, cs_
     L.bits = t.grid_bits;
     L.bits_per_cluster = 0;
     if ((e = cudaMemsetAsync(t.op.gerr, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "memset");
+    if ((e = cudaMemsetAsync(t.op.gbar, 0, 2 * sizeof(unsigned), stream)) != cudaSuccess) return cuda_fail(e, "memset");
     if ((e = counted(launch_grid(L, t.op.G, stream))) != cudaSuccess) return cuda_fail(e, "grid launch");
   }
   return CS_OK;

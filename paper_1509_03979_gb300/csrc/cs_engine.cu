@@ -490,7 +490,10 @@ __device__ __forceinline__ T* cl_map(T* p, int rank) { return cg::this_cluster()
 // Bounded software barrier over the CTAs of a cooperative (grid) launch.  The launch guarantees
 // co-residency; a wait that still exceeds GRID_SPIN_LIMIT polls sets CS_ERR_TIMEOUT in the
 // op's status word and continues, and later barriers stop waiting once the status is set, so
-// the launch always ends.
+// the launch always ends.  One monotonic arrival count (zeroed before every launch): the b-th
+// barrier's arrivals are numbers (b-1) G + 1 .. b G, because no CTA passes barrier b before all
+// G have arrived at it, so a CTA waits until the count reaches the next multiple of G.  The last
+// arrival does no extra write (no reset, no generation word).
 constexpr unsigned long long GRID_SPIN_LIMIT = 1ull << 26;
 
 // Poll *word until it differs from `from`, at most `limit` times about 100 ns apart; false when
@@ -508,16 +511,18 @@ __device__ __noinline__ void grid_sync() {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned* count = C.op.gbar;
-    volatile unsigned* gen = C.op.gbar + 1;
     volatile int* err = C.op.gerr;
-    const unsigned g0 = *gen;
     __threadfence();
-    if (atomicAdd(count, 1u) == (unsigned)C.op.G - 1u) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(const_cast<unsigned*>(gen), 1u);
-    } else if (*err == 0) {
-      if (!spin_until_changed(gen, g0, GRID_SPIN_LIMIT)) atomicExch(const_cast<int*>(err), (int)CS_ERR_TIMEOUT);
+    const unsigned G = (unsigned)C.op.G;
+    const unsigned arrived = atomicAdd(count, 1u) + 1u;
+    const unsigned target = arrived + (G - arrived % G) % G;   // this barrier's last arrival
+    if (arrived != target && *err == 0) {
+      volatile unsigned* vc = count;
+      unsigned long long spins = 0;
+      while ((int)(*vc - target) < 0) {
+        if (++spins > GRID_SPIN_LIMIT) { atomicExch(const_cast<int*>(err), (int)CS_ERR_TIMEOUT); break; }
+        __nanosleep(100);
+      }
     }
     __threadfence();
   }

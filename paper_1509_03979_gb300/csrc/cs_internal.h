@@ -57,7 +57,7 @@ struct OpDev {
   int S1, S2, G, R, W, NB, bpc;  // row length, rows, CTAs, rows per CTA, block width, blocks, blocks per CTA
   float2* gY;                // [S2][S1] row-major intermediate between the two passes
   float2* gsig;              // [G][R][apad(S1)] signal-domain rows owned by each CTA
-  unsigned* gbar;            // [2] grid barrier: arrival count, generation
+  unsigned* gbar;            // [2] grid barrier: arrival count (zeroed before every launch), spare
   int* gerr;                 // device-side status of the last grid launch (0 = ok)
   float* gred;               // [4][G][4] reduction partials
   unsigned long long* gred64;   // [4][G][2]
