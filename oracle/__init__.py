@@ -8,9 +8,10 @@ library: it has its own random-number definition, its own DCT, and closed-form l
 Contents (each module cites the passage it follows):
   rng       -- SplitMix64 definitions of the operator's random draws (Omega, d)
   dct       -- orthonormal DCT-II/III: O(N^2) definition and Makhoul FFT form
-  operator  -- A = P_Omega C_N diag(d) (Eq. 7), A^T, closed-form columns
+  operator  -- A = P_Omega C_N R (Eq. 7), R signs or permutation, optional basis Psi (DCT, 2-D DCT),
+               A^T, closed-form columns
   ls        -- LS(S) by QR / Cholesky, and Algorithm 1's CG
-  greedy    -- OMP (Sec. II, Algorithm 1), SP and OMPR (readings stated in the module)
+  greedy    -- OMP (Sec. II, Algorithm 1), SP, OMPR, OMPR(l) and CoSaMP (readings stated in the module)
   adjoint   -- dL/dy of the fixed-support LS step
 
 Parity status: every function is pinned by the not-gpu tests in tests/test_oracle_*.py against

@@ -165,3 +165,11 @@ def test_cosamp_merging_k_instead_of_2k_is_caught(monkeypatch):
         return orig(a, allowed, K // 2 if allowed.all() and K % 2 == 0 else K)
     monkeypatch.setattr(greedy, "topk_lowest", half)
     caught(pins.test_cosamp_orthonormal_operator_and_2k_merge_finish_in_one_round)
+
+
+def test_psi_applied_as_its_transpose_is_caught(monkeypatch):
+    def bad(self, s):
+        s = np.asarray(s, dtype=np.float64)
+        return s if self.psi is None else self._c(s)      # C_N instead of C_N^T
+    monkeypatch.setattr(oracle.Operator, "_psi", bad)
+    caught(pins.test_psi_dct_with_no_randomiser_is_row_sampling)

@@ -393,3 +393,50 @@ def test_perm_operator_recovers_noiseless_sparse():
         out = greedy.recover(op, op.apply(s), K, algo)
         assert np.array_equal(out["S"], np.flatnonzero(s)), algo
         assert np.linalg.norm(out["s"] - s) <= 1e-9 * np.linalg.norm(s)
+
+
+
+# ------------------------------------------------------------ sparsifying basis Psi
+def test_psi_dct_with_no_randomiser_is_row_sampling():
+    """Closed form: with R = I and Psi = C_N^T, A = P_Omega C_N C_N^T = P_Omega, so A s = s[Omega]
+    and A^T u scatters u onto Omega."""
+    N, M = 256, 64
+    op = oracle.Operator(N, M, 3, randomizer="none", psi="dct")
+    s = np.random.default_rng(0).standard_normal(N)
+    assert np.abs(op.apply(s) - s[op.omega]).max() < 1e-12
+    u = np.random.default_rng(1).standard_normal(M)
+    want = np.zeros(N)
+    want[op.omega] = u
+    assert np.abs(op.apply_t(u) - want).max() < 1e-12
+
+
+def test_psi_dct2d_basis_is_scipy_idctn():
+    """The separable basis: Psi vec(S) = vec(idctn(S)) (scipy, orthonormal), row-major."""
+    import scipy.fft as sfft
+    op = oracle.Operator(512, 128, 4, psi=("dct2d", 16, 32))
+    S = np.random.default_rng(2).standard_normal((16, 32))
+    assert np.abs(op._psi(S.ravel()) - sfft.idctn(S, norm="ortho").ravel()).max() < 1e-12
+    assert np.abs(op._psi_t(S.ravel()) - sfft.dctn(S, norm="ortho").ravel()).max() < 1e-12
+
+
+@pytest.mark.parametrize("psi", ["dct", ("dct2d", 16, 32)])
+def test_psi_operator_keeps_orthonormal_rows_and_columns_agree(psi):
+    N, M = 512, 128
+    op = oracle.Operator(N, M, 5, psi=psi)
+    A = op.dense()
+    assert np.abs(A @ A.T - np.eye(M)).max() < 1e-12
+    x = np.random.default_rng(3).standard_normal(N)
+    assert np.abs(A @ x - op.apply(x)).max() < 1e-12
+    u = np.random.default_rng(4).standard_normal(M)
+    assert np.abs(A.T @ u - op.apply_t(u)).max() < 1e-12
+
+
+@pytest.mark.parametrize("algo", ["omp", "sp", "cosamp"])
+def test_psi_dct_sparse_signal_recovered_exactly(algo):
+    """An image sparse in the 2-D DCT basis (the coefficients are the unknown), noiseless."""
+    N, M, K = 1024, 256, 20
+    op = oracle.Operator(N, M, 6, psi=("dct2d", 32, 32))
+    s = synth.sparse_gaussian(N, K, 7)
+    res = greedy.recover(op, op.apply(s), K, algo)
+    assert np.array_equal(res["S"], np.flatnonzero(s))
+    assert np.abs(res["s"] - s).max() < 1e-9
