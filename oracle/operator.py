@@ -29,8 +29,8 @@ class Operator:
         """randomizer 'signs': R = diag(d) (A = P_Omega C_N diag(d)); 'perm': R the paper's random
         permutation, (R x)_n = x[perm[n]], no signs (A = P_Omega C_N Pi); 'none': R = I (for
         closed-form checks only).  psi: None, "dct" or ("dct2d", n1, n2), see the module text."""
-        if N < 2 or (N & (N - 1)):
-            raise ValueError("N must be a power of two >= 2")
+        if N < 2:
+            raise ValueError("N must be >= 2")   # any N: the FFT step and the draws take any length
         self.N, self.M, self.seed = int(N), int(M), int(seed)
         self.omega = _rng.omega(N, M, seed)
         self.fast = fast

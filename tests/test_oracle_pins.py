@@ -440,3 +440,29 @@ def test_psi_dct_sparse_signal_recovered_exactly(algo):
     res = greedy.recover(op, op.apply(s), K, algo)
     assert np.array_equal(res["S"], np.flatnonzero(s))
     assert np.abs(res["s"] - s).max() < 1e-9
+
+
+
+# -------------------------------------------------------------- any N (not only 2^k)
+@pytest.mark.parametrize("N", [1000, 999, 24])
+def test_operator_at_non_power_of_two_n(N):
+    """The oracle takes any N (the GPU path takes powers of two): A = P_Omega C_N diag(d) equals
+    scipy's orthonormal DCT-II on the rows Omega, and A A^T = I_M."""
+    import scipy.fft as sfft
+    M = N // 4
+    op = oracle.Operator(N, M, 9)
+    C = sfft.dct(np.eye(N), norm="ortho", axis=0)
+    A = C[op.omega] * op.d[None, :]
+    assert np.abs(op.dense() - A).max() < 1e-12
+    assert np.abs(A @ A.T - np.eye(M)).max() < 1e-12
+    x = np.random.default_rng(N).standard_normal(N)
+    assert np.abs(op.apply(x) - A @ x).max() < 1e-12
+
+
+def test_sp_exact_recovery_at_non_power_of_two_n():
+    N, M, K = 1000, 250, 12
+    op = oracle.Operator(N, M, 10)
+    s = synth.sparse_gaussian(N, K, 11)
+    res = greedy.sp(op, op.apply(s), K)
+    assert np.array_equal(res["S"], np.flatnonzero(s))
+    assert np.abs(res["s"] - s).max() < 1e-9
