@@ -2,8 +2,9 @@
 
 Each decoder alternates support detection (a correlation A^T r and a selection over |.|) with
 the least-squares sub-problem on the current support (Sec. II).  The oracle solves every LS
-sub-problem in closed form (QR of A_S) or, when A_S would not fit, by FP64 CG to 1e-13
-relative -- the value the paper's CG approximates (Theorems 1-2).
+sub-problem in closed form (QR of A_S, or for OMP's growing support the incrementally extended
+Cholesky factor of A_S^T A_S) or, when A_S would not fit, by FP64 CG to 1e-13 relative -- the
+value the paper's CG approximates (Theorems 1-2).
 
   * OMP: Sec. II steps 1-4 and the outer loop of Algorithm 1 (exactly K iterations).
   * SP: Subspace Pursuit (Dai & Milenkovic 2009), which the paper only cites.  Reading used:
@@ -24,8 +25,17 @@ relative -- the value the paper's CG approximates (Theorems 1-2).
       accept.  At most L_max rounds.  Needs 3K <= M.
 
 Ties are broken towards the lowest index everywhere.  Every selection records its margin
-mu = (a_(1) - a_(2)) / a_(1) (argmax, argmin) or (a_(K) - a_(K+1)) / a_(K) (top-K); mu <= 1e-3
-marks a near-tie, at which an FP32 decoder may legitimately choose differently.
+mu = (a_(1) - a_(2)) / a_(1) (argmax), (a_(2) - a_(1)) / a_(2) (argmin) or
+(a_(K) - a_(K+1)) / a_(K) (top-K), and every data-dependent stop test records one too:
+|a_j - a_i| / max(a_j, a_i) for OMPR's swap test, |rho - rho'| / max(rho, rho') for the residual
+test rho' >= rho of SP and CoSaMP, and 1 for a test decided by set equality (S' = S).
+mu <= 1e-3 marks a near-tie, at which an FP32 decoder may legitimately choose differently.
+
+Every selection and stop test goes through a `policy` object (default `OwnChoice`: take the
+oracle's own choice).  A replaying policy can substitute another decoder's recorded choices --
+the replay mode in which an FP32 trajectory that took a different member of a near-tied set is
+followed, so that the rest of its run can still be compared.  A policy changes only discrete
+choices, never the arithmetic.
 """
 import numpy as np
 
@@ -35,7 +45,8 @@ NEAR_TIE = 1e-3
 
 
 def _argmax_lowest(a, allowed):
-    """Index of the largest a over `allowed` (lowest index on ties) and the selection margin."""
+    """Index of the largest a over `allowed` (lowest index on ties) and the selection margin
+    (a_(1) - a_(2)) / a_(1), with a_(2) = 0 when only one index is allowed."""
     idx = np.flatnonzero(allowed)
     vals = a[idx]
     order = np.lexsort((idx, -vals))
@@ -46,6 +57,8 @@ def _argmax_lowest(a, allowed):
 
 
 def _argmin_lowest(a, allowed):
+    """Index of the smallest a over `allowed` (lowest index on ties) and the margin
+    (a_(2) - a_(1)) / a_(2); 1 when only one index is allowed."""
     idx = np.flatnonzero(allowed)
     vals = a[idx]
     order = np.lexsort((idx, vals))
@@ -57,7 +70,7 @@ def _argmin_lowest(a, allowed):
 
 def topk_lowest(a, allowed, K):
     """The K indices with the largest a among `allowed` (ties -> lowest index), sorted ascending,
-    and the boundary margin (a_(K) - a_(K+1)) / a_(K)."""
+    and the boundary margin (a_(K) - a_(K+1)) / a_(K), with a_(K+1) = 0 when all are taken."""
     idx = np.flatnonzero(allowed)
     vals = a[idx]
     order = np.lexsort((idx, -vals))
@@ -66,6 +79,40 @@ def topk_lowest(a, allowed, K):
     aK1 = float(vals[order[K]]) if len(order) > K else 0.0
     mu = (aK - aK1) / aK if aK > 0 else 0.0
     return np.sort(pick), mu
+
+
+def _test_margin(x, x_new):
+    """Margin of the comparison x_new >= x: |x - x_new| / max(x, x_new)."""
+    big = max(x, x_new)
+    return abs(x - x_new) / big if big > 0 else 0.0
+
+
+class OwnChoice:
+    """Selection policy that keeps the oracle's own choice at every step.
+
+    select(kind, own, mu, a, allowed): kind is "argmax", "argmin" or "topk"; own the oracle's
+    index (argmax / argmin) or sorted index array (top-K); a the values it selected on and
+    allowed the candidate mask.  decide(kind, own, mu): kind "swap" (own: True = swap) or
+    "stop" (own: True = stop).  Both return the choice the decoder continues with."""
+
+    def select(self, kind, own, mu, a, allowed):
+        return own
+
+    def decide(self, kind, own, mu):
+        return own
+
+
+class ForcedSequence(OwnChoice):
+    """OMP replay: the i-th argmax takes index seq[i]."""
+
+    def __init__(self, seq):
+        self.seq = list(seq)
+        self.i = 0
+
+    def select(self, kind, own, mu, a, allowed):
+        t = int(self.seq[self.i])
+        self.i += 1
+        return t
 
 
 class Result(dict):
@@ -83,10 +130,27 @@ def _finish(op, y, S, sS, iters, trace):
                   resid=float(np.linalg.norm(y - op.apply(s))))
 
 
-def omp(op, y, K, ls_method="auto", replay=None, on_step=None):
-    """OMP (Sec. II, Algorithm 1 outer loop).  `replay[i]` forces the i-th selected index.
-    `on_step(i, S, sS, r)` is called after each iteration (used by invariant tests)."""
+def _warm(S_new, S_old, s_old):
+    """Start for CG on S_new: the old solution where S_new keeps an old index, 0 elsewhere."""
+    x0 = np.zeros(len(S_new))
+    if len(S_old):
+        pos = np.searchsorted(S_old, S_new)
+        pos = np.minimum(pos, len(S_old) - 1)
+        hit = S_old[pos] == S_new
+        x0[hit] = s_old[pos[hit]]
+    return x0
+
+
+def omp(op, y, K, ls_method="auto", replay=None, on_step=None, policy=None):
+    """OMP (Sec. II, Algorithm 1 outer loop).  `replay[i]` forces the i-th selected index
+    (shorthand for policy=ForcedSequence(replay)).  `on_step(i, S, sS, r)` is called after each
+    iteration (used by invariant tests).  ls_method "auto" solves LS(S) by QR of A_S while
+    M |S| <= 4e6 and by the growing Cholesky factor beyond; "grow" forces the latter."""
     y = np.asarray(y, dtype=np.float64)
+    if policy is None:
+        policy = ForcedSequence(replay) if replay is not None else OwnChoice()
+    grow = ls_method == "grow" or (ls_method == "auto" and op.M * K > 4_000_000)
+    chol = _ls.GrowingCholesky(op, y, capacity=max(K, 1)) if grow else None
     r = y.copy()
     S = np.zeros(0, dtype=np.int64)
     sS = np.zeros(0)
@@ -96,24 +160,33 @@ def omp(op, y, K, ls_method="auto", replay=None, on_step=None):
         allowed = np.ones(op.N, dtype=bool)
         allowed[S] = False
         t, mu = _argmax_lowest(a, allowed)
-        if replay is not None:
-            t = int(replay[i])
+        t = int(policy.select("argmax", t, mu, a, allowed))
         trace.append(("argmax", mu))
-        S = np.sort(np.append(S, t))
-        sS = _ls.ls(op, S, y, ls_method)
+        if grow:
+            chol.add(t)
+            S, sS = chol.solve()
+        else:
+            S = np.sort(np.append(S, t))
+            sS = _ls.ls(op, S, y, ls_method)
         r = y - op.apply_support(S, sS)
         if on_step is not None:
             on_step(i, S, sS, r)
     return _finish(op, y, S, sS, K, trace)
 
 
-def sp(op, y, K, ls_method="auto", L_max=50):
+def _topk(policy, a, allowed, K, trace):
+    pick, mu = topk_lowest(a, allowed, K)
+    trace.append(("topk", mu))
+    return np.sort(np.asarray(policy.select("topk", pick, mu, a, allowed), dtype=np.int64))
+
+
+def sp(op, y, K, ls_method="auto", L_max=50, policy=None):
     """Subspace Pursuit with the stopping rule stated in the module docstring."""
     y = np.asarray(y, dtype=np.float64)
+    policy = policy or OwnChoice()
     trace = []
     everything = np.ones(op.N, dtype=bool)
-    S, mu = topk_lowest(np.abs(op.apply_t(y)), everything, K)
-    trace.append(("topk", mu))
+    S = _topk(policy, np.abs(op.apply_t(y)), everything, K, trace)
     sS = _ls.ls(op, S, y, ls_method)
     r = y - op.apply_support(S, sS)
     rn = float(np.linalg.norm(r))
@@ -122,33 +195,35 @@ def sp(op, y, K, ls_method="auto", L_max=50):
         it += 1
         allowed = np.ones(op.N, dtype=bool)
         allowed[S] = False
-        T, mu = topk_lowest(np.abs(op.apply_t(r)), allowed, K)
-        trace.append(("topk", mu))
-        St = np.sort(np.concatenate([S, T]))
-        u = _ls.ls(op, St, y, ls_method)
+        T = _topk(policy, np.abs(op.apply_t(r)), allowed, K, trace)
+        St = np.union1d(S, T)
+        u = _ls.ls(op, St, y, ls_method, x0=_warm(St, S, sS))
         ua = np.zeros(op.N)
         ua[St] = np.abs(u)
         inside = np.zeros(op.N, dtype=bool)
         inside[St] = True
-        Sp, mu = topk_lowest(ua, inside, K)
-        trace.append(("topk", mu))
-        sp_ = _ls.ls(op, Sp, y, ls_method)
+        Sp = _topk(policy, ua, inside, K, trace)
+        sp_ = _ls.ls(op, Sp, y, ls_method, x0=_warm(Sp, St, u))
         rp = y - op.apply_support(Sp, sp_)
         rpn = float(np.linalg.norm(rp))
-        if np.array_equal(Sp, S) or rpn >= rn:
+        same = np.array_equal(Sp, S)
+        mu = 1.0 if same else _test_margin(rn, rpn)
+        stop = bool(policy.decide("stop", same or rpn >= rn, mu))
+        trace.append(("stop", mu))
+        if stop:
             break
         S, sS, r, rn = Sp, sp_, rp, rpn
     return _finish(op, y, S, sS, it, trace)
 
 
-def ompr(op, y, K, ls_method="auto", T_max=100, l=1):
+def ompr(op, y, K, ls_method="auto", T_max=100, l=1, policy=None):
     """OMP with Replacement (eta = 1) as stated in the module docstring: one swap per iteration
     for l = 1; for l > 1 the OMPR(l) step of Jain, Tewari & Dhillon (2011): J = the l largest
     |z| outside S, S' = the K largest |z| over S u J, stop when S' = S."""
     y = np.asarray(y, dtype=np.float64)
+    policy = policy or OwnChoice()
     trace = []
-    S, mu = topk_lowest(np.abs(op.apply_t(y)), np.ones(op.N, dtype=bool), K)
-    trace.append(("topk", mu))
+    S = _topk(policy, np.abs(op.apply_t(y)), np.ones(op.N, dtype=bool), K, trace)
     sS = _ls.ls(op, S, y, ls_method)
     r = y - op.apply_support(S, sS)
     it = 0
@@ -159,17 +234,18 @@ def ompr(op, y, K, ls_method="auto", T_max=100, l=1):
             a = np.abs(z)
             inside = np.zeros(op.N, dtype=bool)
             inside[S] = True
-            J, mu_J = topk_lowest(a, ~inside, min(l, op.N - K))
+            J = _topk(policy, a, ~inside, min(l, op.N - K), trace)
             union = inside.copy()
             union[J] = True
-            S_new, mu_K = topk_lowest(a, union, K)
-            trace.append(("topl", mu_J))
-            trace.append(("topk", mu_K))
-            if np.array_equal(S_new, S):
+            S_new = _topk(policy, a, union, K, trace)
+            same = np.array_equal(S_new, S)
+            stop = bool(policy.decide("stop", same, 1.0))
+            trace.append(("stop", 1.0))
+            if stop:
                 break
             it += 1
+            sS = _ls.ls(op, S_new, y, ls_method, x0=_warm(S_new, S, sS))
             S = S_new
-            sS = _ls.ls(op, S, y, ls_method)
             r = y - op.apply_support(S, sS)
         return _finish(op, y, S, sS, it, trace)
     while it < T_max:
@@ -179,24 +255,27 @@ def ompr(op, y, K, ls_method="auto", T_max=100, l=1):
         inside = np.zeros(op.N, dtype=bool)
         inside[S] = True
         j, mu_j = _argmax_lowest(a, ~inside)
+        j = int(policy.select("argmax", j, mu_j, a, ~inside))
         i, mu_i = _argmin_lowest(a, inside)
-        big = max(a[j], a[i])
-        mu_swap = abs(a[j] - a[i]) / big if big > 0 else 0.0
+        i = int(policy.select("argmin", i, mu_i, a, inside))
+        mu_swap = _test_margin(a[i], a[j])
         trace.append(("argmax", mu_j))
         trace.append(("argmin", mu_i))
         trace.append(("swap", mu_swap))
-        if a[j] <= a[i]:
+        if not policy.decide("swap", bool(a[j] > a[i]), mu_swap):
             break
         it += 1
-        S = np.sort(np.append(S[S != i], j))
-        sS = _ls.ls(op, S, y, ls_method)
+        S_new = np.sort(np.append(S[S != i], j))
+        sS = _ls.ls(op, S_new, y, ls_method, x0=_warm(S_new, S, sS))
+        S = S_new
         r = y - op.apply_support(S, sS)
     return _finish(op, y, S, sS, it, trace)
 
 
-def cosamp(op, y, K, ls_method="auto", L_max=50):
+def cosamp(op, y, K, ls_method="auto", L_max=50, policy=None):
     """CoSaMP with the reading stated in the module docstring."""
     y = np.asarray(y, dtype=np.float64)
+    policy = policy or OwnChoice()
     trace = []
     everything = np.ones(op.N, dtype=bool)
     S = np.zeros(0, dtype=np.int64)
@@ -206,20 +285,22 @@ def cosamp(op, y, K, ls_method="auto", L_max=50):
     it = 0
     while it < L_max:
         it += 1
-        Om, mu = topk_lowest(np.abs(op.apply_t(r)), everything, 2 * K)
-        trace.append(("topk", mu))
+        Om = _topk(policy, np.abs(op.apply_t(r)), everything, 2 * K, trace)
         T = np.union1d(S, Om)
-        b = _ls.ls(op, T, y, ls_method)
+        b = _ls.ls(op, T, y, ls_method, x0=_warm(T, S, sS))
         ba = np.zeros(op.N)
         ba[T] = np.abs(b)
         inside = np.zeros(op.N, dtype=bool)
         inside[T] = True
-        Sp, mu = topk_lowest(ba, inside, K)
-        trace.append(("topk", mu))
+        Sp = _topk(policy, ba, inside, K, trace)
         sp_ = b[np.searchsorted(T, Sp)]
         rp = y - op.apply_support(Sp, sp_)
         rpn = float(np.linalg.norm(rp))
-        if np.array_equal(Sp, S) or rpn >= rn:
+        same = np.array_equal(Sp, S)
+        mu = 1.0 if same else _test_margin(rn, rpn)
+        stop = bool(policy.decide("stop", same or rpn >= rn, mu))
+        trace.append(("stop", mu))
+        if stop:
             break
         S, sS, r, rn = Sp, sp_, rp, rpn
     return _finish(op, y, S, sS, it, trace)

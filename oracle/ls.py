@@ -7,11 +7,15 @@ min ||y - A W_S theta|| (Eq. 9) and its normal-equation form min ||W^T A^T (y - 
 H = W^T A^T A W with b = W^T A^T y.  On the support, H restricted to S is A_S^T A_S (proof of
 Theorem 5), so CG is run on |S|-long vectors.
 
-Three solvers:
+Solvers:
   * `ls_qr`        -- Householder QR of the dense A_S (the closed form; ground truth).
   * `ls_cholesky`  -- Cholesky of the Gram matrix A_S^T A_S (independent cross-check).
   * `cg_alg1`      -- Algorithm 1's CG with the loop test read as "while ||r_j|| > tol"
                       (the printed "<=" cannot be meant: the loop would never start).
+  * `GrowingCholesky` -- the Cholesky route for a support that only grows (OMP): the Gram
+                      matrix gains one row and column per step, A_S^T a_t = (A^T A e_t)[S] is
+                      one A and one A^T application, and the factor is extended by one row
+                      instead of refactored.  Same closed form as `ls_cholesky`.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -61,16 +65,19 @@ def cg_alg1(op, S, b, tol, maxit, x0=None, absolute=False):
     return x, j, float(np.sqrt(rr))
 
 
-def ls_cg(op, S, y, tol=1e-13, maxit=None):
-    """LS(S) through CG in FP64 to a relative residual `tol` (O-fast tier for large |S|)."""
+def ls_cg(op, S, y, tol=1e-13, maxit=None, x0=None):
+    """LS(S) through CG in FP64 to a relative residual `tol` (O-fast tier for large |S|).
+    x0 (optional, |S| entries) is a starting point: the solution is unique, so a start only
+    changes the number of steps, not what the solver converges to."""
     S = np.asarray(S, dtype=np.int64)
     b = op.apply_t(y)[S]
-    x, _, _ = cg_alg1(op, S, b, tol, maxit if maxit is not None else 10 * len(S) + 50)
+    x, _, _ = cg_alg1(op, S, b, tol, maxit if maxit is not None else 10 * len(S) + 50, x0=x0)
     return x
 
 
-def ls(op, S, y, method="auto"):
-    """LS(S): closed form when A_S fits comfortably, else FP64 CG to 1e-13."""
+def ls(op, S, y, method="auto", x0=None):
+    """LS(S): closed form when A_S fits comfortably, else FP64 CG to 1e-13 (started at x0 when
+    given)."""
     S = np.asarray(S, dtype=np.int64)
     if len(S) == 0:
         return np.zeros(0)
@@ -80,4 +87,49 @@ def ls(op, S, y, method="auto"):
         return ls_qr(op.columns(S), np.asarray(y, dtype=np.float64))
     if method == "cholesky":
         return ls_cholesky(op.columns(S), np.asarray(y, dtype=np.float64))
-    return ls_cg(op, S, y)
+    return ls_cg(op, S, y, x0=x0)
+
+
+class GrowingCholesky:
+    """LS(S) for a support that gains one index per step (OMP), by the Cholesky factor
+    G = L L^T of the Gram matrix G = A_S^T A_S kept in the order the indices arrived.
+
+    Adding index t: g = A_S^T a_t = (A^T (A e_t))[S] (one application each of A and A^T),
+    gamma = ||a_t||^2 = (A^T A e_t)[t]; the new row of L is l = L^{-1} g and its diagonal
+    entry sqrt(gamma - l.l).  LS(S) is then L^{-T} L^{-1} (A^T y)[S] -- the closed form of
+    `ls_cholesky`, built incrementally."""
+
+    def __init__(self, op, y, capacity=16):
+        self.op = op
+        self.aty = op.apply_t(np.asarray(y, dtype=np.float64))
+        self.order = []
+        self.L = np.zeros((capacity, capacity))   # the leading k x k block is the factor
+
+    def add(self, t):
+        e = np.zeros(self.op.N)
+        e[t] = 1.0
+        col = self.op.apply_t(self.op.apply(e))
+        k = len(self.order)
+        if k == self.L.shape[0]:                  # grow the storage, keep the factor
+            big = np.zeros((2 * k, 2 * k))
+            big[:k, :k] = self.L
+            self.L = big
+        Lk = self.L[:k, :k]
+        g = col[np.asarray(self.order, dtype=np.int64)] if k else np.zeros(0)
+        l = sla.solve_triangular(Lk, g, lower=True) if k else np.zeros(0)
+        diag2 = col[t] - float(l @ l)
+        if not diag2 > 0.0:
+            raise np.linalg.LinAlgError("A_S lost full column rank")
+        self.L[k, :k] = l
+        self.L[k, k] = np.sqrt(diag2)
+        self.order.append(int(t))
+
+    def solve(self):
+        """(S sorted ascending, LS(S) in that order)."""
+        o = np.asarray(self.order, dtype=np.int64)
+        k = len(o)
+        Lk = self.L[:k, :k]
+        z = sla.solve_triangular(Lk, self.aty[o], lower=True)
+        x = sla.solve_triangular(Lk, z, lower=True, trans="T")
+        perm = np.argsort(o)
+        return o[perm], x[perm]

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from oracle import adjoint, dct, greedy, ls, rng
+from tests import test_oracle_margins as margins
 from tests import test_oracle_pins as pins
 
 
@@ -173,3 +174,48 @@ def test_psi_applied_as_its_transpose_is_caught(monkeypatch):
         return s if self.psi is None else self._c(s)      # C_N instead of C_N^T
     monkeypatch.setattr(oracle.Operator, "_psi", bad)
     caught(pins.test_psi_dct_with_no_randomiser_is_row_sampling)
+
+
+# ------------------------------------------------------------------------ margins
+def test_every_margin_forced_to_zero_is_caught(monkeypatch):
+    """Every selection reported as a near-tie would silently switch off every exact support
+    check on the GPU side."""
+    orig = greedy._finish
+    monkeypatch.setattr(greedy, "_finish",
+                        lambda op, y, S, sS, iters, trace: orig(op, y, S, sS, iters, [(k, 0.0) for k, _ in trace]))
+    caught(margins.test_finish_counts_near_ties_at_and_below_the_threshold)
+    caught(margins.test_omp_margins_are_the_gaps_of_the_sorted_signal_on_an_orthonormal_operator)
+
+
+def test_argmax_margin_over_the_runner_up_is_caught(monkeypatch):
+    def bad(a, allowed):
+        idx = np.flatnonzero(allowed)
+        vals = a[idx]
+        order = np.lexsort((idx, -vals))
+        a1 = float(vals[order[0]])
+        a2 = float(vals[order[1]]) if len(order) > 1 else 0.0
+        return int(idx[order[0]]), (a1 - a2) / a2 if a2 > 0 else 1.0    # wrong denominator
+    monkeypatch.setattr(greedy, "_argmax_lowest", bad)
+    caught(margins.test_argmax_margin_uses_the_winner_as_denominator)
+    caught(margins.test_omp_margins_are_the_gaps_of_the_sorted_signal_on_an_orthonormal_operator)
+
+
+def test_topk_margin_against_the_wrong_neighbour_is_caught(monkeypatch):
+    def bad(a, allowed, K):
+        idx = np.flatnonzero(allowed)
+        vals = a[idx]
+        order = np.lexsort((idx, -vals))
+        aK = float(vals[order[K - 1]])
+        aKm1 = float(vals[order[K - 2]]) if K >= 2 else aK             # a_(K-1) for a_(K+1)
+        return np.sort(idx[order[:K]]), (aKm1 - aK) / aKm1 if aKm1 > 0 else 0.0
+    monkeypatch.setattr(greedy, "topk_lowest", bad)
+    caught(margins.test_topk_boundary_and_margin, 2, [0, 1], 0.25)
+
+
+def test_ompr_that_never_stops_is_caught(monkeypatch):
+    class Always(greedy.OwnChoice):
+        def decide(self, kind, own, mu):
+            return True if kind == "swap" else own
+    orig = greedy.ompr
+    monkeypatch.setattr(greedy, "ompr", lambda *a, **k: orig(*a, **dict(k, policy=Always())))
+    caught(pins.test_ompr_final_state_has_no_improving_swap)

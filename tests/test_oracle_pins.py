@@ -296,7 +296,8 @@ def test_ompr_final_state_has_no_improving_swap():
     z[S] += res["s"][S]
     out = np.ones(N, bool)
     out[S] = False
-    assert np.abs(z[out]).max() <= np.abs(z[S]).min() or res["iters"] == 200
+    assert res["iters"] < 200                      # it stopped on its own rule, not on the cap
+    assert np.abs(z[out]).max() <= np.abs(z[S]).min()
 
 
 # ---------------------------------------------------------------- adjoint of the LS step
