@@ -76,9 +76,10 @@ typedef struct {
   int32_t outer_iters;     /* greedy iterations (OMP: K; SP/OMPR: rounds run) */
   int32_t cg_iters_total;  /* CG steps over all LS solves (each = one H d product) */
   int32_t cg_maxit_hits;   /* LS solves that stopped on cg_maxit */
-  int32_t near_ties;       /* reserved (not computed on the device): 0 */
+  int32_t near_ties;       /* recoveries: selections and stop tests whose margin is <= 1e-3
+                              (see cs_op_set_trace for the margins); LS calls: 0 */
   float final_resid;       /* ||y - A s_hat||_2 of the returned solution */
-  float min_margin;        /* reserved: -1 */
+  float min_margin;        /* recoveries: the smallest margin (1 if none); LS calls: -1 */
   int32_t status;          /* cs_status of the device-side run */
   int32_t transforms;      /* N-point DCT-II / DCT-III applications executed */
 } cs_stats;
@@ -207,6 +208,30 @@ cs_status cs_operator_draws(int64_t N, int64_t M, uint64_t seed, int32_t* omega_
  * without host synchronisation.  K = 0 writes zeros. */
 cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float cg_tol,
                      int32_t cg_maxit, float* s_out, int32_t* support_out);
+
+/* Selection trace of this op's later recoveries (cs_recover, cs_recover_batched,
+ * cs_recover_noalloc; no counterpart in the paper).  The decoders are heuristics whose discrete
+ * choices can legitimately differ from an FP64 run where two candidates are nearly tied; the
+ * trace records every choice and its margin, so a reference implementation can compare the
+ * choices one by one and follow this run's choice at a near-tie (replay).
+ *   trace_dev  [words] device int32, caller-owned; NULL disables the trace.  Every traced
+ *              recovery first zeroes it on the op's stream, then writes it.
+ *   words      capacity, 4 <= words < 2^31.
+ * Layout (32-bit words): header {words used, records, overflow (1 if a record did not fit: the
+ * records before it are complete, nothing after it is written), W = ceil(N / 32)}, then records
+ * {kind, payload words, margin (float bits), aux} + payload, in decoder order:
+ *   kind 1 argmax  (OMP selection; OMPR j = argmax outside S of |z|): aux = index
+ *   kind 2 argmin  (OMPR i = argmin inside S of |z|): aux = index
+ *   kind 3 top-K   (SP, CoSaMP, OMPR initial support and OMPR(l)): aux = K requested, payload =
+ *                  W words, the bitmask of the selected indices (bit n & 31 of word n >> 5)
+ *   kind 4 stop    (the SP / CoSaMP / OMPR(l) stopping test of a round): aux = 1 if it stopped
+ *   kind 5 swap    (the OMPR swap test |z_j| > |z_i|): aux = 1 if it swapped
+ * Margins (FP32, from the values the GPU selected on): argmax (a1 - a2) / a1 with a2 the
+ * runner-up; argmin (a2 - a1) / a2; top-K (a_K - a_{K+1}) / a_K with a_{K+1} the largest
+ * candidate not taken; a comparison x' >= x: |x - x'| / max(x, x'); a test decided by set
+ * equality: 1.  The same margins feed cs_stats.near_ties and min_margin, which every
+ * recovery that reports statistics computes (cs_recover; cs_recover_batched with stats_host). */
+cs_status cs_op_set_trace(cs_op_t op, int32_t* trace_dev, int64_t words);
 
 /* Same recovery as cs_recover, for callers that cannot allocate device memory when they
  * recover (a host framework that owns every device allocation, a loop that forbids allocation

@@ -90,15 +90,18 @@ def _test_margin(x, x_new):
 class OwnChoice:
     """Selection policy that keeps the oracle's own choice at every step.
 
-    select(kind, own, mu, a, allowed): kind is "argmax", "argmin" or "topk"; own the oracle's
-    index (argmax / argmin) or sorted index array (top-K); a the values it selected on and
-    allowed the candidate mask.  decide(kind, own, mu): kind "swap" (own: True = swap) or
-    "stop" (own: True = stop).  Both return the choice the decoder continues with."""
+    select(kind, own, mu, a, allowed, values): kind is "argmax", "argmin" or "topk"; own the
+    oracle's index (argmax / argmin) or sorted index array (top-K); a the values it selected on,
+    allowed the candidate mask, values what a holds: "corr" (correlations |A^T r|, or z outside
+    the support) or "coef" (least-squares coefficients, or z inside the support).
+    decide(kind, own, mu, vals): kind "swap" (own: True = swap; vals = (|z_i|, |z_j|, |S|)) or "stop"
+    (own: True = stop; vals = (||r||, ||r'||), None when set equality decided it).  Both return
+    the choice the decoder continues with."""
 
-    def select(self, kind, own, mu, a, allowed):
+    def select(self, kind, own, mu, a, allowed, values="corr"):
         return own
 
-    def decide(self, kind, own, mu):
+    def decide(self, kind, own, mu, vals=None):
         return own
 
 
@@ -109,7 +112,7 @@ class ForcedSequence(OwnChoice):
         self.seq = list(seq)
         self.i = 0
 
-    def select(self, kind, own, mu, a, allowed):
+    def select(self, kind, own, mu, a, allowed, values="corr"):
         t = int(self.seq[self.i])
         self.i += 1
         return t
@@ -144,12 +147,13 @@ def _warm(S_new, S_old, s_old):
 def omp(op, y, K, ls_method="auto", replay=None, on_step=None, policy=None):
     """OMP (Sec. II, Algorithm 1 outer loop).  `replay[i]` forces the i-th selected index
     (shorthand for policy=ForcedSequence(replay)).  `on_step(i, S, sS, r)` is called after each
-    iteration (used by invariant tests).  ls_method "auto" solves LS(S) by QR of A_S while
-    M |S| <= 4e6 and by the growing Cholesky factor beyond; "grow" forces the latter."""
+    iteration (used by invariant tests).  ls_method "auto" solves every LS(S) by QR of A_S
+    when M K <= 2.5e5 and otherwise by the growing Cholesky factor (a QR per step would cost
+    O(M K^3) over the run); "grow" forces the latter."""
     y = np.asarray(y, dtype=np.float64)
     if policy is None:
         policy = ForcedSequence(replay) if replay is not None else OwnChoice()
-    grow = ls_method == "grow" or (ls_method == "auto" and op.M * K > 4_000_000)
+    grow = ls_method == "grow" or (ls_method == "auto" and op.M * K > 250_000)
     chol = _ls.GrowingCholesky(op, y, capacity=max(K, 1)) if grow else None
     r = y.copy()
     S = np.zeros(0, dtype=np.int64)
@@ -160,7 +164,7 @@ def omp(op, y, K, ls_method="auto", replay=None, on_step=None, policy=None):
         allowed = np.ones(op.N, dtype=bool)
         allowed[S] = False
         t, mu = _argmax_lowest(a, allowed)
-        t = int(policy.select("argmax", t, mu, a, allowed))
+        t = int(policy.select("argmax", t, mu, a, allowed, "corr"))
         trace.append(("argmax", mu))
         if grow:
             chol.add(t)
@@ -174,10 +178,10 @@ def omp(op, y, K, ls_method="auto", replay=None, on_step=None, policy=None):
     return _finish(op, y, S, sS, K, trace)
 
 
-def _topk(policy, a, allowed, K, trace):
+def _topk(policy, a, allowed, K, trace, values):
     pick, mu = topk_lowest(a, allowed, K)
     trace.append(("topk", mu))
-    return np.sort(np.asarray(policy.select("topk", pick, mu, a, allowed), dtype=np.int64))
+    return np.sort(np.asarray(policy.select("topk", pick, mu, a, allowed, values), dtype=np.int64))
 
 
 def sp(op, y, K, ls_method="auto", L_max=50, policy=None):
@@ -186,7 +190,7 @@ def sp(op, y, K, ls_method="auto", L_max=50, policy=None):
     policy = policy or OwnChoice()
     trace = []
     everything = np.ones(op.N, dtype=bool)
-    S = _topk(policy, np.abs(op.apply_t(y)), everything, K, trace)
+    S = _topk(policy, np.abs(op.apply_t(y)), everything, K, trace, "corr")
     sS = _ls.ls(op, S, y, ls_method)
     r = y - op.apply_support(S, sS)
     rn = float(np.linalg.norm(r))
@@ -195,20 +199,20 @@ def sp(op, y, K, ls_method="auto", L_max=50, policy=None):
         it += 1
         allowed = np.ones(op.N, dtype=bool)
         allowed[S] = False
-        T = _topk(policy, np.abs(op.apply_t(r)), allowed, K, trace)
+        T = _topk(policy, np.abs(op.apply_t(r)), allowed, K, trace, "corr")
         St = np.union1d(S, T)
         u = _ls.ls(op, St, y, ls_method, x0=_warm(St, S, sS))
         ua = np.zeros(op.N)
         ua[St] = np.abs(u)
         inside = np.zeros(op.N, dtype=bool)
         inside[St] = True
-        Sp = _topk(policy, ua, inside, K, trace)
+        Sp = _topk(policy, ua, inside, K, trace, "coef")
         sp_ = _ls.ls(op, Sp, y, ls_method, x0=_warm(Sp, St, u))
         rp = y - op.apply_support(Sp, sp_)
         rpn = float(np.linalg.norm(rp))
         same = np.array_equal(Sp, S)
         mu = 1.0 if same else _test_margin(rn, rpn)
-        stop = bool(policy.decide("stop", same or rpn >= rn, mu))
+        stop = bool(policy.decide("stop", same or rpn >= rn, mu, None if same else (rn, rpn)))
         trace.append(("stop", mu))
         if stop:
             break
@@ -223,7 +227,7 @@ def ompr(op, y, K, ls_method="auto", T_max=100, l=1, policy=None):
     y = np.asarray(y, dtype=np.float64)
     policy = policy or OwnChoice()
     trace = []
-    S = _topk(policy, np.abs(op.apply_t(y)), np.ones(op.N, dtype=bool), K, trace)
+    S = _topk(policy, np.abs(op.apply_t(y)), np.ones(op.N, dtype=bool), K, trace, "corr")
     sS = _ls.ls(op, S, y, ls_method)
     r = y - op.apply_support(S, sS)
     it = 0
@@ -234,12 +238,12 @@ def ompr(op, y, K, ls_method="auto", T_max=100, l=1, policy=None):
             a = np.abs(z)
             inside = np.zeros(op.N, dtype=bool)
             inside[S] = True
-            J = _topk(policy, a, ~inside, min(l, op.N - K), trace)
+            J = _topk(policy, a, ~inside, min(l, op.N - K), trace, "corr")
             union = inside.copy()
             union[J] = True
-            S_new = _topk(policy, a, union, K, trace)
+            S_new = _topk(policy, a, union, K, trace, "coef")
             same = np.array_equal(S_new, S)
-            stop = bool(policy.decide("stop", same, 1.0))
+            stop = bool(policy.decide("stop", same, 1.0, None))
             trace.append(("stop", 1.0))
             if stop:
                 break
@@ -255,14 +259,14 @@ def ompr(op, y, K, ls_method="auto", T_max=100, l=1, policy=None):
         inside = np.zeros(op.N, dtype=bool)
         inside[S] = True
         j, mu_j = _argmax_lowest(a, ~inside)
-        j = int(policy.select("argmax", j, mu_j, a, ~inside))
+        j = int(policy.select("argmax", j, mu_j, a, ~inside, "corr"))
         i, mu_i = _argmin_lowest(a, inside)
-        i = int(policy.select("argmin", i, mu_i, a, inside))
+        i = int(policy.select("argmin", i, mu_i, a, inside, "coef"))
         mu_swap = _test_margin(a[i], a[j])
         trace.append(("argmax", mu_j))
         trace.append(("argmin", mu_i))
         trace.append(("swap", mu_swap))
-        if not policy.decide("swap", bool(a[j] > a[i]), mu_swap):
+        if not policy.decide("swap", bool(a[j] > a[i]), mu_swap, (float(a[i]), float(a[j]), len(S))):
             break
         it += 1
         S_new = np.sort(np.append(S[S != i], j))
@@ -285,20 +289,20 @@ def cosamp(op, y, K, ls_method="auto", L_max=50, policy=None):
     it = 0
     while it < L_max:
         it += 1
-        Om = _topk(policy, np.abs(op.apply_t(r)), everything, 2 * K, trace)
+        Om = _topk(policy, np.abs(op.apply_t(r)), everything, 2 * K, trace, "corr")
         T = np.union1d(S, Om)
         b = _ls.ls(op, T, y, ls_method, x0=_warm(T, S, sS))
         ba = np.zeros(op.N)
         ba[T] = np.abs(b)
         inside = np.zeros(op.N, dtype=bool)
         inside[T] = True
-        Sp = _topk(policy, ba, inside, K, trace)
+        Sp = _topk(policy, ba, inside, K, trace, "coef")
         sp_ = b[np.searchsorted(T, Sp)]
         rp = y - op.apply_support(Sp, sp_)
         rpn = float(np.linalg.norm(rp))
         same = np.array_equal(Sp, S)
         mu = 1.0 if same else _test_margin(rn, rpn)
-        stop = bool(policy.decide("stop", same or rpn >= rn, mu))
+        stop = bool(policy.decide("stop", same or rpn >= rn, mu, None if same else (rn, rpn)))
         trace.append(("stop", mu))
         if stop:
             break

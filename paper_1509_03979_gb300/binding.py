@@ -53,6 +53,7 @@ SIGNATURES = {
     "cs_operator_draws": (_I32, [_I64, _I64, _U64, _P, _P]),
     "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
     "cs_recover_noalloc": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
+    "cs_op_set_trace": (_I32, [_P, _P, _I64]),
     "cs_recover_batched": (_I32, [_I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P]),
     "cs_ls_solve": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
     "cs_ls_backward": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
@@ -183,6 +184,16 @@ class Operator:
     def concurrency(self):
         """Signals of this size the GPU runs at once (resident clusters)."""
         return int(lib().cs_op_concurrency(self._h))
+
+    def set_trace(self, trace):
+        """Record the selection trace of later recoveries into `trace` (a CUDA int32 tensor;
+        None disables it).  The tensor must outlive the recoveries that write it."""
+        if trace is None:
+            _check(lib().cs_op_set_trace(self._h, None, 0))
+            self._trace = None
+            return
+        _check(lib().cs_op_set_trace(self._h, _dev(trace, torch.int32, None, "trace"), int(trace.numel())))
+        self._trace = trace
 
     def set_ompr_replacements(self, l):
         """Replacements per OMPR round (1: single swap; l > 1: OMPR(l))."""

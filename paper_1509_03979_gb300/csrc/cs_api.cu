@@ -125,6 +125,8 @@ struct cs_op {
   int ompr_l = 1;               // OMPR replacements per round (cs_op_set_ompr_replacements)
   int tuned_nc[2] = {0, 0};     // per mode (A, A^T): 0 untuned, -1 cluster engine, else CTAs per vector
   std::vector<cudaStream_t> fork_streams;   // created on first use, kept until cs_op_destroy
+  uint32_t* trace = nullptr;    // selection trace of later recoveries (cs_op_set_trace), caller-owned
+  int64_t trace_words = 0;
 };
 
 namespace {
@@ -162,7 +164,15 @@ Task base_task(const cs_op* op, int mode) {
   t.stats = op->d_stats;
   t.grid_scratch = op->d_scratch;
   t.grid_bits = op->d_bits;
+  t.trace = op->trace;
+  t.trace_cap = (int)op->trace_words;
   return t;
+}
+
+// A recovery with a trace starts from a zeroed trace buffer (its top-K records are OR-ed in).
+cudaError_t clear_trace(const cs_op* op, cudaStream_t s) {
+  if (!op->trace) return cudaSuccess;
+  return cudaMemsetAsync(op->trace, 0, sizeof(uint32_t) * (size_t)op->trace_words, s);
 }
 
 Launch single_launch(const cs_op* op, const Task& t) {
@@ -743,7 +753,18 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
   t.in = y;
   t.out = s_out;
   t.supp_out = support_out;
+  cudaError_t e = clear_trace(op, op->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "trace memset");
   return run_single(op, t);
+}
+
+cs_status cs_op_set_trace(cs_op_t op, int32_t* trace_dev, int64_t words) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  if (trace_dev && (words < TRACE_HEADER || words > INT32_MAX))
+    return fail(CS_ERR_INVALID_ARG, "trace capacity must be in [4, 2^31 - 1] words");
+  op->trace = reinterpret_cast<uint32_t*>(trace_dev);
+  op->trace_words = trace_dev ? words : 0;
+  return CS_OK;
 }
 
 // Task tables reach the device inside kernel launch parameters, TASK_CHUNK tasks per launch of
@@ -751,7 +772,7 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
 // launch is issued, so the call can return (and its host vector die) at once, and a launch
 // captured into a CUDA graph carries its own tables rather than a pointer into freed host
 // memory.  The first chunk also zeroes the dynamic-claim counter that follows the table.
-constexpr int TASK_CHUNK = 120;
+constexpr int TASK_CHUNK = 112;
 struct TaskChunk {
   Task t[TASK_CHUNK];
   int n;                     // tasks in this chunk
@@ -937,6 +958,10 @@ cs_status cs_recover_batched(int32_t B, const cs_op_t* ops, const float* const* 
       cudaMemsetAsync(s_out[b], 0, sizeof(float) * (size_t)ops[b]->N, stream);
       continue;
     }
+    if ((e = clear_trace(ops[b], stream)) != cudaSuccess) {
+      cudaFreeAsync(d_stats, stream);
+      return cuda_fail(e, "trace memset");
+    }
     Task t = base_task(ops[b], MODE_RECOVER);
     t.algo = algo[b];
     t.K = K[b];
@@ -1109,6 +1134,10 @@ extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, c
   t.out = s_out;
   t.supp_out = support_out;
   t.stats = nullptr;   // the op's statistics buffer is left untouched
+  if (op->trace) {
+    const cudaError_t e = cudaMemsetAsync(op->trace, 0, sizeof(uint32_t) * (size_t)op->trace_words, op->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "trace memset");
+  }
   Launch L{};
   L.tasks = nullptr;
   L.single = t;

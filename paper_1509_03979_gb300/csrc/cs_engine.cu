@@ -480,6 +480,15 @@ struct Ctx {
   int cg_hits;
   int ntrans;         // N-point DCT applications (forward or inverse)
   int next_task;      // cluster rank 0: the task index it claimed for the cluster
+  // selection margins and the selection trace (recoveries that report statistics or a trace)
+  int want_margins;   // 1: compute the margin of every selection and stop test
+  int near_ties;      // selections and stop tests with margin <= NEAR_TIE (thread 0)
+  float min_margin;   // smallest margin seen (thread 0)
+  uint32_t* trace;    // selection trace, or null
+  int trace_cap;      // its capacity in words
+  int trace_off;      // word offset of the next record (advanced identically in every CTA)
+  int trace_recs;     // records written
+  int trace_over;     // 1 once a record did not fit: nothing more is written
 };
 __shared__ Ctx C;
 
@@ -684,6 +693,48 @@ __device__ __noinline__ void cluster_sum(float* v, int n) {
   }
   __syncthreads();
   for (int i = 0; i < n; ++i) v[i] = fscr[i];
+}
+
+// A cluster-wide sum split around a barrier that the caller already has: reduce_publish
+// stores this CTA's partial of v (fixed-order warp tree, then the warps in order) in the next
+// ring slot (grid launches: the partials array) and returns the slot; after a cluster (grid)
+// barrier that every CTA passes after publishing, reduce_collect adds the partials in rank order,
+// so every CTA holds the bit-identical total.  Saves the barrier of a separate cluster_sum.
+__device__ __noinline__ int reduce_publish(float v) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* wsum = shp(C.sm.wsum);
+  const float s = warp_sum(v);
+  if (lane == 0) wsum[warp] = s;
+  const int slot = C.ring_slot;                    // read by every thread before the barrier
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < NT / 32; ++w) t += wsum[w];
+    if (C.grid) C.op.gred[(size_t)slot * C.g.P * 4 + C.g.c * 4] = t;
+    else shp(C.sm.ring)[4 * slot] = t;
+    C.ring_slot = (slot + 1) & 3;                  // next reader is past the caller's barrier
+  }
+  return slot;
+}
+__device__ __noinline__ float reduce_collect(int slot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* fscr = shp(C.sm.fscr);
+  const int G = C.g.P;
+  if (warp == 0) {
+    float t = 0.f;
+    if (C.grid) {
+      const float* gred = C.op.gred + (size_t)slot * G * 4;
+      for (int r = lane; r < G; r += 32) t += __ldcg(gred + r * 4);
+    } else if (lane < G) {
+      t = *cl_map(shp(C.sm.ring) + 4 * slot, lane);
+    }
+    t = warp_sum(t);
+    if (lane == 0) fscr[4] = t;
+  }
+  __syncthreads();
+  const float r = fscr[4];
+  __syncthreads();
+  return r;
 }
 
 // Max of up to two 64-bit keys over the cluster.
@@ -990,7 +1041,8 @@ __device__ __forceinline__ void dct3_pair(const float* X, int k, bool self, cons
 }
 
 // Frequency stage: DCT-II post-processing of (Z_k, Z_{L-k}), the Omega step, and DCT-III
-// pre-processing back into the pair.  Returns this thread's MID_RESID sum of squares.
+// pre-processing back into the pair.  Returns this thread's sum of squares of the MID_RESID
+// residual y - A x on Omega, or for MID_MASK of the kept outputs A d on Omega.
 // MASK: the kind is MID_MASK (the H d step), compiled without the y-side state.
 template <bool MASK>
 __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, const int4* rank4, int kind,
@@ -1054,8 +1106,10 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
       if (MASK) {
         const uint32_t bits = fb[t];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
           if (!((bits >> i) & 1u)) X[i] = 0.f;
+          acc = fmaf(X[i], X[i], acc);             // ||P_Omega A W d||^2 = d^T H d (Parseval)
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -1305,14 +1359,16 @@ __device__ __noinline__ void grid_row_inverse(int lr) {
 }
 
 __device__ __noinline__ float transform_grid(int src, int nloc, const float* dense, const float* gin, int kind, bool inv,
-                                             const float* vin, float* vout) {
+                                             const float* vin, float* vout, bool fuse) {
   if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
   if (src != SRC_NONE)
     for (int lr = 0; lr < C.op.R; ++lr) grid_row_forward(lr, src, nloc, dense, gin);
   grid_sync();                                      // every row of pass 1 is stored
   float acc = 0.f;
   for (int j = 0; j < C.op.bpc; ++j) acc += grid_col_block(j, kind, src != SRC_NONE, inv, vin, vout);
-  grid_sync();                                      // every column block is stored
+  const int slot = fuse ? reduce_publish(acc) : 0;
+  grid_sync();                                      // every column block is stored (and every partial)
+  if (fuse) acc = reduce_collect(slot);
   if (inv)
     for (int lr = 0; lr < C.op.R; ++lr) grid_row_inverse(lr);
   return acc;
@@ -1326,10 +1382,13 @@ __device__ __noinline__ float transform_grid(int src, int nloc, const float* den
 //   kind  frequency step: MID_MASK keeps the Omega rows (H d), MID_RESID forms y - A x on Omega,
 //         MID_OUT writes y_M = A x, MID_IN reads u_M (A^T u)
 //   inv   run the DCT-III back to the signal domain (result left in the A buffer)
-// Returns this thread's sum of squares of the MID_RESID residual.
+//   fuse  reduce the frequency step's sum of squares over the cluster through the transform's
+//         own last barrier and return the total to every thread
+// Returns the frequency step's sum of squares (MID_RESID: ||y - A x||^2 on Omega; MID_MASK:
+// ||P_Omega A W d||^2 = d^T H d): this thread's share, or with `fuse` the cluster-wide total.
 __device__ __noinline__ float transform(int src, int nloc, const float* dense, const float* gin, int kind,
-                                        bool inv, const float* vin, float* vout) {
-  if (C.grid) return transform_grid(src, nloc, dense, gin, kind, inv, vin, vout);
+                                        bool inv, const float* vin, float* vout, bool fuse = false) {
+  if (C.grid) return transform_grid(src, nloc, dense, gin, kind, inv, vin, vout, fuse);
   // Each step is its own call and this function holds almost nothing live across them, so
   // every step gets the full register budget (ptxas allocates registers across calls).
   if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
@@ -1346,14 +1405,71 @@ __device__ __noinline__ float transform(int src, int nloc, const float* dense, c
     cl_sync();                                    // every CTA is done with its A before any push
   }
   const float acc = freq_half(kind, src != SRC_NONE, inv, vin, vout);
+  const int slot = fuse ? reduce_publish(acc) : 0;
   if (inv) {
     exchange_inv();
     cl_sync();                                    // every push into A has landed; B is scratch again
+    if (fuse) {
+      const float tot = reduce_collect(slot);     // the partials were published before the barrier
+      local_fft<1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
+      return tot;
+    }
     local_fft<1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
   } else {
     cl_sync();                                    // nobody still reads this CTA's A
+    if (fuse) return reduce_collect(slot);
   }
   return acc;
+}
+
+__device__ __forceinline__ float key_value(uint32_t k) { return k ? __uint_as_float(k - 1u) : 0.f; }
+
+// ---------------------------------------------------------------- margins and the trace
+// Selection margins as the oracle defines them: argmax (a_(1) - a_(2)) / a_(1), argmin
+// (a_(2) - a_(1)) / a_(2), top-K (a_(K) - a_(K+1)) / a_(K), a comparison test
+// |x - x'| / max(x, x'); a margin <= NEAR_TIE is a near-tie.
+constexpr float NEAR_TIE = 1e-3f;
+__device__ __forceinline__ float test_margin(float x, float xn) {
+  const float big = fmaxf(x, xn);
+  return big > 0.f ? fabsf(x - xn) / big : 0.f;
+}
+
+// Word offset of the next trace record if a record with `payload` words still fits, else -1.
+// Every thread calls it before the barriers of the selection it records.
+__device__ __forceinline__ int trace_reserve(int payload) {
+  if (!C.trace || C.trace_over) return -1;
+  const int off = C.trace_off;
+  return off + TRACE_HEADER + payload <= C.trace_cap ? off : -1;
+}
+
+// Account for one selection or stop test (every thread calls it, after the selection's last
+// barrier; cluster-uniform arguments): the near-tie statistics and, with a trace, the record's
+// header at `rec` (reserved by trace_reserve, whose payload the selection has written) -- or,
+// for rec == RESERVE_HERE, a record without payload reserved now.
+constexpr int RESERVE_HERE = -2;
+__device__ __noinline__ void note_selection(int kind, float mu, int aux, int rec, int payload) {
+  if (threadIdx.x == 0) {
+    if (mu <= NEAR_TIE) C.near_ties += 1;
+    C.min_margin = fminf(C.min_margin, mu);
+    if (C.trace && !C.trace_over) {
+      if (rec == RESERVE_HERE)
+        rec = C.trace_off + TRACE_HEADER + payload <= C.trace_cap ? C.trace_off : -1;
+      if (rec >= 0) {
+        if (C.g.c == 0) {
+          uint32_t* tr = C.trace + rec;
+          tr[0] = (uint32_t)kind;
+          tr[1] = (uint32_t)payload;
+          tr[2] = __float_as_uint(mu);
+          tr[3] = (uint32_t)aux;
+        }
+        C.trace_off = rec + TRACE_HEADER + payload;
+        C.trace_recs += 1;
+      } else {
+        C.trace_over = 1;
+      }
+    }
+  }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------------------ selection
@@ -1449,28 +1565,49 @@ __device__ void radix_select(int count, int K, KeyFn key, uint32_t* tau, int* ne
 
 // Select the K largest keys (ties towards the lowest signal index) and call mark(i) for each
 // selected index; the second radix pass on the index only runs when the threshold is tied.
+// With margins on, the boundary margin (a_(K) - a_(K+1)) / a_(K) is taken from the smallest
+// selected and the largest unselected nonzero key, and a trace record stores the selected
+// signal indices as an N-bit mask.
 template <class KeyFn, class IdxFn, class MarkFn>
 __device__ void select_topk(int count, int K, KeyFn key, IdxFn nidx, MarkFn mark) {
+  const bool margins = C.want_margins;
+  const int tpay = (C.g.N + 31) >> 5;
+  const int rec = margins ? trace_reserve(tpay) : -1;   // read before the barriers below
+  uint32_t* tbits = rec >= 0 ? C.trace + rec + TRACE_HEADER : nullptr;
   uint32_t tau;
   int need, eq;
   radix_select(count, K, key, &tau, &need, &eq);
-  if (need > 0 && eq > need) {
-    const uint32_t N = (uint32_t)C.g.N;
-    uint32_t tau2;
+  const bool tied = need > 0 && eq > need;
+  const uint32_t N = (uint32_t)C.g.N;
+  uint32_t tau2 = 0u;
+  if (tied) {
     int need2, eq2;
     radix_select(
         count, need, [&](int i) { return key(i) == tau ? N - (uint32_t)nidx(i) : 0u; }, &tau2, &need2, &eq2);
-    for (int i = threadIdx.x; i < count; i += NT) {
-      const uint32_t kk = key(i);
-      if (kk > tau || (kk == tau && N - (uint32_t)nidx(i) >= tau2)) mark(i);
-    }
-  } else {
-    for (int i = threadIdx.x; i < count; i += NT) {
-      const uint32_t kk = key(i);
-      if (kk != 0u && kk >= tau) mark(i);
+  }
+  uint32_t minsel = 0xffffffffu, maxun = 0u;
+  for (int i = threadIdx.x; i < count; i += NT) {
+    const uint32_t kk = key(i);
+    const bool sel = tied ? (kk > tau || (kk == tau && N - (uint32_t)nidx(i) >= tau2)) : (kk != 0u && kk >= tau);
+    if (sel) {
+      mark(i);
+      if (tbits) {
+        const int n = nidx(i);
+        atomicOr(tbits + (n >> 5), 1u << (n & 31));
+      }
+      minsel = min(minsel, kk);
+    } else if (kk != 0u) {
+      maxun = max(maxun, kk);
     }
   }
   __syncthreads();
+  if (margins) {
+    unsigned long long v[2] = {maxun, 0xffffffffull - minsel};
+    cluster_max64(v, 2);
+    const float aK = v[1] ? key_value((uint32_t)(0xffffffffull - v[1])) : 0.f;
+    const float aK1 = key_value((uint32_t)v[0]);
+    note_selection(TR_TOPK, aK > 0.f ? (aK - aK1) / aK : 0.f, K, rec, tpay);
+  }
 }
 
 __device__ __forceinline__ uint32_t abs_key(float v) { return (__float_as_uint(v) & 0x7fffffffu) + 1u; }
@@ -1521,7 +1658,9 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
   if (maxit == 0) maxit = (int)v[2];
   int it = 0;
   while (it < maxit && rr > stop2) {
-    transform(SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr);
+    // H d, with d^T H d = ||P_Omega A W d||^2 summed in the frequency step and reduced through
+    // the transform's last cluster barrier (one reduction per step fewer than a dot with H d)
+    const float pq = transform(SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr, true);
     // pointers are re-read from the context after the call (nothing held live across it)
     const SigView Ax = sigview();
     const uint32_t* sw = shp(C.sm.signw);
@@ -1530,13 +1669,8 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
     float* pr = C.cgr;
     float* pp = C.cgp;
     float* pq_ = C.cgq;
-    float pq = 0.f;
-    for (int i = threadIdx.x; i < nloc; i += NT) {
-      const float q = corr_at(Ax, sw, li[i]);
-      pq_[i] = q;
-      pq = fmaf(pp[i], q, pq);
-    }
-    cluster_sum(&pq, 1);
+    for (int i = threadIdx.x; i < nloc; i += NT) pq_[i] = corr_at(Ax, sw, li[i]);
+    __syncthreads();
     if (!(pq > 0.f)) break;   // H d = 0 in FP32: the residual is at rounding level (uniform: pq is cluster-wide)
     const float alpha = rr / pq;
     float rn = 0.f;
@@ -1567,9 +1701,7 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
 
 // Residual-correlation: A buffer <- C^T P^T (y - A xd) (unsigned slots), returns ||y - A xd||^2.
 __device__ __noinline__ float resid_corr(int wi, int nloc, const float* y) {
-  float v = transform(SRC_DENSE_SLOTS, nloc, C.xd[wi], nullptr, MID_RESID, true, y, nullptr);
-  cluster_sum(&v, 1);
-  return v;
+  return transform(SRC_DENSE_SLOTS, nloc, C.xd[wi], nullptr, MID_RESID, true, y, nullptr, true);
 }
 
 // ------------------------------------------------------------------------ task execution
@@ -1652,23 +1784,29 @@ __device__ __noinline__ void write_recovery(const Task& t, int wi, int nloc, flo
     st.outer_iters = outer;
     st.cg_iters_total = C.cg_total;
     st.cg_maxit_hits = C.cg_hits;
-    st.near_ties = 0;
+    st.near_ties = C.near_ties;
     st.final_resid = sqrtf(rn2);
-    st.min_margin = -1.f;
+    st.min_margin = C.min_margin;
     st.status = C.grid ? *(volatile int*)C.op.gerr : CS_OK;
     st.transforms = C.ntrans;
     *t.stats = st;
+  }
+  if (g.c == 0 && threadIdx.x == 0 && C.trace) {
+    C.trace[0] = (uint32_t)C.trace_off;
+    C.trace[1] = (uint32_t)C.trace_recs;
+    C.trace[2] = (uint32_t)C.trace_over;
+    C.trace[3] = (uint32_t)((N + 31) >> 5);
   }
 }
 
 // A^T y into cy (dense by slot, signed) and the A buffer; returns ||y||^2.
 __device__ __noinline__ float init_correlation(const float* y) {
-  float v = transform(SRC_NONE, 0, nullptr, nullptr, MID_RESID, true, y, nullptr);
+  const float v = transform(SRC_NONE, 0, nullptr, nullptr, MID_RESID, true, y, nullptr, true);
   const SigView A = sigview();
   const uint32_t* signw = shp(C.sm.signw);
   float* cy = C.cy;
   for (int sg = threadIdx.x; sg < 2 * C.g.F; sg += NT) cy[sg] = corr_at(A, signw, sg);
-  cluster_sum(&v, 1);
+  __syncthreads();
   return v;
 }
 
@@ -1707,6 +1845,19 @@ __device__ __noinline__ int omp_select(uint32_t* mA) {
   cluster_max64(&key, 1);
   if (key == 0ull) return -1;   // no candidate left (uniform: key is cluster-reduced)
   const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
+  if (C.want_margins) {
+    // runner-up over the same candidates: margin (a_(1) - a_(2)) / a_(1)
+    unsigned long long k2 = 0;
+    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+      if (mask_bit(mA, sg)) continue;
+      const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) |
+                                    (0xffffffffu - (uint32_t)sig_of_slot(g, sg));
+      if (kk != key && kk > k2) k2 = kk;
+    }
+    cluster_max64(&k2, 1);
+    const float a1 = key_value((uint32_t)(key >> 32)), a2 = key_value((uint32_t)(k2 >> 32));
+    note_selection(TR_ARGMAX, a1 > 0.f ? (a1 - a2) / a1 : 0.f, n, RESERVE_HERE, 0);
+  }
   int owner, sg;
   slot_of_sig(C.g, n, owner, sg);
   if (owner == C.g.c && threadIdx.x == 0) {
@@ -1793,7 +1944,10 @@ __device__ __noinline__ void run_sp(const Task& t) {
     cg_solve(wi, nW, true, R0_FROM_A, t.cg_tol, t.cg_maxit);
     const float rn2_new = resid_corr(wi, nW, t.in);
     const float diff = mask_diff(wi, acc);
-    if (diff == 0.f || rn2_new >= rn2) break;
+    const bool stop = diff == 0.f || rn2_new >= rn2;
+    if (C.want_margins)
+      note_selection(TR_STOP, diff == 0.f ? 1.f : test_margin(sqrtf(rn2), sqrtf(rn2_new)), stop ? 1 : 0, RESERVE_HERE, 0);
+    if (stop) break;
     acc = wi;
     rn2 = rn2_new;
   }
@@ -1836,7 +1990,10 @@ __device__ __noinline__ void run_cosamp(const Task& t) {
     nW = build_list(mW);
     const float rn2_new = resid_corr(wi, nW, t.in);
     const float diff = mask_diff(wi, acc);
-    if (diff == 0.f || rn2_new >= rn2) break;
+    const bool stop = diff == 0.f || rn2_new >= rn2;
+    if (C.want_margins)
+      note_selection(TR_STOP, diff == 0.f ? 1.f : test_margin(sqrtf(rn2), sqrtf(rn2_new)), stop ? 1 : 0, RESERVE_HERE, 0);
+    if (stop) break;
     acc = wi;
     rn2 = rn2_new;
   }
@@ -1869,9 +2026,37 @@ __device__ __noinline__ bool ompr_swap() {
   cluster_max64(key, 2);
   const uint32_t zj = (uint32_t)(key[0] >> 32) - 1u;                  // |z_j| bits
   const uint32_t zi = 0xffffffffu - (uint32_t)(key[1] >> 32);         // |z_i| bits
-  if (key[0] == 0ull || key[1] == 0ull || zj <= zi) return false;     // no improving swap
+  const bool swap = !(key[0] == 0ull || key[1] == 0ull || zj <= zi);
   const int nj = (int)(0xffffffffu - (uint32_t)(key[0] & 0xffffffffu));
   const int ni = (int)(0xffffffffu - (uint32_t)(key[1] & 0xffffffffu));
+  if (C.want_margins && key[0] != 0ull && key[1] != 0ull) {
+    // runners-up: the second largest |z| outside S and the second smallest inside
+    unsigned long long k2[2] = {0ull, 0ull};
+    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+      const uint32_t lo = 0xffffffffu - (uint32_t)sig_of_slot(g, sg);
+      if (mask_bit(mA, sg)) {
+        const float z = xd[sg] + corr_at(A, signw, sg);
+        const unsigned long long kk =
+            ((unsigned long long)(0xffffffffu - (__float_as_uint(z) & 0x7fffffffu)) << 32) | lo;
+        if (kk != key[1] && kk > k2[1]) k2[1] = kk;
+      } else {
+        const unsigned long long kk = ((unsigned long long)abs_key(corr_at(A, signw, sg)) << 32) | lo;
+        if (kk != key[0] && kk > k2[0]) k2[0] = kk;
+      }
+    }
+    cluster_max64(k2, 2);
+    const float aj = __uint_as_float(zj), ai = __uint_as_float(zi);
+    const float aj2 = key_value((uint32_t)(k2[0] >> 32));
+    float mu_i = 1.f;   // a single support entry has nothing to tie with
+    if (k2[1] != 0ull) {
+      const float ai2 = __uint_as_float(0xffffffffu - (uint32_t)(k2[1] >> 32));
+      mu_i = ai2 > 0.f ? (ai2 - ai) / ai2 : (ai2 > ai ? 1.f : 0.f);
+    }
+    note_selection(TR_ARGMAX, aj > 0.f ? (aj - aj2) / aj : 0.f, nj, RESERVE_HERE, 0);
+    note_selection(TR_ARGMIN, mu_i, ni, RESERVE_HERE, 0);
+    note_selection(TR_SWAP, test_margin(ai, aj), swap ? 1 : 0, RESERVE_HERE, 0);
+  }
+  if (!swap) return false;                                             // no improving swap
   int oj, sj, oi, si;
   slot_of_sig(g, nj, oj, sj);
   slot_of_sig(g, ni, oi, si);
@@ -1907,7 +2092,9 @@ __device__ __noinline__ bool ompr_replace(int l, int K) {
   }
   __syncthreads();
   sp_prune(1, nW, K, mW);                            // S' = topK |z| over S u J
-  if (mask_diff(1, 0) == 0.f) return false;
+  const bool same = mask_diff(1, 0) == 0.f;
+  if (C.want_margins) note_selection(TR_STOP, 1.f, same ? 1 : 0, RESERVE_HERE, 0);   // decided by set equality
+  if (same) return false;
   {
     float* xa = C.xd[0];
     for (int w = threadIdx.x; w < C.nwords; w += NT) {
@@ -2037,6 +2224,15 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     C.omask = op.omask; C.orank = op.orank;
     C.cg_total = 0; C.cg_hits = 0; C.ntrans = 0;
     C.cg_abs = tp->cg_abs;
+    const bool rec = tp->mode == MODE_RECOVER;
+    C.want_margins = rec && (tp->stats != nullptr || tp->trace != nullptr);
+    C.near_ties = 0;
+    C.min_margin = 1.f;
+    C.trace = rec && tp->trace_cap >= TRACE_HEADER ? tp->trace : nullptr;
+    C.trace_cap = tp->trace_cap;
+    C.trace_off = TRACE_HEADER;
+    C.trace_recs = 0;
+    C.trace_over = 0;
     const size_t a = 2 * (size_t)F_alloc;
     C.list = C.glist;
     C.cgx = C.gcg; C.cgr = C.gcg + a; C.cgp = C.gcg + 2 * a; C.cgq = C.gcg + 3 * a;

@@ -82,7 +82,17 @@ struct Task {
   cs_stats* stats;           // device, may be null
   float* grid_scratch;       // streamed geometry: the op's own scratch and output bitmask
   uint32_t* grid_bits;
+  uint32_t* trace;           // selection trace (recover), zeroed by the host, or null
+  int trace_cap;             // its capacity in 32-bit words
 };
+
+// Selection trace written by a recovery (cs_op_set_trace): a header of TRACE_HEADER words
+// {words used, records, overflow flag, N/32 rounded up}, then records of TRACE_HEADER words
+// {kind, payload words, margin (float bits), aux} followed by the payload.  Kinds follow the
+// decoders' selections and stop tests; a top-K record's payload is the N-bit mask of the
+// selected signal indices, the other kinds carry the index or the decision in aux.
+enum TraceKind : int { TR_ARGMAX = 1, TR_ARGMIN = 2, TR_TOPK = 3, TR_STOP = 4, TR_SWAP = 5 };
+constexpr int TRACE_HEADER = 4;
 
 // Kernel launch parameters (passed by value).
 struct Launch {

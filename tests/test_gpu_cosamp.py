@@ -7,7 +7,7 @@ import pytest
 import oracle
 from oracle import greedy
 from paper_1509_03979_gb300 import synth
-from tests.gpu_common import SHAT_TOL, measurements, rel, to_dev
+from tests.gpu_common import SHAT_TOL, measurements, rel, replay_parity, to_dev
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -20,17 +20,6 @@ def B():
     return binding
 
 
-def _check(op, ref_op, y, K, s_hat, supp):
-    want = greedy.cosamp(ref_op, y.astype(np.float64), K)
-    assert op.stats()["status"] == 0
-    supp = supp.cpu().numpy()
-    assert np.all(np.diff(supp) > 0)
-    if want["near_ties"] == 0:
-        assert np.array_equal(supp, want["S"])
-    assert rel(s_hat.cpu().numpy(), want["s"]) <= SHAT_TOL
-    return want
-
-
 @pytest.mark.parametrize("N,M,K,noise", [
     (256, 96, 8, 0.0), (4096, 1024, 60, 1e-3), (1 << 15, 1 << 13, 400, 1e-3), (1 << 16, 1 << 14, 700, 0.0),
     (1 << 18, 1 << 16, 2000, 1e-3), (1 << 19, 1 << 17, 600, 1e-3)])
@@ -39,11 +28,11 @@ def test_cosamp_matches_oracle(B, N, M, K, noise):
     ref_op = oracle.Operator(N, M, p.op_seed)
     _, y = measurements(p, ref_op)
     op = B.Operator(N, M, p.op_seed)
-    s_hat, supp = op.recover(to_dev(y), K, "cosamp", 1e-6, 200)
-    _check(op, ref_op, y, K, s_hat, supp)
+    rep, s_hat, supp, st, want = replay_parity(op, ref_op, y, K, "cosamp", 1e-6, 200)
+    assert np.all(np.diff(supp) > 0)
     if N <= 1 << 16:
         s2, k2 = op.recover_noalloc(to_dev(y), K, "cosamp", 1e-6, 200)
-        assert rel(s2.cpu().numpy(), s_hat.cpu().numpy()) <= SHAT_TOL
+        assert rel(s2.cpu().numpy(), want["s"]) <= SHAT_TOL
 
 
 def test_cosamp_in_a_mixed_batch(B):
@@ -70,9 +59,8 @@ def test_cosamp_with_the_permutation_randomiser(B):
     s = synth.sparse_gaussian(N, K, 0x7712)
     y = ref_op.apply(s).astype(np.float32)
     op = B.Operator(N, M, 0x7711, randomizer="perm")
-    s_hat, supp = op.recover(to_dev(y), K, "cosamp", 1e-6, 200)
-    _check(op, ref_op, y, K, s_hat, supp)
-    assert rel(s_hat.cpu().numpy(), s) <= SHAT_TOL
+    rep, s_hat, supp, st, want = replay_parity(op, ref_op, y, K, "cosamp", 1e-6, 200)
+    assert rel(s_hat, s) <= SHAT_TOL
 
 
 def test_cosamp_needs_3k_le_m(B):

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from oracle import greedy, ls
 from paper_1509_03979_gb300 import synth
-from tests.gpu_common import APPLY_TOL, SHAT_TOL, measurements, rel, to_dev
+from tests.gpu_common import APPLY_TOL, SHAT_TOL, measurements, rel, replay_parity, to_dev
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -94,7 +94,4 @@ def test_single_measurement(B):
     u = np.array([0.75], dtype=np.float32)
     assert rel(op.apply(to_dev(x)).cpu().numpy(), ref.apply(x.astype(np.float64))) <= APPLY_TOL
     assert rel(op.apply_t(to_dev(u)).cpu().numpy(), ref.apply_t(u.astype(np.float64))) <= APPLY_TOL
-    s_hat, supp = op.recover(to_dev(u), 1, "omp", 1e-6, 10)
-    want = greedy.recover(ref, u.astype(np.float64), 1, "omp")
-    assert int(supp.cpu().numpy()[0]) == int(want["S"][0]) or want["near_ties"] > 0
-    assert rel(s_hat.cpu().numpy(), want["s"]) <= SHAT_TOL or want["near_ties"] > 0
+    replay_parity(op, ref, u, 1, "omp", 1e-6, 10)

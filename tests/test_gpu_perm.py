@@ -6,7 +6,7 @@ import pytest
 import oracle
 from oracle import adjoint, greedy, ls
 from paper_1509_03979_gb300 import synth
-from tests.gpu_common import APPLY_TOL, SHAT_TOL, rel, to_dev
+from tests.gpu_common import APPLY_TOL, SHAT_TOL, rel, replay_parity, to_dev
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -47,12 +47,7 @@ def test_perm_decoders_match_oracle(B, N, M, K, algo):
     y = ref.apply(s)
     y = (y + 1e-3 * np.linalg.norm(y) / np.sqrt(M) * synth.normals(seed + 2, M)).astype(np.float32)
     op = B.Operator(N, M, seed, randomizer="perm")
-    s_hat, supp = op.recover(to_dev(y), K, algo, 1e-6, 200)
-    assert op.stats()["status"] == 0
-    want = greedy.recover(ref, y.astype(np.float64), K, algo)
-    if want["near_ties"] == 0:
-        assert np.array_equal(np.sort(supp.cpu().numpy()), want["S"])
-    assert rel(s_hat.cpu().numpy(), want["s"]) <= SHAT_TOL
+    rep, s_hat, supp, st, want = replay_parity(op, ref, y, K, algo, 1e-6, 200)
     if N <= 1 << 16:
         s2, _ = op.recover_noalloc(to_dev(y), K, algo, 1e-6, 200)
         assert rel(s2.cpu().numpy(), want["s"]) <= SHAT_TOL

@@ -142,11 +142,11 @@ class _Recorder(greedy.OwnChoice):
     def __init__(self):
         self.events = []
 
-    def select(self, kind, own, mu, a, allowed):
+    def select(self, kind, own, mu, a, allowed, values="corr"):
         self.events.append(kind)
         return own
 
-    def decide(self, kind, own, mu):
+    def decide(self, kind, own, mu, vals=None):
         self.events.append(kind)
         return own
 
@@ -177,7 +177,7 @@ def test_forced_sequence_replays_omp_and_can_take_another_member_of_a_tie():
     rec = []
 
     class Log(greedy.OwnChoice):
-        def select(self, kind, own, mu, a, allowed):
+        def select(self, kind, own, mu, a, allowed, values="corr"):
             rec.append(own)
             return own
     own = greedy.omp(op, y, 4, policy=Log())

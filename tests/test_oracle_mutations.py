@@ -214,7 +214,7 @@ def test_topk_margin_against_the_wrong_neighbour_is_caught(monkeypatch):
 
 def test_ompr_that_never_stops_is_caught(monkeypatch):
     class Always(greedy.OwnChoice):
-        def decide(self, kind, own, mu):
+        def decide(self, kind, own, mu, vals=None):
             return True if kind == "swap" else own
     orig = greedy.ompr
     monkeypatch.setattr(greedy, "ompr", lambda *a, **k: orig(*a, **dict(k, policy=Always())))

@@ -48,3 +48,34 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     y = torch.zeros(1 << 15, dtype=torch.float32, device="cuda")
     with pytest.raises(RuntimeError, match="65536"):
         op.recover_noalloc(y, 10, "omp")
+
+
+def test_noalloc_allocates_nothing_and_matches_the_oracle():
+    """After a warm-up call, two more calls leave the device's free memory and the torch
+    allocator's counters unchanged (the call allocates nothing), and the result matches the FP64
+    oracle selection by selection (its trace replayed) with s_hat within the recovery tolerance."""
+    from paper_1509_03979_gb300 import binding
+    from oracle import replay
+    binding.lib()
+    p = synth.Problem(1 << 15, 1 << 13, 400, "sp", 0x78001, 0x78002, 0x78003, 1e-3)
+    ref_op = oracle.Operator(p.N, p.M, p.op_seed)
+    _, y = measurements(p, ref_op)
+    op = binding.Operator(p.N, p.M, p.op_seed)
+    yd = to_dev(y)
+    s_out = torch.empty(p.N, dtype=torch.float32, device=yd.device)
+    k_out = torch.empty(p.K, dtype=torch.int32, device=yd.device)
+    tr = torch.zeros(replay.trace_words(p.N, p.K, "sp"), dtype=torch.int32, device=yd.device)
+    op.set_trace(tr)
+    op.recover_noalloc(yd, p.K, "sp", 1e-6, 200, s_out, k_out)      # warm-up: first call on the device
+    torch.cuda.synchronize()
+    keys = ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.allocated")
+    before = {k: torch.cuda.memory_stats().get(k, 0) for k in keys}
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        op.recover_noalloc(yd, p.K, "sp", 1e-6, 200, s_out, k_out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert {k: torch.cuda.memory_stats().get(k, 0) for k in keys} == before
+    op.set_trace(None)
+    replay.check_recovery(ref_op, y.astype(np.float64), p.K, "sp", tr.cpu().numpy(), s_out.cpu().numpy(),
+                          k_out.cpu().numpy(), SHAT_TOL)
