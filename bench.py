@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the loop of single-signal calls")
-    ap.add_argument("--paper-max-log2n", type=int, default=23, help="largest log2 N of the paper sweep")
+    ap.add_argument("--paper-max-log2n", type=int, default=24, help="largest log2 N of the paper sweep")
     ap.add_argument("--profile-case", default=None, choices=["apply", "apply_t", "sp", "omp", "ompr", "mixed"],
                     help="run one small fixed case for a profiler and exit (no timing, no JSON)")
     ap.add_argument("--case-N", type=int, default=1 << 18)
@@ -154,19 +154,25 @@ def flops_per_dct(N):
 
 
 def cpu_info():
+    """Host cores available to this process and the CPU model (lscpu, else /proc/cpuinfo)."""
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     model = None
     try:
-        for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
                 model = line.split(":", 1)[1].strip()
                 break
-    except OSError:
-        pass
-    try:
-        model = model or subprocess.run(["lscpu"], capture_output=True, text=True).stdout.split("Model name:")[1].split("\n")[0].strip()
     except Exception:
         pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
     return cores, model
 
 
@@ -601,7 +607,9 @@ def run_profile_case(args):
               for op, p in zip(ops, probs)]
         for _ in range(args.case_reps):
             binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs], CG_TOL, CG_MAXIT)
-    else:
+        _, _, st = binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs], CG_TOL, CG_MAXIT,
+                                           want_stats=True)   # after the profiled launches: their work
+        print("transforms per launch", sum(x["transforms"] for x in st), "engine", engine_sha())
         N, M = args.case_N, args.case_N // 4
         op = binding.Operator(N, M, 0x0C5002)
         op.set_batched_impl(args.case_impl)
@@ -614,9 +622,12 @@ def run_profile_case(args):
             K = max(1, M // 10)
             S = np.stack([synth.sparse_gaussian(N, K, 100 + b) for b in range(args.case_batch)]).astype(np.float32)
             Y = op.apply_batched(torch.from_numpy(S).to(dev))
+            args_r = ([op] * args.case_batch, [Y[b] for b in range(args.case_batch)], [K] * args.case_batch,
+                      [args.profile_case] * args.case_batch, 1e-6, 100)
             for _ in range(args.case_reps):
-                binding.recover_batched([op] * args.case_batch, [Y[b] for b in range(args.case_batch)],
-                                        [K] * args.case_batch, [args.profile_case] * args.case_batch, 1e-6, 100)
+                binding.recover_batched(*args_r)
+            _, _, st = binding.recover_batched(*args_r, want_stats=True)   # after the profiled launches
+            print("transforms per launch", sum(x["transforms"] for x in st), "engine", engine_sha())
     torch.cuda.synchronize()
     print("ok", args.profile_case, args.case_N, args.case_batch)
 
@@ -738,7 +749,8 @@ def run_paper_sweep(args, rank, local_rank):
     computation as xi = 1e-10.  One timed recovery per (decoder, N, precision) after a warm-up on
     the same input; SNR = 20 log10(||s|| / ||s_hat - s||), and the SNR change of xi = 1e-5 from
     exact precision (Sec. IV-C reports about +-0.1 dB).  OMPR runs both as the single-swap
-    decoder (swap cap 100) and as OMPR(l) with l = K/4 replacements per round."""
+    decoder (swap cap 100, and up to K swaps for N <= 2^18) and as OMPR(l) with l = K/4
+    replacements per round; `converged` says whether a single-swap run stopped on its rule."""
     import torch
     from paper_1509_03979_gb300 import binding
 
@@ -748,16 +760,20 @@ def run_paper_sweep(args, rank, local_rank):
     rows = []
     top = args.paper_max_log2n
     sizes = {"omp": range(11, min(18, top) + 1), "sp": range(11, top + 1), "ompr": range(11, top + 1),
-             "ompr(l=K/4)": range(11, top + 1)}
-    for variant in ("omp", "sp", "ompr", "ompr(l=K/4)"):
+             "ompr(cap=K)": range(11, min(18, top) + 1), "ompr(l=K/4)": range(11, top + 1)}
+    for variant in ("omp", "sp", "ompr", "ompr(cap=K)", "ompr(l=K/4)"):
         algo = "ompr" if variant.startswith("ompr") else variant
         for e in sizes[variant]:
             N = 1 << e
             M, K, s, noise = synth.paper_workload(N, 0x1509 + e)
             op = binding.Operator(N, M, 0x1509 + e)
             op.set_cg_tol_mode("absolute")
-            if variant != algo:
+            cap = 100
+            if variant == "ompr(l=K/4)":
                 op.set_ompr_replacements(max(1, K // 4))
+            elif variant == "ompr(cap=K)":
+                cap = K
+                op.set_outer_cap(cap)                  # single swaps, up to K of them
             sd = torch.from_numpy(s.astype(np.float32)).to(devc)
             y = (op.apply(sd) + torch.from_numpy(noise.astype(np.float32)).to(devc)).contiguous()
             s_out = torch.empty(N, device=devc)
@@ -777,7 +793,7 @@ def run_paper_sweep(args, rank, local_rank):
                 rows.append({"algo": variant, "log2N": e, "precision": name, "seconds": e0.elapsed_time(e1) / 1e3,
                              "snr_db": snr[name], "outer_iters": st["outer_iters"], "cg_iters": st["cg_iters_total"],
                              "status": st["status"], "near_ties": st["near_ties"],
-                             "converged": not (algo == "ompr" and variant == algo and st["outer_iters"] >= 100),
+                             "converged": not (algo == "ompr" and "l=" not in variant and st["outer_iters"] >= cap),
                              "paper_seconds": None if paper is None else (paper[2] if name == "xi=1e-5" else paper[0])})
             rows[-2]["snr_delta_db_vs_exact"] = snr["xi=1e-5"] - snr["exact"]
             op.close()

@@ -21,10 +21,14 @@
  *     FP32 values and int32 indices, contiguous, unless a comment says "host".
  *   - Calls are asynchronous on the operator's stream (cs_op_set_stream); they return after
  *     the launch.  Argument errors are returned synchronously and nothing is launched.
- *   - N must be a power of two with 16 <= N <= 2^23 (else CS_ERR_UNSUPPORTED_N);
+ *   - N must be a power of two with 16 <= N <= 2^24, or any N with 16 <= N <= 4096 (else
+ *     CS_ERR_UNSUPPORTED_N);
  *     1 <= M <= N; 0 <= K <= M; for SP also 2K <= M, for CoSaMP 3K <= M (else
  *     CS_ERR_INVALID_ARG).
- *     N <= 2^18 runs on one thread-block cluster per signal; 2^18 < N <= 2^23 runs on a
+ *     An N that is not a power of two runs on the any-N path: one CTA per signal holds it in
+ *     natural order and computes the DCT-II / DCT-III as chirp-z transforms (Bluestein) over
+ *     power-of-two FFTs of at least 2N - 1 points; the sign randomiser only.
+ *     A power of two N <= 2^18 runs on one thread-block cluster per signal; 2^18 < N <= 2^24 runs on a
  *     cooperative grid of up to 128 CTAs per signal that streams the transform through L2
  *     (such signals are processed one after another, also inside the batched calls).
  *     A grid-wide wait that does not finish within its iteration limit ends the launch early:
@@ -99,6 +103,17 @@ cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed);
 enum { CS_RANDOMIZER_SIGNS = 0, CS_RANDOMIZER_PERMUTATION = 1 };
 cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer);
 
+/* The operator with a sparsifying basis Psi (Sec. III-A: y = Phi Psi s, the signal sparse in
+ * the basis; the image experiment of Sec. IV-A takes a DCT basis): A = P_Omega C_N diag(d) Psi,
+ * the unknown s holds the basis coefficients of x = Psi s, and every entry point recovers,
+ * solves and differentiates in s.  CS_BASIS_IDENTITY is cs_op_create's operator;
+ * CS_BASIS_DCT is Psi = C_N^T (s = the orthonormal DCT-II coefficients of x), for
+ * 16 <= N <= 4096 (else CS_ERR_UNSUPPORTED_N) with the sign randomiser d.  Psi is orthonormal,
+ * so A A^T = I_M still holds.  Such operators run on the any-N path (one CTA, chirp-z DCTs),
+ * whatever N is.  Returns NULL on failure. */
+enum { CS_BASIS_IDENTITY = 0, CS_BASIS_DCT = 1 };
+cs_op_t cs_op_create_basis(int64_t N, int64_t M, uint64_t seed, int32_t basis);
+
 /* Host-only draw of the permutation randomiser for (N, seed) into perm_N_host [N] HOST. */
 cs_status cs_operator_perm(int64_t N, uint64_t seed, int32_t* perm_N_host);
 
@@ -158,6 +173,13 @@ cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, 
  * largest |z| over S u J (ties to the lowest index), stop when S' = S; the swap cap of
  * cs_recover counts rounds.  l is clamped to N - K. */
 cs_status cs_op_set_ompr_replacements(cs_op_t op, int32_t l);
+
+/* Cap on the outer iterations of this op's later recoveries (no counterpart in the paper, which
+ * leaves SP's and OMPR's iteration limits open): SP and CoSaMP rounds, OMPR swaps (single-swap)
+ * or rounds (OMPR(l)).  0 (the default) means 50 SP / CoSaMP rounds and 100 OMPR swaps or
+ * rounds.  A recovery that reaches the cap returns its current state; cs_stats.outer_iters
+ * equals the cap then. */
+cs_status cs_op_set_outer_cap(cs_op_t op, int32_t cap);
 
 enum { CS_CG_TOL_RELATIVE = 0, CS_CG_TOL_ABSOLUTE = 1 };
 /* Stopping rule of every CG solve of this op's later recover / LS calls (see the conventions

@@ -33,6 +33,7 @@ _I64, _U64, _I32, _F32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes
 SIGNATURES = {
     "cs_op_create": (_P, [_I64, _I64, _U64]),
     "cs_op_create_ex": (_P, [_I64, _I64, _U64, _I32]),
+    "cs_op_create_basis": (_P, [_I64, _I64, _U64, _I32]),
     "cs_operator_perm": (_I32, [_I64, _U64, _P]),
     "cs_op_export_perm": (_I32, [_P, _P]),
     "cs_op_destroy": (None, [_P]),
@@ -54,6 +55,7 @@ SIGNATURES = {
     "cs_recover": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
     "cs_recover_noalloc": (_I32, [_P, _P, _I32, _I32, _F32, _I32, _P, _P]),
     "cs_op_set_trace": (_I32, [_P, _P, _I64]),
+    "cs_op_set_outer_cap": (_I32, [_P, _I32]),
     "cs_recover_batched": (_I32, [_I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P]),
     "cs_ls_solve": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
     "cs_ls_backward": (_I32, [_P, _P, _I32, _P, _F32, _I32, _P]),
@@ -117,12 +119,20 @@ class Operator:
     """A = P_Omega C_N diag(d) on the current CUDA device (Sec. III-A, Eq. 7)."""
 
     RANDOMIZERS = {"signs": 0, "perm": 1}
+    BASES = {None: 0, "dct": 1}
 
-    def __init__(self, N, M, seed, randomizer="signs"):
-        """randomizer: 'signs' (R = diag(d), the default) or 'perm' (R a random permutation)."""
+    def __init__(self, N, M, seed, randomizer="signs", psi=None):
+        """randomizer: 'signs' (R = diag(d), the default) or 'perm' (R a random permutation);
+        psi: None (s sparse itself) or 'dct' (s the DCT coefficients of x = C_N^T s)."""
         self.N, self.M, self.seed = int(N), int(M), int(seed)
         self.randomizer = randomizer
-        h = lib().cs_op_create_ex(self.N, self.M, self.seed, self.RANDOMIZERS[randomizer])
+        self.psi = psi
+        if psi is not None:
+            if randomizer != "signs":
+                raise ValueError("a sparsifying basis takes the sign randomiser")
+            h = lib().cs_op_create_basis(self.N, self.M, self.seed, self.BASES[psi])
+        else:
+            h = lib().cs_op_create_ex(self.N, self.M, self.seed, self.RANDOMIZERS[randomizer])
         if not h:
             raise RuntimeError(f"cs_op_create failed: {lib().cs_last_error().decode()}")
         self._h = ctypes.c_void_p(h)
@@ -194,6 +204,10 @@ class Operator:
             return
         _check(lib().cs_op_set_trace(self._h, _dev(trace, torch.int32, None, "trace"), int(trace.numel())))
         self._trace = trace
+
+    def set_outer_cap(self, cap):
+        """Cap on SP / CoSaMP rounds and OMPR swaps of later recoveries (0: 50 and 100)."""
+        _check(lib().cs_op_set_outer_cap(self._h, int(cap)))
 
     def set_ompr_replacements(self, l):
         """Replacements per OMPR round (1: single swap; l > 1: OMPR(l))."""

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -92,12 +93,51 @@ int8_t draw_sign(uint64_t sign_key, int64_t n) {
 }
 
 cs_status check_nm(int64_t N, int64_t M) {
-  if (!is_pow2(N) || N < N_MIN || N > N_MAX_GRID)
-    return fail(CS_ERR_UNSUPPORTED_N, "N must be a power of two in [16, 2^23], got " + std::to_string(N));
+  if (N < N_MIN || N > N_MAX_GRID || (!is_pow2(N) && N > N_MAX_ANY))
+    return fail(CS_ERR_UNSUPPORTED_N, "N must be in [16, 4096] or a power of two in [16, 2^24], got " +
+                                          std::to_string(N));
   if (M < 1 || M > N) return fail(CS_ERR_INVALID_ARG, "M must satisfy 1 <= M <= N");
   return CS_OK;
 }
 int log2i(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+
+// In-place radix-2 FFT in FP64 (exp(-2 pi i j k / n)), n a power of two: the host builds the
+// any-N path's chirp-kernel table with it.
+void fft_host(std::vector<std::complex<double>>& a) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const double ang = -2.0 * M_PI / (double)len;
+    for (size_t i = 0; i < n; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const std::complex<double> w(std::cos(ang * (double)k), std::sin(ang * (double)k));
+        const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+  }
+}
+
+// Two-level table of omega_T^j = exp(-2 pi i j / T) for j < 2^(lo_bits + hi_bits):
+// [2^lo_bits] entries omega^i, then [2^hi_bits] entries omega^(j << lo_bits).
+std::vector<float2> twiddle_table(double T, int lo_bits, int hi_bits) {
+  const int nlo = 1 << lo_bits, nhi = 1 << hi_bits;
+  std::vector<float2> tw((size_t)(nlo + nhi));
+  for (int i = 0; i < nlo; ++i) {
+    const double a = 2.0 * M_PI * (double)i / T;
+    tw[(size_t)i] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  for (int j = 0; j < nhi; ++j) {
+    const double a = 2.0 * M_PI * (double)((int64_t)j << lo_bits) / T;
+    tw[(size_t)(nlo + j)] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  return tw;
+}
 
 }  // namespace
 
@@ -123,8 +163,10 @@ struct cs_op {
   int batched_impl = CS_BATCHED_AUTO;
   int cg_abs = 0;               // CG stopping rule: 0 relative, 1 absolute (cs_op_set_cg_tol_mode)
   int ompr_l = 1;               // OMPR replacements per round (cs_op_set_ompr_replacements)
+  int outer_cap = 0;            // cap on SP / CoSaMP rounds and OMPR swaps (0: 50 and 100)
   int tuned_nc[2] = {0, 0};     // per mode (A, A^T): 0 untuned, -1 cluster engine, else CTAs per vector
   std::vector<cudaStream_t> fork_streams;   // created on first use, kept until cs_op_destroy
+  float2* d_czt = nullptr;      // any-N path: chirp-kernel FFT [czt_n], then the FFT twiddle table
   uint32_t* trace = nullptr;    // selection trace of later recoveries (cs_op_set_trace), caller-owned
   int64_t trace_words = 0;
 };
@@ -145,6 +187,7 @@ void free_op(cs_op* op) {
   cudaFree(op->d_prank);
   cudaFree(op->d_perm);
   cudaFree(op->d_stream_err);
+  cudaFree(op->d_czt);
   for (cudaStream_t s : op->fork_streams) cudaStreamDestroy(s);
   delete op;
 }
@@ -181,7 +224,7 @@ Launch single_launch(const cs_op* op, const Task& t) {
   L.single = t;
   L.ntasks = 1;
   L.F_alloc = op->dev.F;
-  L.plan = op->dev.grid ? grid_plan(op->dev) : cluster_plan(op->dev.F);
+  L.plan = op_plan(op->dev);
   L.scratch = op->d_scratch;
   L.scratch_per_cluster = (size_t)op->dev.P * scratch_floats_per_cta(op->dev.F);
   L.bits = op->d_bits;
@@ -212,6 +255,11 @@ cs_status check_cg(float cg_tol, int32_t cg_maxit) {
 constexpr int SP_ROUNDS = 50;     // SP / CoSaMP outer-iteration cap
 constexpr int STREAM_CLUSTER = 4;  // default CTAs per vector of the streamed batched operator (fastest untuned at 256 vectors)
 constexpr int OMPR_SWAPS = 100;   // OMPR replacement cap
+
+int outer_cap_of(const cs_op* op, int algo) {
+  if (op->outer_cap > 0) return op->outer_cap;
+  return (algo == CS_SP || algo == CS_COSAMP) ? SP_ROUNDS : OMPR_SWAPS;
+}
 
 }  // namespace
 
@@ -244,7 +292,25 @@ cs_status cs_operator_perm(int64_t N, uint64_t seed, int32_t* perm_N_host) {
 
 cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) { return cs_op_create_ex(N, M, seed, CS_RANDOMIZER_SIGNS); }
 
+static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer, int32_t basis);
+
 cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer) {
+  return create_op(N, M, seed, randomizer, CS_BASIS_IDENTITY);
+}
+
+cs_op_t cs_op_create_basis(int64_t N, int64_t M, uint64_t seed, int32_t basis) {
+  if (basis != CS_BASIS_IDENTITY && basis != CS_BASIS_DCT) {
+    fail(CS_ERR_INVALID_ARG, "unknown sparsifying basis");
+    return nullptr;
+  }
+  if (basis != CS_BASIS_IDENTITY && N > N_MAX_ANY) {
+    fail(CS_ERR_UNSUPPORTED_N, "a sparsifying basis needs N <= 4096");
+    return nullptr;
+  }
+  return create_op(N, M, seed, CS_RANDOMIZER_SIGNS, basis);
+}
+
+static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer, int32_t basis) {
   if (check_nm(N, M) != CS_OK) return nullptr;
   if (randomizer != CS_RANDOMIZER_SIGNS && randomizer != CS_RANDOMIZER_PERMUTATION) {
     fail(CS_ERR_INVALID_ARG, "unknown randomiser");
@@ -261,30 +327,41 @@ cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer)
   std::vector<int32_t> orank((size_t)W, 0);
   for (int32_t v : op->h_omega) omask[(size_t)(v >> 5)] |= 1u << (v & 31);
   for (int64_t w = 1; w < W; ++w) orank[(size_t)w] = orank[(size_t)w - 1] + __builtin_popcount(omask[(size_t)w - 1]);
-  // twiddles omega_{4N}^j = exp(-2 pi i j / 4N), two-level split
-  const int T = log2i(4 * N);
-  const int lo_bits = (T + 1) / 2, hi_bits = T - lo_bits;
-  const int nlo = 1 << lo_bits, nhi = 1 << hi_bits;
-  std::vector<float2> tw((size_t)(nlo + nhi));
-  const double four_n = 4.0 * (double)N;
-  for (int i = 0; i < nlo; ++i) {
-    const double a = 2.0 * M_PI * (double)i / four_n;
-    tw[(size_t)i] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  // twiddles omega_{4N}^j = exp(-2 pi i j / 4N), two-level split over j < 4N, or for
+  // N >= N_TW_QUARTER over one quarter period j < N (the device folds j = q N + r); for an N
+  // that is not a power of two (the any-N path) 128 low entries and enough high ones for j < 4N
+  const bool generic = !is_pow2(N) || basis != CS_BASIS_IDENTITY;
+  if (generic && randomizer != CS_RANDOMIZER_SIGNS) {
+    fail(CS_ERR_UNSUPPORTED_N, "N that is not a power of two supports the sign randomiser only");
+    delete op;
+    return nullptr;
   }
-  for (int j = 0; j < nhi; ++j) {
-    const double a = 2.0 * M_PI * (double)((int64_t)j << lo_bits) / four_n;
-    tw[(size_t)(nlo + j)] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  const bool quarter = N >= N_TW_QUARTER;
+  int lo_bits, hi_bits;
+  if (generic) {
+    lo_bits = 7;
+    hi_bits = log2i((4 * N + 127) / 128);
+  } else {
+    const int T = log2i(quarter ? N : 4 * N);
+    lo_bits = (T + 1) / 2;
+    hi_bits = T - lo_bits;
   }
+  const std::vector<float2> tw = twiddle_table(4.0 * (double)N, lo_bits, hi_bits);
   const int64_t L = N / 2;
   OpDev& d = op->dev;
   d.N = (int)N;
   d.M = (int)M;
   d.lo_bits = lo_bits;
   d.hi_bits = hi_bits;
+  d.tw_quarter = quarter ? 1 : 0;
   d.sign_key = seed ^ SIGN_SALT;
   d.grid = N > N_MAX ? 1 : 0;
   int P = 1, F = (int)L;
-  if (d.grid) {
+  d.generic = generic ? 1 : 0;
+  d.psi = basis == CS_BASIS_DCT ? 1 : 0;
+  if (generic) {
+    F = (int)((N + 1) / 2);   // 2F >= N real slots on one CTA
+  } else if (d.grid) {
     // streamed geometry: rows of S1 points, G CTAs owning R rows each, column blocks of W
     d.S1 = GRID_S1;
     d.S2 = (int)(L / GRID_S1);
@@ -334,7 +411,35 @@ cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer)
     d.perm = op->d_perm;
     d.iperm = op->d_perm + N;
   }
-  if (!d.grid && N >= STREAM_N_MIN && randomizer == CS_RANDOMIZER_SIGNS) {
+  if (generic) {
+    // chirp-z tables: the FFT over czt_n >= 2N - 1 points of the kernel b_m = c_{|m|} (indices
+    // mod czt_n, zero for |m| >= N), c_m = exp(i pi m^2 / 2N), scaled by 1 / czt_n; then the
+    // two-level omega_{4 czt_n} table of that FFT
+    const int cn = 1 << log2i(2 * N - 1);
+    std::vector<std::complex<double>> b((size_t)cn, 0.0);
+    for (int64_t m = 0; m < N; ++m) {
+      const double ph = M_PI * (double)((m * m) % (4 * N)) / (2.0 * (double)N);
+      const std::complex<double> c(std::cos(ph), std::sin(ph));
+      b[(size_t)m] = c;
+      if (m > 0) b[(size_t)(cn - m)] = c;
+    }
+    fft_host(b);
+    const int T2 = log2i(4 * (int64_t)cn);
+    const int lo2 = (T2 + 1) / 2, hi2 = T2 - lo2;
+    const std::vector<float2> tw2 = twiddle_table(4.0 * (double)cn, lo2, hi2);
+    std::vector<float2> tab((size_t)cn + tw2.size());
+    for (int k = 0; k < cn; ++k)
+      tab[(size_t)k] = make_float2((float)(b[(size_t)k].real() / cn), (float)(b[(size_t)k].imag() / cn));
+    std::copy(tw2.begin(), tw2.end(), tab.begin() + cn);
+    CSG_TRY(cudaMalloc(&op->d_czt, sizeof(float2) * tab.size()));
+    CSG_TRY(cudaMemcpy(op->d_czt, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice));
+    d.czt_n = cn;
+    d.czt_hat = op->d_czt;
+    d.tw2 = op->d_czt + cn;
+    d.tw2_lo_bits = lo2;
+    d.tw2_hi_bits = hi2;
+  }
+  if (!d.grid && N >= STREAM_N_MIN && randomizer == CS_RANDOMIZER_SIGNS && !generic) {
     std::vector<uint32_t> dbits((size_t)W, 0u);
     for (int64_t n = 0; n < N; ++n)
       if (draw_sign(d.sign_key, n) < 0) dbits[(size_t)(n >> 5)] |= 1u << (n & 31);
@@ -386,7 +491,10 @@ cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer)
     const size_t off_red = off_bar + 64;
     const size_t off_red64 = off_red + (size_t)4 * d.G * 4 * sizeof(float);
     const size_t off_hist = off_red64 + (size_t)4 * d.G * 2 * sizeof(unsigned long long);
-    const size_t total = off_hist + (size_t)2 * d.G * 256 * sizeof(uint32_t);
+    const size_t off_fb = off_hist + (size_t)2 * d.G * 256 * sizeof(uint32_t);
+    // N = 2^24: the Omega bits of each CTA's frequency tasks live here, not in shared memory
+    const int fb_stride = N >= N_TW_QUARTER ? (d.bpc * ((d.W / 2) * d.S2 + d.S2 + 1) + 15) / 16 * 16 : 0;
+    const size_t total = off_fb + (size_t)d.G * fb_stride;
     if ((e = cudaMalloc(&op->d_grid, total)) != cudaSuccess) {
       cuda_fail(e, "cudaMalloc(grid state)");
       free_op(op);
@@ -405,6 +513,8 @@ cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer)
     d.gred = reinterpret_cast<float*>(b + off_red);
     d.gred64 = reinterpret_cast<unsigned long long*>(b + off_red64);
     d.ghist = reinterpret_cast<uint32_t*>(b + off_hist);
+    d.gfb = fb_stride ? reinterpret_cast<uint8_t*>(b + off_fb) : nullptr;
+    d.gfb_stride = fb_stride;
     if (!grid_fits(d)) {
       fail(CS_ERR_UNSUPPORTED_N, "the streamed geometry's cooperative launch does not fit this device");
       free_op(op);
@@ -412,7 +522,7 @@ cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer)
     }
     return op;
   }
-  if (max_active_clusters(P, F) < 1) {
+  if (max_active_plan(P, op_plan(d)) < 1) {
     fail(CS_ERR_UNSUPPORTED_N, "a cluster of " + std::to_string(P) + " CTAs cannot be scheduled on this device");
     free_op(op);
     return nullptr;
@@ -521,6 +631,7 @@ cs_status cs_op_apply_t_batched(cs_op_t op, int32_t B, const float* U, float* X)
 cs_status cs_op_set_cluster_size(cs_op_t op, int32_t P) {
   if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
   if (op->dev.grid) return fail(CS_ERR_UNSUPPORTED_N, "the cluster size applies to N <= 2^18");
+  if (op->dev.generic) return fail(CS_ERR_UNSUPPORTED_N, "an N that is not a power of two runs on one CTA");
   const int64_t L = op->N / 2;
   const int Pmin = L > F_MAX ? (int)(L / F_MAX) : 1;
   if (P == 0) P = Pmin;
@@ -552,7 +663,7 @@ cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, 
   constexpr int NCAND = 5;
   if (ms_out)
     for (int i = 0; i < NCAND; ++i) ms_out[i] = -1.f;
-  if (op->dev.grid) return CS_OK;   // one geometry only
+  if (op->dev.grid || op->dev.generic) return CS_OK;   // one geometry only
   cs_status st = check_cg(cg_tol, cg_maxit);
   if (st != CS_OK) return st;
   if (K < 1 || K > op->M || algo < CS_OMP || algo > CS_COSAMP || (algo == CS_SP && 2 * (int64_t)K > op->M) ||
@@ -605,6 +716,13 @@ cs_status cs_op_tune_recover(cs_op_t op, int32_t K, int32_t algo, float cg_tol, 
   cudaFree(so);
   cudaFree(supp);
   return st != CS_OK ? st : st2;
+}
+
+cs_status cs_op_set_outer_cap(cs_op_t op, int32_t cap) {
+  if (!op) return fail(CS_ERR_INVALID_ARG, "null operator");
+  if (cap < 0) return fail(CS_ERR_INVALID_ARG, "the outer-iteration cap must be >= 0");
+  op->outer_cap = cap;
+  return CS_OK;
 }
 
 cs_status cs_op_set_ompr_replacements(cs_op_t op, int32_t l) {
@@ -704,7 +822,7 @@ cs_status cs_probe_bounded_wait(uint64_t polls, int32_t set_flag) {
 int32_t cs_op_concurrency(cs_op_t op) {
   if (!op) return 1;
   if (op->dev.grid) return 1;
-  return std::max(1, max_active_clusters(op->dev.P, op->dev.F));
+  return std::max(1, max_active_plan(op->dev.P, op_plan(op->dev)));
 }
 
 cs_status cs_op_export(cs_op_t op, int32_t* omega_M_host, int8_t* d_N_host) {
@@ -749,7 +867,7 @@ cs_status cs_recover(cs_op_t op, const float* y, int32_t K, cs_algo algo, float 
   t.K = K;
   t.cg_tol = cg_tol;
   t.cg_maxit = cg_maxit;
-  t.outer_max = (algo == CS_SP || algo == CS_COSAMP) ? SP_ROUNDS : OMPR_SWAPS;
+  t.outer_max = outer_cap_of(op, (int)algo);
   t.in = y;
   t.out = s_out;
   t.supp_out = support_out;
@@ -772,7 +890,7 @@ cs_status cs_op_set_trace(cs_op_t op, int32_t* trace_dev, int64_t words) {
 // launch is issued, so the call can return (and its host vector die) at once, and a launch
 // captured into a CUDA graph carries its own tables rather than a pointer into freed host
 // memory.  The first chunk also zeroes the dynamic-claim counter that follows the table.
-constexpr int TASK_CHUNK = 112;
+constexpr int TASK_CHUNK = 92;
 struct TaskChunk {
   Task t[TASK_CHUNK];
   int n;                     // tasks in this chunk
@@ -807,11 +925,12 @@ static cudaError_t upload_tasks(const std::vector<Task>& g, Task* dst, int* clai
 // Launch a list of tasks grouped by cluster size; scratch and task arrays come from the
 // stream-ordered allocator and are released on the same stream.
 static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream, cs_op* owner) {
+  // groups: cluster size P (power-of-two N), or 1000 + czt_n for the any-N path (own plan)
   std::map<int, std::vector<Task>> groups;
   std::vector<Task> grid_tasks;
   for (const Task& t : tasks) {
     if (t.op.grid) grid_tasks.push_back(t);
-    else groups[t.op.P].push_back(t);
+    else groups[t.op.generic ? 1000 + t.op.czt_n : t.op.P].push_back(t);
   }
   // One persistent launch per cluster size.  With several sizes the launches run concurrently on
   // streams forked from `stream` (event record + wait) and joined back into it, so a long signal
@@ -840,8 +959,9 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream, cs_
   });
   cs_status st = CS_OK;
   for (auto& og : order) {
-    const int P = og.first;
     std::vector<Task>& g = *og.second;
+    const int P = g[0].op.P;
+    const bool generic = g[0].op.generic != 0;
     cudaStream_t s = stream;
     if (fork) {
       const size_t i = aux.size();
@@ -856,15 +976,21 @@ static cs_status launch_tasks(std::vector<Task>& tasks, cudaStream_t stream, cs_
     std::stable_sort(g.begin(), g.end(), [](const Task& a, const Task& b) {
       return (int64_t)a.op.N * std::max(a.K, a.k_in) > (int64_t)b.op.N * std::max(b.K, b.k_in);
     });
-    int F_alloc = 0, Nmax = 0;
-    for (const Task& t : g) { F_alloc = std::max(F_alloc, t.op.F); Nmax = std::max(Nmax, t.op.N); }
-    const int maxc = max_active_clusters(P, F_alloc);
+    int F_alloc = 0, Nmax = 0, hi_max = 0, t2l = 0, t2h = 0;
+    for (const Task& t : g) {
+      F_alloc = std::max(F_alloc, t.op.F);
+      Nmax = std::max(Nmax, t.op.N);
+      hi_max = std::max(hi_max, 1 << t.op.hi_bits);
+      if (generic) { t2l = std::max(t2l, 1 << t.op.tw2_lo_bits); t2h = std::max(t2h, 1 << t.op.tw2_hi_bits); }
+    }
+    const SmemPlan plan = generic ? generic_plan(g[0].op.czt_n, F_alloc, hi_max, t2l, t2h) : cluster_plan(F_alloc);
+    const int maxc = max_active_plan(P, plan);
     if (maxc < 1) { st = fail(CS_ERR_UNSUPPORTED_N, "cluster configuration cannot be scheduled"); break; }
     const int G = std::min<int>((int)g.size(), maxc);
     Launch L{};
     L.ntasks = (int)g.size();
     L.F_alloc = F_alloc;
-    L.plan = cluster_plan(F_alloc);
+    L.plan = plan;
     L.scratch_per_cluster = (size_t)P * scratch_floats_per_cta(F_alloc);
     L.bits_per_cluster = (size_t)(Nmax + 31) / 32;
     Task* d_tasks = nullptr;
@@ -967,7 +1093,7 @@ cs_status cs_recover_batched(int32_t B, const cs_op_t* ops, const float* const* 
     t.K = K[b];
     t.cg_tol = cg_tol;
     t.cg_maxit = cg_maxit;
-    t.outer_max = (algo[b] == CS_SP || algo[b] == CS_COSAMP) ? SP_ROUNDS : OMPR_SWAPS;
+    t.outer_max = outer_cap_of(ops[b], algo[b]);
     t.in = y[b];
     t.out = s_out[b];
     t.supp_out = support_out[b];
@@ -1129,7 +1255,7 @@ extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, c
   t.K = K;
   t.cg_tol = cg_tol;
   t.cg_maxit = cg_maxit;
-  t.outer_max = (algo == CS_SP || algo == CS_COSAMP) ? SP_ROUNDS : OMPR_SWAPS;
+  t.outer_max = outer_cap_of(op, (int)algo);
   t.in = y;
   t.out = s_out;
   t.supp_out = support_out;
@@ -1143,7 +1269,7 @@ extern "C" cs_status cs_recover_noalloc(cs_op_t op, const float* y, int32_t K, c
   L.single = t;
   L.ntasks = 1;
   L.F_alloc = op->dev.F;
-  L.plan = cluster_plan(op->dev.F);
+  L.plan = op_plan(op->dev);
   L.scratch = base;
   L.scratch_per_cluster = (size_t)op->dev.P * scratch_floats_per_cta(op->dev.F);
   L.bits = reinterpret_cast<uint32_t*>(base + NOALLOC_SCRATCH);

@@ -121,16 +121,27 @@ __host__ __device__ constexpr int apad(int F) { return F + F / 16; }
 // Two-level twiddle table: omega_{4N}^j = exp(-2 pi i j / 4N) = lo[j & m] * hi[j >> lo_bits];
 // lo is stored with the same one-in-16 padding as the FFT buffer, which keeps the strided
 // lookups of the FFT passes and the DCT twiddles (strides 1, 4, 8) free of bank conflicts.
+// For N = 2^24 the two levels would not fit next to the streamed plan, so the table covers
+// one quarter period instead: j = q N + r with r < N, omega_{4N}^j = (-i)^q omega_{4N}^r
+// (qbits = log2 N, qmask = N - 1).  Otherwise qbits = 31 and q is always 0.
 struct Tw {
   const float2* lo;
   const float2* hi;
   int lo_bits;
   int lo_mask;
   int mask4n;   // 4N - 1
+  int qbits;    // log2 N with a quarter-period table, else 31
+  int qmask;    // N - 1 with a quarter-period table, else 0x7fffffff
   template <int DIR>
   __device__ __forceinline__ float2 get(int j) const {
     j &= mask4n;
-    const float2 w = cmul(lo[aidx(j & lo_mask)], hi[j >> lo_bits]);
+    const int q = j >> qbits;
+    j &= qmask;
+    float2 w = cmul(lo[aidx(j & lo_mask)], hi[j >> lo_bits]);
+    if (q != 0) {   // times (-i)^q, exact
+      if (q & 1) w = make_float2(w.y, -w.x);
+      if (q & 2) w = make_float2(-w.x, -w.y);
+    }
     return DIR > 0 ? cconj(w) : w;
   }
 };
@@ -350,6 +361,9 @@ struct Smem {
   float* fscr;        // [8]
   int* cgl;           // [cap] support list when it fits
   float* cgv;         // [4][cap] CG x, r, p, q when they fit
+  float2* S;          // any-N path: signal-domain values by slot (natural order)
+  float2* tw2lo;      // any-N path: twiddles of the chirp-z FFT
+  float2* tw2hi;
 };
 
 // Bump allocator over the dynamic shared-memory window (16-byte granules).
@@ -384,7 +398,11 @@ __host__ __device__ inline void layout(const SmemPlan& pl, Bump& take, Smem* s) 
   unsigned char* fs = take(4 * 8);
   unsigned char* cl = take(4 * (size_t)cap);
   unsigned char* cv = take(16 * (size_t)cap);
+  unsigned char* sv = take(sizeof(float2) * (size_t)pl.slot_n);
+  unsigned char* t2l = take(sizeof(float2) * (size_t)(pl.tw2_lo_n ? apad(pl.tw2_lo_n) : 0));
+  unsigned char* t2h = take(sizeof(float2) * (size_t)pl.tw2_hi_n);
   if (s) {
+    s->S = (float2*)sv; s->tw2lo = (float2*)t2l; s->tw2hi = (float2*)t2h;
     s->A = (float2*)A; s->B = (float2*)B; s->twlo = (float2*)tl; s->twhi = (float2*)th;
     s->signw = (uint32_t*)sw; s->mask[0] = (uint32_t*)m0; s->mask[1] = (uint32_t*)m1;
     s->fbits = (uint8_t*)fb; s->hist = (uint32_t*)hi; s->htot = (uint32_t*)ht; s->ring = (float*)rg;
@@ -410,6 +428,26 @@ SmemPlan cluster_plan(int F_alloc) {
   p.slot_words = (2 * F_alloc + 31) / 32;
   p.fb_bytes = F_alloc / 2 + P_MAX + 16;
   p.cg_cap = cluster_cg_cap(F_alloc);
+  p.slot_n = 0;
+  p.tw2_lo_n = 0;
+  p.tw2_hi_n = 0;
+  return p;
+}
+
+// Any-N launches: FFT buffers of czt_n points, the DCT twiddle table (128 low entries), the
+// slot buffer of F_alloc complex entries (2 F_alloc >= N real slots) and the FFT's twiddles.
+SmemPlan generic_plan(int czt_n, int F_alloc, int tw_hi_n, int tw2_lo_n, int tw2_hi_n) {
+  SmemPlan p;
+  p.fft_n = czt_n;
+  p.tw_lo_n = 128;
+  p.tw_hi_n = tw_hi_n;
+  p.slot_words = (2 * F_alloc + 31) / 32;
+  p.fb_bytes = 16;
+  // next to two 8192-point FFT buffers only 1024 support entries fit on chip (20 KB)
+  p.cg_cap = czt_n >= F_MAX ? 1024 : cluster_cg_cap(F_alloc);
+  p.slot_n = apad(F_alloc);
+  p.tw2_lo_n = tw2_lo_n;
+  p.tw2_hi_n = tw2_hi_n;
   return p;
 }
 
@@ -421,9 +459,18 @@ SmemPlan grid_plan(const OpDev& op) {
   p.tw_lo_n = 1 << op.lo_bits;
   p.tw_hi_n = 1 << op.hi_bits;
   p.slot_words = (2 * op.R * op.S1 + 31) / 32;
-  p.fb_bytes = op.bpc * ((op.W / 2) * op.S2 + op.S2 + 1) + 16;
+  p.fb_bytes = op.gfb ? 16 : op.bpc * ((op.W / 2) * op.S2 + op.S2 + 1) + 16;
   p.cg_cap = 0;
+  p.slot_n = 0;
+  p.tw2_lo_n = 0;
+  p.tw2_hi_n = 0;
   return p;
+}
+
+SmemPlan op_plan(const OpDev& op) {
+  if (op.grid) return grid_plan(op);
+  if (op.generic) return generic_plan(op.czt_n, op.F, 1 << op.hi_bits, 1 << op.tw2_lo_bits, 1 << op.tw2_hi_bits);
+  return cluster_plan(op.F);
 }
 
 size_t smem_bytes(const SmemPlan& pl) {
@@ -439,6 +486,7 @@ enum SrcKind : int { SRC_NONE = 0, SRC_CG = 1, SRC_DENSE_SLOTS = 2, SRC_GLOBAL_N
 // Geometry of one signal as seen by one CTA (all sizes powers of two); kept in registers.
 struct Geo {
   int N, L, P, F, h, lh, S2, c, four_n;
+  int nat;   // 1: slot sigma is signal index sigma (the any-N path), 0: the stride-P Makhoul layout
 };
 
 // Per-CTA context of the signal being processed.  It lives in shared memory (one copy per CTA)
@@ -489,8 +537,23 @@ struct Ctx {
   int trace_off;      // word offset of the next record (advanced identically in every CTA)
   int trace_recs;     // records written
   int trace_over;     // 1 once a record did not fit: nothing more is written
+  // the any-N path
+  int gen;            // 1: this task runs the any-N transform
+  int nslots;         // valid slots of this CTA (2F, or N on the any-N path)
+  int czt_n;
+  const float2* czt_hat;
+  Tw tw2;             // twiddles of the chirp-z FFT (omega_{4 czt_n})
+  SmemPlan plan;      // the launch's shared-memory plan
 };
 __shared__ Ctx C;
+
+// The twiddle tables of the current task, addressed in shared memory.
+__device__ __forceinline__ Tw smem_tw() {
+  Tw t = C.tw;
+  t.lo = shp(C.sm.twlo);
+  t.hi = shp(C.sm.twhi);
+  return t;
+}
 
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
 template <class T>
@@ -556,7 +619,7 @@ struct SigView {
 __device__ __forceinline__ SigView sigview() {
   SigView v;
   if (C.grid) { v.base = reinterpret_cast<float*>(C.sig); v.rmask = C.rmask; v.rshift = C.rshift; v.rowstride = C.rowstride; }
-  else { v.base = reinterpret_cast<float*>(shp(C.sm.A)); v.rmask = 0; v.rshift = 0; v.rowstride = 0; }
+  else { v.base = reinterpret_cast<float*>(C.gen ? shp(C.sm.S) : shp(C.sm.A)); v.rmask = 0; v.rshift = 0; v.rowstride = 0; }
   return v;
 }
 
@@ -566,11 +629,17 @@ __device__ __forceinline__ float& slot_ref(float2* A, int sigma) {
 // Signal index of local real slot sigma of CTA c: complex point m = q P + c of z, real index
 // v = 2 m + b of Makhoul's reordered sequence, v < N/2 -> n = 2 v, else n = 2 (N - 1 - v) + 1.
 __device__ __forceinline__ int n_of_slot(const Geo& g, int sigma) {
+  if (g.nat) return sigma;
   const int m = (sigma >> 1) * g.P + g.c;
   const int v = 2 * m + (sigma & 1);
   return v < (g.N >> 1) ? 2 * v : 2 * (g.N - 1 - v) + 1;
 }
 __device__ __forceinline__ void slot_of_n(const Geo& g, int n, int& owner, int& sigma) {
+  if (g.nat) {
+    owner = 0;
+    sigma = n;
+    return;
+  }
   const int v = (n & 1) ? g.N - 1 - (n >> 1) : (n >> 1);
   const int m = v >> 1;
   owner = m & (g.P - 1);
@@ -849,15 +918,22 @@ __device__ __noinline__ int build_list(const uint32_t* m) {
   return total;
 }
 
+// Omega bits of this CTA's frequency tasks on the streamed path: shared memory, or for
+// N = 2^24 (whose plan has no room left) the CTA's slice of a global table.
+__device__ __forceinline__ uint8_t* grid_fbits() {
+  return C.op.gfb ? C.op.gfb + (size_t)C.g.c * C.op.gfb_stride : shp(C.sm.fbits);
+}
+
 // Omega membership bits of every frequency task of this CTA (bit i <-> output f[i]).
 __device__ __noinline__ void build_fbits() {
   if (C.grid) {
     // one table per column block of this CTA, each of h S2 + S2 + 1 entries
     const OpDev& op = C.op;
     const int fbstride = (op.W / 2) * op.S2 + op.S2 + 1;
+    uint8_t* fb0 = grid_fbits();
     for (int j = 0; j < op.bpc; ++j) {
       const Geo gb = block_geo(op, C.g.c + j * op.G);
-      uint8_t* fb = shp(C.sm.fbits) + j * fbstride;
+      uint8_t* fb = fb0 + j * fbstride;
       const int nt = ntasks(gb);
       for (int t = threadIdx.x; t < nt; t += NT) {
         int sa, kpa, sb, kpb;
@@ -978,7 +1054,7 @@ __device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, 
 // Cluster barrier (every CTA's A is final), then the fused pull + P-point DFT into B.
 __device__ __noinline__ void exchange_fwd() {
   const Geo g = C.g;
-  const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+  const Tw tw = smem_tw();
   float2* A = shp(C.sm.A);
   float2* B = shp(C.sm.B);
   cl_sync();
@@ -1047,7 +1123,7 @@ __device__ __forceinline__ void dct3_pair(const float* X, int k, bool self, cons
 template <bool MASK>
 __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, const int4* rank4, int kind,
                                            bool fwd_done, bool inv, const float* vin, float* vout) {
-  const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+  const Tw tw = smem_tw();
   const uint32_t* omask = C.omask;
   const int32_t* orank = C.orank;
   const int F = g.F, S2 = g.S2;
@@ -1155,7 +1231,7 @@ __device__ __forceinline__ float freq_half(int kind, bool fwd_done, bool inv, co
 // FFT reads A.
 __device__ __noinline__ void exchange_inv() {
   const Geo g = C.g;
-  const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+  const Tw tw = smem_tw();
   float2* A = shp(C.sm.A);
   float2* B = shp(C.sm.B);
   const int F = g.F, S2 = g.S2;
@@ -1243,7 +1319,8 @@ __device__ __noinline__ void col_fft(float2* X, float2* Y, int Lc, int lw, Tw tw
     case 7: col_plan<7, DIR>(X, Y, lw, tw, four_n); break;
     case 8: col_plan<8, DIR>(X, Y, lw, tw, four_n); break;
     case 9: col_plan<9, DIR>(X, Y, lw, tw, four_n); break;
-    default: col_plan<10, DIR>(X, Y, lw, tw, four_n); break;
+    case 10: col_plan<10, DIR>(X, Y, lw, tw, four_n); break;
+    default: col_plan<11, DIR>(X, Y, lw, tw, four_n); break;
   }
 }
 
@@ -1280,7 +1357,7 @@ __device__ __noinline__ void grid_row_forward(int lr, int src, int nloc, const f
   __syncthreads();
   local_fft<-1>(C.sm.A, C.sm.B, S1, C.tw, g.four_n);
   {
-    const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+    const Tw tw = smem_tw();
     float2* row = C.op.gY + (size_t)n2 * S1;
     float2 w = tw.get<-1>(8 * n2 * (int)threadIdx.x);
     const float2 step = tw.get<-1>(8 * n2 * NT);
@@ -1315,7 +1392,7 @@ __device__ __noinline__ float grid_col_block(int j, int kind, bool fwd_done, boo
     col_fft<-1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
   }
   const int fbstride = (W / 2) * S2 + S2 + 1;
-  const uint8_t* fbj = shp(C.sm.fbits) + j * fbstride;
+  const uint8_t* fbj = grid_fbits() + j * fbstride;
   const float acc = kind == MID_MASK ? freq_core<true>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout)
                                      : freq_core<false>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout);
   __syncthreads();
@@ -1337,7 +1414,7 @@ __device__ __noinline__ void grid_row_inverse(int lr) {
   const int S1 = C.op.S1, n2 = g.c + lr * C.op.G;
   float2* X = shp(C.sm.A);
   {
-    const Tw tw = {shp(C.sm.twlo), shp(C.sm.twhi), C.tw.lo_bits, C.tw.lo_mask, C.tw.mask4n};
+    const Tw tw = smem_tw();
     const float2* row = C.op.gY + (size_t)n2 * S1;
     float2 w = tw.get<1>(8 * n2 * (int)threadIdx.x);
     const float2 step = tw.get<1>(8 * n2 * NT);
@@ -1374,6 +1451,158 @@ __device__ __noinline__ float transform_grid(int src, int nloc, const float* den
   return acc;
 }
 
+// ------------------------------------------------ any-N transform (one CTA, natural order)
+// For N not a power of two (16 <= N <= N_MAX_ANY) one CTA holds the signal in natural order
+// (slot sigma = signal index sigma) and computes the orthonormal DCT-II and DCT-III as chirp-z
+// transforms (Bluestein 1970).  With W = exp(-i pi / N) and the chirp c_m = exp(i pi m^2 / 2N),
+//   sum_n a_n W^{nk} = conj(c_k) sum_n (a_n conj(c_n)) c_{k-n}    (0 <= n, k < N),
+// a linear convolution done by power-of-two FFTs of czt_n >= 2N - 1 points against a table
+// holding the FFT of the chirp kernel (scaled by 1 / czt_n).  Then, with omega = omega_{4N},
+//   DCT-II:  X_k = w_k Re(omega^k sum_n x_n W^{nk}),
+//   DCT-III: x_n = Re(sum_k (w_k X_k omega^k) W^{kn}),
+// and conj(c_m) = omega^{m^2 mod 4N} comes from the operator's omega_{4N} table.
+__device__ __forceinline__ int sq_mod(int m, int four_n) { return (int)(((long long)m * m) % four_n); }
+
+// A <- IFFT(FFT(A) . hat): the chirp-z convolution (B is scratch; the result lands in A).
+__device__ __noinline__ void czt_conv() {
+  local_fft<-1>(C.sm.A, C.sm.B, C.czt_n, C.tw2, 4 * C.czt_n);
+  float2* A = shp(C.sm.A);
+  const float2* hat = C.czt_hat;
+  for (int k = threadIdx.x; k < C.czt_n; k += NT) A[aidx(k)] = cmul(A[aidx(k)], __ldg(hat + k));
+  __syncthreads();
+  local_fft<1>(C.sm.A, C.sm.B, C.czt_n, C.tw2, 4 * C.czt_n);
+}
+
+// One chirp-z DCT stage over A, whose entries' real parts hold N real values (k < N) on entry
+// and on exit: TO_FREQ applies the DCT-II, TO_TIME the DCT-III.
+enum CztDir : int { TO_FREQ = 0, TO_TIME = 1 };
+__device__ __noinline__ void czt_stage(int dir) {
+  const int N = C.g.N, Lc = C.czt_n, four_n = C.g.four_n;
+  const float wk = sqrtf(2.0f / (float)N), w0 = sqrtf(1.0f / (float)N);
+  {
+    float2* A = shp(C.sm.A);
+    const Tw tw = smem_tw();
+    for (int k = threadIdx.x; k < Lc; k += NT) {
+      float2 a = make_float2(0.f, 0.f);
+      if (k < N) {
+        const float v = A[aidx(k)].x;
+        const float2 cc = tw.get<-1>(sq_mod(k, four_n));                  // conj(c_k)
+        a = dir == TO_FREQ ? cscale(cc, v) : cscale(cmul(tw.get<-1>(k), cc), (k == 0 ? w0 : wk) * v);
+      }
+      A[aidx(k)] = a;
+    }
+    __syncthreads();
+  }
+  czt_conv();
+  float2* A = shp(C.sm.A);
+  const Tw tw = smem_tw();
+  for (int k = threadIdx.x; k < N; k += NT) {
+    const float2 o = cmul(tw.get<-1>(sq_mod(k, four_n)), A[aidx(k)]);     // conj(c_k) conv_k
+    float v;
+    if (dir == TO_FREQ) {
+      const float2 om = tw.get<-1>(k);
+      v = (k == 0 ? w0 : wk) * fmaf(om.x, o.x, -om.y * o.y);              // w_k Re(omega^k o)
+    } else {
+      v = o.x;
+    }
+    A[aidx(k)] = make_float2(v, 0.f);
+  }
+  __syncthreads();
+}
+
+// The sign flip d between the sparsifying basis and the DCT (operators with a basis Psi; the
+// others flip the signs on the slots).
+__device__ __noinline__ void psi_signs() {
+  float2* A = shp(C.sm.A);
+  for (int n = threadIdx.x; n < C.g.N; n += NT) {
+    const uint64_t h = mix64(C.op.sign_key + (uint64_t)n + 0x9E3779B97F4A7C15ull);
+    if (h >> 63) A[aidx(n)].x = -A[aidx(n)].x;
+  }
+  __syncthreads();
+}
+
+// x -> C d x (no basis) or C d Psi x (basis Psi = C^T): the forward operator before the rows are
+// picked, on the real parts of A.
+__device__ __forceinline__ void generic_forward() {
+  if (C.op.psi) {
+    czt_stage(TO_TIME);
+    psi_signs();
+  }
+  czt_stage(TO_FREQ);
+}
+// The transpose: C^T (no basis; the slot signs are applied by the readers) or Psi^T d C^T.
+__device__ __forceinline__ void generic_inverse() {
+  czt_stage(TO_TIME);
+  if (C.op.psi) {
+    psi_signs();
+    czt_stage(TO_FREQ);
+  }
+}
+
+__device__ __noinline__ float transform_generic(int src, int nloc, const float* dense, const float* gin, int kind,
+                                                bool inv, const float* vin, float* vout, bool fuse) {
+  const int N = C.g.N, Lc = C.czt_n;
+  if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
+  if (src != SRC_NONE) {
+    // the source values (times the slot signs d, which are all +1 with a basis) into A
+    float2* A = shp(C.sm.A);
+    const uint32_t* signw = shp(C.sm.signw);
+    for (int n = threadIdx.x; n < Lc; n += NT) A[aidx(n)] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (src == SRC_GLOBAL_N) {
+      for (int n = threadIdx.x; n < N; n += NT) A[aidx(n)].x = __ldg(gin + sig_of_slot(C.g, n)) * sgn_bits(signw, n);
+    } else {
+      const int* list = C.list;
+      const float* vals = C.cgp;
+      for (int i = threadIdx.x; i < nloc; i += NT) {
+        const int n = list[i];
+        A[aidx(n)].x = (src == SRC_CG ? vals[i] : dense[n]) * sgn_bits(signw, n);
+      }
+    }
+    __syncthreads();
+    generic_forward();
+  }
+  // the Omega step on X_k = A[k].x (0 when the forward input is zero)
+  float acc = 0.f;
+  {
+    float2* A = shp(C.sm.A);
+    const uint32_t* omask = C.omask;
+    const int32_t* orank = C.orank;
+    for (int k = threadIdx.x; k < N; k += NT) {
+      float X = src != SRC_NONE ? A[aidx(k)].x : 0.f;
+      const uint32_t wd = omask[k >> 5];
+      const bool in = (wd >> (k & 31)) & 1u;
+      const int rk = in ? orank[k >> 5] + __popc(wd & ((1u << (k & 31)) - 1u)) : -1;
+      if (kind == MID_MASK) {
+        X = in ? X : 0.f;
+        acc = fmaf(X, X, acc);
+      } else if (kind == MID_RESID) {
+        X = in ? __ldg(vin + rk) - X : 0.f;
+        acc = fmaf(X, X, acc);
+      } else if (kind == MID_OUT) {
+        if (in) vout[rk] = X;
+      } else {   // MID_IN
+        X = in ? __ldg(vin + rk) : 0.f;
+      }
+      A[aidx(k)] = make_float2(X, 0.f);
+    }
+    __syncthreads();
+  }
+  if (inv) {
+    generic_inverse();
+    const float2* A = shp(C.sm.A);
+    float* S = reinterpret_cast<float*>(shp(C.sm.S));
+    for (int n = threadIdx.x; n < 2 * C.g.F; n += NT) S[2 * aidx(n >> 1) + (n & 1)] = n < N ? A[aidx(n)].x : 0.f;
+    __syncthreads();
+  }
+  if (fuse) {
+    const int slot = reduce_publish(acc);
+    __syncthreads();
+    return reduce_collect(slot);
+  }
+  return acc;
+}
+
 // One application of A (forward), A^T (inverse) or A^T mask A, driven by src / kind.
 //   src   SRC_NONE: the forward input is zero (skip the forward transform)
 //         SRC_CG: compressed CG vector cgp on the local list (nloc entries)
@@ -1389,6 +1618,7 @@ __device__ __noinline__ float transform_grid(int src, int nloc, const float* den
 __device__ __noinline__ float transform(int src, int nloc, const float* dense, const float* gin, int kind,
                                         bool inv, const float* vin, float* vout, bool fuse = false) {
   if (C.grid) return transform_grid(src, nloc, dense, gin, kind, inv, vin, vout, fuse);
+  if (C.gen) return transform_generic(src, nloc, dense, gin, kind, inv, vin, vout, fuse);
   // Each step is its own call and this function holds almost nothing live across them, so
   // every step gets the full register budget (ptxas allocates registers across calls).
   if (threadIdx.x == 0) C.ntrans += (src != SRC_NONE ? 1 : 0) + (inv ? 1 : 0);
@@ -1820,7 +2050,7 @@ __device__ __noinline__ void topk_corr(int K, const uint32_t* excl, uint32_t* ds
   const Geo g = C.g;
   const SigView A = sigview();
   select_topk(
-      2 * g.F, K,
+      C.nslots, K,
       [&](int sg) -> uint32_t {
         if (excl && mask_bit(excl, sg)) return 0u;
         return abs_key(A.at(sg));
@@ -1836,7 +2066,7 @@ __device__ __noinline__ int omp_select(uint32_t* mA) {
   const Geo g = C.g;
   const SigView A = sigview();
   unsigned long long key = 0;
-  for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+  for (int sg = threadIdx.x; sg < C.nslots; sg += NT) {
     if (mask_bit(mA, sg)) continue;
     const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) |
                                   (0xffffffffu - (uint32_t)sig_of_slot(g, sg));
@@ -1848,7 +2078,7 @@ __device__ __noinline__ int omp_select(uint32_t* mA) {
   if (C.want_margins) {
     // runner-up over the same candidates: margin (a_(1) - a_(2)) / a_(1)
     unsigned long long k2 = 0;
-    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+    for (int sg = threadIdx.x; sg < C.nslots; sg += NT) {
       if (mask_bit(mA, sg)) continue;
       const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) |
                                     (0xffffffffu - (uint32_t)sig_of_slot(g, sg));
@@ -2011,7 +2241,7 @@ __device__ __noinline__ bool ompr_swap() {
   uint32_t* mA = shp(C.sm.mask[0]);
   unsigned long long key[2] = {0ull, 0ull};
   const float* xd = C.xd[0];
-  for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+  for (int sg = threadIdx.x; sg < C.nslots; sg += NT) {
     const uint32_t lo = 0xffffffffu - (uint32_t)sig_of_slot(g, sg);
     if (mask_bit(mA, sg)) {
       const float z = xd[sg] + corr_at(A, signw, sg);
@@ -2032,7 +2262,7 @@ __device__ __noinline__ bool ompr_swap() {
   if (C.want_margins && key[0] != 0ull && key[1] != 0ull) {
     // runners-up: the second largest |z| outside S and the second smallest inside
     unsigned long long k2[2] = {0ull, 0ull};
-    for (int sg = threadIdx.x; sg < 2 * g.F; sg += NT) {
+    for (int sg = threadIdx.x; sg < C.nslots; sg += NT) {
       const uint32_t lo = 0xffffffffu - (uint32_t)sig_of_slot(g, sg);
       if (mask_bit(mA, sg)) {
         const float z = xd[sg] + corr_at(A, signw, sg);
@@ -2196,7 +2426,11 @@ __device__ __noinline__ void run_ls_backward(const Task& t) {
 // allocates registers across calls: whatever a caller holds live is denied to its callees).
 __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc) {
   const OpDev& op = tp->op;
-  if (op.P != P || op.F > F_alloc || op.grid != C.grid) {   // host grouping error: skip uniformly
+  const bool plan_ok = op.generic ? (C.plan.slot_n >= apad(op.F) && C.plan.fft_n >= op.czt_n &&
+                                     C.plan.tw_hi_n >= (1 << op.hi_bits) && C.plan.tw2_lo_n >= (1 << op.tw2_lo_bits) &&
+                                     C.plan.tw2_hi_n >= (1 << op.tw2_hi_bits))
+                                  : C.plan.slot_n == 0;
+  if (op.P != P || op.F > F_alloc || op.grid != C.grid || !plan_ok) {   // host grouping error: skip uniformly
     if (c == 0 && threadIdx.x == 0 && tp->stats) tp->stats->status = CS_ERR_INVALID_ARG;
     return;
   }
@@ -2209,6 +2443,11 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     Geo& g = C.g;
     g.N = op.N; g.L = op.N >> 1; g.P = P; g.F = op.F; g.c = c;
     g.h = op.F / (2 * P); g.lh = __ffs(g.h) - 1; g.S2 = 2 * g.h; g.four_n = 4 * op.N;
+    g.nat = op.generic;
+    C.gen = op.generic;
+    C.nslots = op.generic ? op.N : 2 * op.F;
+    C.czt_n = op.czt_n;
+    C.czt_hat = op.czt_hat;
     C.op = op;
     if (C.grid) {
       // CTA c owns rows c + lr G (lr < R); slot q = n1 R + lr is point m = q G + c, as in a
@@ -2237,7 +2476,14 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     C.list = C.glist;
     C.cgx = C.gcg; C.cgr = C.gcg + a; C.cgp = C.gcg + 2 * a; C.cgq = C.gcg + 3 * a;
     C.tw.lo = C.sm.twlo; C.tw.hi = C.sm.twhi; C.tw.lo_bits = op.lo_bits; C.tw.lo_mask = nlo - 1;
-    C.tw.mask4n = g.four_n - 1;
+    C.tw.mask4n = op.generic ? 0x7fffffff : g.four_n - 1;   // any-N: 4N is no power of two, every index is < 4N
+    C.tw.qbits = op.tw_quarter ? __ffs(op.N) - 1 : 31;
+    C.tw.qmask = op.tw_quarter ? op.N - 1 : 0x7fffffff;
+    if (op.generic) {   // the chirp-z FFT's own table, omega_{4 czt_n}
+      C.tw2.lo = C.sm.tw2lo; C.tw2.hi = C.sm.tw2hi; C.tw2.lo_bits = op.tw2_lo_bits;
+      C.tw2.lo_mask = (1 << op.tw2_lo_bits) - 1; C.tw2.mask4n = 4 * op.czt_n - 1;
+      C.tw2.qbits = 31; C.tw2.qmask = 0x7fffffff;
+    }
   }
   __syncthreads();
   if (!loaded) {
@@ -2246,6 +2492,13 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     float2* twhi = shp(C.sm.twhi);
     for (int i = threadIdx.x; i < nlo; i += NT) twlo[aidx(i)] = op.tw[i];
     for (int i = threadIdx.x; i < nhi; i += NT) twhi[i] = op.tw[nlo + i];
+    if (op.generic) {
+      float2* t2l = shp(C.sm.tw2lo);
+      float2* t2h = shp(C.sm.tw2hi);
+      const int n2l = 1 << op.tw2_lo_bits, n2h = 1 << op.tw2_hi_bits;
+      for (int i = threadIdx.x; i < n2l; i += NT) t2l[aidx(i)] = op.tw2[i];
+      for (int i = threadIdx.x; i < n2h; i += NT) t2h[i] = op.tw2[n2l + i];
+    }
     uint32_t* signw = shp(C.sm.signw);
     const Geo gg = C.g;
     const int nwords = C.nwords;
@@ -2255,13 +2508,13 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
         const int sg = 32 * w + b;
         if (sg < 2 * op.F) {
           const uint64_t hsh = mix64(op.sign_key + (uint64_t)n_of_slot(gg, sg) + 0x9E3779B97F4A7C15ull);
-          if (!op.perm) bitsw |= (uint32_t)(hsh >> 63) << b;   // the permutation randomiser has no signs
+          if (!op.perm && !op.psi) bitsw |= (uint32_t)(hsh >> 63) << b;   // permutation / basis: no slot signs
         }
       }
       signw[w] = bitsw;
     }
     __syncthreads();
-    build_fbits();
+    if (!op.generic) build_fbits();   // the any-N path reads Omega directly
     if (threadIdx.x == 0) C.setup_key = (const void*)op.omask;
   }
   const Task& t = *tp;
@@ -2274,7 +2527,7 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
       const SigView A = sigview();
       const uint32_t* signw = shp(C.sm.signw);
       const Geo gg = C.g;
-      for (int sg = threadIdx.x; sg < 2 * gg.F; sg += NT) t.out[sig_of_slot(gg, sg)] = corr_at(A, signw, sg);
+      for (int sg = threadIdx.x; sg < C.nslots; sg += NT) t.out[sig_of_slot(gg, sg)] = corr_at(A, signw, sg);
       break;
     }
     case MODE_RECOVER:
@@ -2297,6 +2550,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const Launch lp) {
   const int ncl = gridDim.x / P;
   if (threadIdx.x == 0) {
     C.sm = carve(lp.plan);
+    C.plan = lp.plan;
     C.grid = 0;
     C.ring_slot = 0;
     C.hist_slot = 0;
@@ -2342,6 +2596,7 @@ __global__ void __launch_bounds__(NT, 1) grid_kernel(const Launch lp) {
   const int c = blockIdx.x;
   if (threadIdx.x == 0) {
     C.sm = carve(lp.plan);
+    C.plan = lp.plan;
     C.grid = 1;
     C.ring_slot = 0;
     C.hist_slot = 0;
@@ -2388,8 +2643,10 @@ cudaError_t launch_engine(const Launch& L, int P, int num_clusters, cudaStream_t
   return cudaLaunchKernelEx(&cfg, engine_kernel, L);
 }
 
-int max_active_clusters(int P, int F_alloc) {
-  const size_t smem = smem_bytes(cluster_plan(F_alloc));
+int max_active_clusters(int P, int F_alloc) { return max_active_plan(P, cluster_plan(F_alloc)); }
+
+int max_active_plan(int P, const SmemPlan& plan) {
+  const size_t smem = smem_bytes(plan);
   if (cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   if (P > 8 && cudaFuncSetAttribute(engine_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
@@ -2674,7 +2931,8 @@ __device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, 
   float2* R1 = R0 + apad(F);
   float2* TB = R1 + apad(F);
   const OpDev& op = a.op;
-  const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1};
+  const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1,
+                 31, 0x7fffffff};
   Geo g;
   g.N = op.N; g.L = op.N >> 1; g.P = op.P; g.F = F; g.c = 0; g.h = 0; g.lh = 0; g.S2 = 0; g.four_n = 4 * op.N;
   const int rs = apad(F);
@@ -2726,7 +2984,8 @@ __device__ __noinline__ void stream_cols(const StreamArgs& a, int b, float2* T, 
   constexpr int F = STREAM_F;
   const OpDev& op = a.op;
   float2* TB = reinterpret_cast<float2*>(smem_raw) + 2 * apad(F);
-  const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1};
+  const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1,
+                 31, 0x7fffffff};
   if (a.mode == MODE_APPLY)
     stream_cols_fwd<PT>(reinterpret_cast<const float4*>(a.in + (size_t)b * op.N), a.dbits, T, tw, rot, c, nc);
   else

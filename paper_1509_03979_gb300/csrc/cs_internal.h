@@ -21,7 +21,8 @@ constexpr int SCRATCH_ARRAYS = 8;   // per-CTA global arrays of 2F words (see Sc
 constexpr int GRID_S1 = 4096;
 constexpr int GRID_G_MAX = 128;
 constexpr int GRID_BLOCK = 4096;    // complex points per column block (W = GRID_BLOCK / S2)
-constexpr int N_MAX_GRID = 1 << 23;   // 2^23: the streamed plan's 225 KB of shared memory per CTA
+constexpr int N_MAX_GRID = 1 << 24;   // 2^24: with the quarter-period twiddle table and global Omega task bits
+constexpr int N_TW_QUARTER = 1 << 24;  // from this N on the twiddle table covers a quarter period
 
 // Shared-memory sizing of one launch.
 struct SmemPlan {
@@ -31,6 +32,9 @@ struct SmemPlan {
   int slot_words;   // 32-bit words of each per-slot bitmask (2F slots)
   int fb_bytes;     // Omega bits of the CTA's frequency tasks
   int cg_cap;       // support entries per CTA whose list and CG vectors live in shared memory
+  int slot_n;       // any-N path: complex entries of the slot buffer S (0 otherwise)
+  int tw2_lo_n;     // any-N path: entries of the FFT twiddle tables (0 otherwise)
+  int tw2_hi_n;
 };
 
 enum Mode : int {
@@ -45,7 +49,8 @@ enum Mode : int {
 struct OpDev {
   int N, M;
   int P, F;                  // cluster size and complex points per CTA (P * F = N / 2)
-  int lo_bits, hi_bits;      // twiddle table split: 4N = 2^(lo_bits + hi_bits)
+  int lo_bits, hi_bits;      // twiddle table split: 4N = 2^(lo_bits + hi_bits), or N with tw_quarter
+  int tw_quarter;            // 1: the table covers omega_{4N}^j for j < N only (N >= N_TW_QUARTER)
   uint64_t sign_key;         // seed ^ 0xD1B54A32D192ED03
   const uint32_t* omask;     // [N/32] bitmask of Omega
   const int32_t* orank;      // [N/32] number of Omega members below word w
@@ -62,7 +67,17 @@ struct OpDev {
   float* gred;               // [4][G][4] reduction partials
   unsigned long long* gred64;   // [4][G][2]
   uint32_t* ghist;           // [2][G][256] radix histograms
+  uint8_t* gfb;              // [G][gfb_stride] Omega bits of the frequency tasks (N = 2^24), or null
+  int gfb_stride;
+  // any-N path (N not a power of two, N <= N_MAX_ANY): one CTA, natural order, chirp-z DCTs
+  int generic;               // 1 for this path
+  int czt_n;                 // power-of-two FFT length of the chirp-z convolution, >= 2N - 1
+  const float2* czt_hat;     // [czt_n] FFT of the chirp kernel, scaled by 1 / czt_n
+  const float2* tw2;         // [2^tw2_lo_bits] then [2^tw2_hi_bits]: omega_{4 czt_n}^j, two levels
+  int tw2_lo_bits, tw2_hi_bits;
+  int psi;                   // sparsifying basis (any-N path): 0 identity, 1 Psi = C_N^T (Sec. III-A)
 };
+constexpr int N_MAX_ANY = 4096;   // largest N (not a power of two) of the any-N path: czt_n <= F_MAX
 
 // One unit of work for a cluster.
 struct Task {
@@ -137,6 +152,9 @@ cudaError_t launch_stream(const StreamArgs& a, int nc, int clusters, cudaStream_
 cudaError_t launch_wait_probe(unsigned* flag, unsigned long long limit, int* status, cudaStream_t stream);
 
 SmemPlan cluster_plan(int F_alloc);
+SmemPlan generic_plan(int czt_n, int F_alloc, int tw_hi_n, int tw2_lo_n, int tw2_hi_n);
+SmemPlan op_plan(const OpDev& op);              // the plan a single task of this operator runs with
+int max_active_plan(int P, const SmemPlan& plan);   // clusters of P CTAs resident with this plan
 SmemPlan grid_plan(const OpDev& op);
 size_t smem_bytes(const SmemPlan& plan);
 cudaError_t launch_engine(const Launch& L, int P, int num_clusters, cudaStream_t stream);

@@ -21,7 +21,7 @@ def B():
 
 
 @pytest.mark.parametrize("N,M", [(1 << 19, 1 << 17), (1 << 20, 300000), (1 << 21, 1 << 19), (1 << 22, 1 << 20),
-                                 (1 << 23, 1 << 21)])
+                                 (1 << 23, 1 << 21), (1 << 24, 1 << 22)])
 def test_streamed_apply_and_transpose(B, N, M):
     op = B.Operator(N, M, 91)
     ref = oracle.Operator(N, M, 91)
@@ -116,3 +116,21 @@ def test_n23_recovery_properties(B, algo, K):
     assert rel(s, s_true) <= SHAT_TOL
     sS = ls.ls_cg(ref_op, S, y.astype(np.float64), tol=1e-12)
     assert rel(s[S], sS) <= SHAT_TOL
+
+
+@pytest.mark.parametrize("algo,K", [("sp", 4000), ("ompr", 1000)])
+def test_n24_recovery_properties(B, algo, K):
+    """N = 2^24, the largest size of the paper's Tables III-IV (quarter-period twiddle table and
+    global Omega task bits on the streamed path), M = N/4, noiseless K-sparse Gaussian signal:
+    exact recovery -- the returned support is the true one and s_hat is within 1e-4 of it (on
+    the true support of a noiseless y the least-squares solution is the signal itself)."""
+    N, M = 1 << 24, 1 << 22
+    ref_op = oracle.Operator(N, M, 0x24001)
+    s_true = synth.sparse_gaussian(N, K, 0x24002)
+    y = ref_op.apply(s_true).astype(np.float32)
+    op = B.Operator(N, M, 0x24001)
+    s, supp = op.recover(to_dev(y), K, algo, 1e-6, 200)
+    st = op.stats()
+    assert st["status"] == 0
+    assert np.array_equal(supp.cpu().numpy().astype(np.int64), np.flatnonzero(s_true))
+    assert rel(s.cpu().numpy(), s_true) <= SHAT_TOL

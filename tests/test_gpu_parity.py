@@ -123,4 +123,4 @@ def test_invalid_arguments_raise(B):
     with pytest.raises(RuntimeError):
         op.recover(y, 300, "omp")         # K > M
     with pytest.raises(RuntimeError):
-        B.Operator(1 << 24, 10, 1)        # N beyond the streamed path
+        B.Operator(1 << 25, 10, 1)        # N beyond the streamed path

@@ -39,14 +39,15 @@ def test_exports_every_declared_symbol(lib):
 
 
 @pytest.mark.parametrize("N,M,seed", [(16, 8, 1), (4096, 1024, 0x0C5001), (1 << 14, 1 << 12, 99),
-                                      (1 << 18, 1 << 16, 0x0C5002)])
+                                      (1 << 18, 1 << 16, 0x0C5002), (1000, 300, 5), (999, 333, 6), (4095, 17, 7)])
 def test_operator_draws_match_oracle(lib, N, M, seed):
     om, d = binding.operator_draws(N, M, seed)
     assert np.array_equal(om.astype(np.int64), rng.omega(N, M, seed))
     assert np.array_equal(d.astype(np.float64), rng.signs(N, seed))
 
 
-@pytest.mark.parametrize("N,M,code", [(24, 8, 2), (8, 4, 2), (1 << 24, 8, 2), (64, 0, 1), (64, 65, 1)])
+@pytest.mark.parametrize("N,M,code", [(4097, 8, 2), (8, 4, 2), (1 << 25, 8, 2), (3 << 20, 8, 2), (64, 0, 1),
+                                      (64, 65, 1), (1000, 1001, 1)])
 def test_invalid_sizes_rejected_without_gpu(lib, N, M, code):
     om = np.zeros(max(M, 1), dtype=np.int32)
     st = lib.cs_operator_draws(N, M, 1, om.ctypes.data_as(ctypes.c_void_p), None)
