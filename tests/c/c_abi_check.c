@@ -24,7 +24,7 @@ int main(int argc, char** argv) {
     if (d[n] != 1 && d[n] != -1) return 1;
   if (cs_operator_perm(N, 7u, perm) != CS_OK) return 1;
   /* an unsupported size is refused with a message */
-  if (cs_operator_draws(24, 8, 1u, omega, NULL) != CS_ERR_UNSUPPORTED_N || strlen(cs_last_error()) == 0) return 1;
+  if (cs_operator_draws(4097, 8, 1u, omega, NULL) != CS_ERR_UNSUPPORTED_N || strlen(cs_last_error()) == 0) return 1;
   if (cs_launch_count() < 0) return 1;
   printf("omega[0]=%d omega[M-1]=%d d[0]=%d perm[0]=%d launches=%lld\n", (int)omega[0], (int)omega[M - 1], (int)d[0],
          (int)perm[0], (long long)cs_launch_count());
