@@ -107,12 +107,14 @@ cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer)
  * the basis; the image experiment of Sec. IV-A takes a DCT basis): A = P_Omega C_N diag(d) Psi,
  * the unknown s holds the basis coefficients of x = Psi s, and every entry point recovers,
  * solves and differentiates in s.  CS_BASIS_IDENTITY is cs_op_create's operator;
- * CS_BASIS_DCT is Psi = C_N^T (s = the orthonormal DCT-II coefficients of x), for
- * 16 <= N <= 4096 (else CS_ERR_UNSUPPORTED_N) with the sign randomiser d.  Psi is orthonormal,
- * so A A^T = I_M still holds.  Such operators run on the any-N path (one CTA, chirp-z DCTs),
- * whatever N is.  Returns NULL on failure. */
-enum { CS_BASIS_IDENTITY = 0, CS_BASIS_DCT = 1 };
-cs_op_t cs_op_create_basis(int64_t N, int64_t M, uint64_t seed, int32_t basis);
+ * CS_BASIS_DCT is Psi = C_N^T (s = the orthonormal DCT-II coefficients of x); CS_BASIS_DCT2D is
+ * the separable 2-D basis Psi_2 (x) Psi_1 of an n1 x n2 image stored row-major (x = C_{n1}^T S
+ * C_{n2} for the n1 x n2 coefficient array S; n1 >= 2 divides N, n2 = N / n1 >= 2; n1 is
+ * ignored for the other bases).  A basis needs 16 <= N <= 4096 (else CS_ERR_UNSUPPORTED_N) and
+ * takes the sign randomiser d.  Psi is orthonormal, so A A^T = I_M still holds.  Such operators
+ * run on the any-N path (one CTA, chirp-z DCTs), whatever N is.  Returns NULL on failure. */
+enum { CS_BASIS_IDENTITY = 0, CS_BASIS_DCT = 1, CS_BASIS_DCT2D = 2 };
+cs_op_t cs_op_create_basis(int64_t N, int64_t M, uint64_t seed, int32_t basis, int32_t n1);
 
 /* Host-only draw of the permutation randomiser for (N, seed) into perm_N_host [N] HOST. */
 cs_status cs_operator_perm(int64_t N, uint64_t seed, int32_t* perm_N_host);

@@ -33,7 +33,7 @@ _I64, _U64, _I32, _F32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes
 SIGNATURES = {
     "cs_op_create": (_P, [_I64, _I64, _U64]),
     "cs_op_create_ex": (_P, [_I64, _I64, _U64, _I32]),
-    "cs_op_create_basis": (_P, [_I64, _I64, _U64, _I32]),
+    "cs_op_create_basis": (_P, [_I64, _I64, _U64, _I32, _I32]),
     "cs_operator_perm": (_I32, [_I64, _U64, _P]),
     "cs_op_export_perm": (_I32, [_P, _P]),
     "cs_op_destroy": (None, [_P]),
@@ -119,18 +119,22 @@ class Operator:
     """A = P_Omega C_N diag(d) on the current CUDA device (Sec. III-A, Eq. 7)."""
 
     RANDOMIZERS = {"signs": 0, "perm": 1}
-    BASES = {None: 0, "dct": 1}
+    BASES = {None: 0, "dct": 1, "dct2d": 2}
 
     def __init__(self, N, M, seed, randomizer="signs", psi=None):
         """randomizer: 'signs' (R = diag(d), the default) or 'perm' (R a random permutation);
-        psi: None (s sparse itself) or 'dct' (s the DCT coefficients of x = C_N^T s)."""
+        psi: None (s sparse itself), 'dct' (s the DCT coefficients of x = C_N^T s) or
+        ('dct2d', n1, n2) (s the 2-D DCT coefficients of an n1 x n2 row-major image)."""
         self.N, self.M, self.seed = int(N), int(M), int(seed)
         self.randomizer = randomizer
         self.psi = psi
         if psi is not None:
             if randomizer != "signs":
                 raise ValueError("a sparsifying basis takes the sign randomiser")
-            h = lib().cs_op_create_basis(self.N, self.M, self.seed, self.BASES[psi])
+            kind, n1 = (psi, 0) if psi == "dct" else (psi[0], int(psi[1]))
+            if kind == "dct2d" and n1 * int(psi[2]) != self.N:
+                raise ValueError("psi=('dct2d', n1, n2) needs n1 n2 = N")
+            h = lib().cs_op_create_basis(self.N, self.M, self.seed, self.BASES[kind], n1)
         else:
             h = lib().cs_op_create_ex(self.N, self.M, self.seed, self.RANDOMIZERS[randomizer])
         if not h:

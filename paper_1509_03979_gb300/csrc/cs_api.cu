@@ -292,14 +292,14 @@ cs_status cs_operator_perm(int64_t N, uint64_t seed, int32_t* perm_N_host) {
 
 cs_op_t cs_op_create(int64_t N, int64_t M, uint64_t seed) { return cs_op_create_ex(N, M, seed, CS_RANDOMIZER_SIGNS); }
 
-static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer, int32_t basis);
+static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer, int32_t basis, int32_t n1);
 
 cs_op_t cs_op_create_ex(int64_t N, int64_t M, uint64_t seed, int32_t randomizer) {
-  return create_op(N, M, seed, randomizer, CS_BASIS_IDENTITY);
+  return create_op(N, M, seed, randomizer, CS_BASIS_IDENTITY, 0);
 }
 
-cs_op_t cs_op_create_basis(int64_t N, int64_t M, uint64_t seed, int32_t basis) {
-  if (basis != CS_BASIS_IDENTITY && basis != CS_BASIS_DCT) {
+cs_op_t cs_op_create_basis(int64_t N, int64_t M, uint64_t seed, int32_t basis, int32_t n1) {
+  if (basis != CS_BASIS_IDENTITY && basis != CS_BASIS_DCT && basis != CS_BASIS_DCT2D) {
     fail(CS_ERR_INVALID_ARG, "unknown sparsifying basis");
     return nullptr;
   }
@@ -307,10 +307,24 @@ cs_op_t cs_op_create_basis(int64_t N, int64_t M, uint64_t seed, int32_t basis) {
     fail(CS_ERR_UNSUPPORTED_N, "a sparsifying basis needs N <= 4096");
     return nullptr;
   }
-  return create_op(N, M, seed, CS_RANDOMIZER_SIGNS, basis);
+  if (basis == CS_BASIS_DCT2D && (n1 < 2 || N % n1 != 0 || N / n1 < 2)) {
+    fail(CS_ERR_INVALID_ARG, "the 2-D basis needs n1 >= 2 dividing N with N / n1 >= 2");
+    return nullptr;
+  }
+  return create_op(N, M, seed, CS_RANDOMIZER_SIGNS, basis, basis == CS_BASIS_DCT2D ? n1 : 0);
 }
 
-static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer, int32_t basis) {
+// Orthonormal DCT-II matrix C_n [n][n] (row k = frequency k) in FP64, stored as FP32.
+static std::vector<float> dct_matrix_host(int n) {
+  std::vector<float> c((size_t)n * n);
+  for (int k = 0; k < n; ++k) {
+    const double w = k == 0 ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+    for (int j = 0; j < n; ++j) c[(size_t)k * n + j] = (float)(w * std::cos(M_PI * (2.0 * j + 1.0) * k / (2.0 * n)));
+  }
+  return c;
+}
+
+static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer, int32_t basis, int32_t n1) {
   if (check_nm(N, M) != CS_OK) return nullptr;
   if (randomizer != CS_RANDOMIZER_SIGNS && randomizer != CS_RANDOMIZER_PERMUTATION) {
     fail(CS_ERR_INVALID_ARG, "unknown randomiser");
@@ -358,7 +372,7 @@ static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer
   d.grid = N > N_MAX ? 1 : 0;
   int P = 1, F = (int)L;
   d.generic = generic ? 1 : 0;
-  d.psi = basis == CS_BASIS_DCT ? 1 : 0;
+  d.psi = basis == CS_BASIS_DCT ? 1 : (basis == CS_BASIS_DCT2D ? 2 : 0);
   if (generic) {
     F = (int)((N + 1) / 2);   // 2F >= N real slots on one CTA
   } else if (d.grid) {
@@ -431,8 +445,23 @@ static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer
     for (int k = 0; k < cn; ++k)
       tab[(size_t)k] = make_float2((float)(b[(size_t)k].real() / cn), (float)(b[(size_t)k].imag() / cn));
     std::copy(tw2.begin(), tw2.end(), tab.begin() + cn);
+    if (basis == CS_BASIS_DCT2D) {   // the two small DCT-II matrices follow, as floats
+      const std::vector<float> m1 = dct_matrix_host(n1), m2 = dct_matrix_host((int)(N / n1));
+      const size_t base = tab.size();
+      tab.resize(base + (m1.size() + m2.size() + 1) / 2);
+      float* f = reinterpret_cast<float*>(tab.data() + base);
+      std::copy(m1.begin(), m1.end(), f);
+      std::copy(m2.begin(), m2.end(), f + m1.size());
+      d.n1 = n1;
+      d.n2 = (int)(N / n1);
+    }
     CSG_TRY(cudaMalloc(&op->d_czt, sizeof(float2) * tab.size()));
     CSG_TRY(cudaMemcpy(op->d_czt, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice));
+    if (basis == CS_BASIS_DCT2D) {
+      const float* f = reinterpret_cast<const float*>(op->d_czt + cn + tw2.size());
+      d.c1 = f;
+      d.c2 = f + (size_t)n1 * n1;
+    }
     d.czt_n = cn;
     d.czt_hat = op->d_czt;
     d.tw2 = op->d_czt + cn;
@@ -890,7 +919,7 @@ cs_status cs_op_set_trace(cs_op_t op, int32_t* trace_dev, int64_t words) {
 // launch is issued, so the call can return (and its host vector die) at once, and a launch
 // captured into a CUDA graph carries its own tables rather than a pointer into freed host
 // memory.  The first chunk also zeroes the dynamic-claim counter that follows the table.
-constexpr int TASK_CHUNK = 92;
+constexpr int TASK_CHUNK = (int)(31000 / sizeof(Task));   // as many tasks as fit the parameter space
 struct TaskChunk {
   Task t[TASK_CHUNK];
   int n;                     // tasks in this chunk

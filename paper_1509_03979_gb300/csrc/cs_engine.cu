@@ -121,17 +121,27 @@ __host__ __device__ constexpr int apad(int F) { return F + F / 16; }
 // Two-level twiddle table: omega_{4N}^j = exp(-2 pi i j / 4N) = lo[j & m] * hi[j >> lo_bits];
 // lo is stored with the same one-in-16 padding as the FFT buffer, which keeps the strided
 // lookups of the FFT passes and the DCT twiddles (strides 1, 4, 8) free of bank conflicts.
-// For N = 2^24 the two levels would not fit next to the streamed plan, so the table covers
-// one quarter period instead: j = q N + r with r < N, omega_{4N}^j = (-i)^q omega_{4N}^r
-// (qbits = log2 N, qmask = N - 1).  Otherwise qbits = 31 and q is always 0.
 struct Tw {
   const float2* lo;
   const float2* hi;
   int lo_bits;
   int lo_mask;
   int mask4n;   // 4N - 1
-  int qbits;    // log2 N with a quarter-period table, else 31
-  int qmask;    // N - 1 with a quarter-period table, else 0x7fffffff
+  template <int DIR>
+  __device__ __forceinline__ float2 get(int j) const {
+    j &= mask4n;
+    const float2 w = cmul(lo[aidx(j & lo_mask)], hi[j >> lo_bits]);
+    return DIR > 0 ? cconj(w) : w;
+  }
+};
+// The streamed path's table.  For N = 2^24 the two levels would not fit next to the streamed
+// plan, so the table covers one quarter period instead: j = q N + r with r < N,
+// omega_{4N}^j = (-i)^q omega_{4N}^r (qbits = log2 N, qmask = N - 1); otherwise qbits = 31 and
+// q is always 0.  Only the streamed path's functions are instantiated with it, so the fold
+// costs the on-chip paths nothing.
+struct TwQ : Tw {
+  int qbits;
+  int qmask;
   template <int DIR>
   __device__ __forceinline__ float2 get(int j) const {
     j &= mask4n;
@@ -148,8 +158,8 @@ struct Tw {
 
 // v[r] *= w^r with w = omega_{4N}^t (DIR < 0) or its conjugate; powers built from w, w^2,
 // w^4, w^8 read from the table, so every factor carries at most three rounded products.
-template <int R, int DIR>
-__device__ __forceinline__ void twiddle_powers(float2* v, const Tw& tw, int t) {
+template <int R, int DIR, class TW>
+__device__ __forceinline__ void twiddle_powers(float2* v, const TW& tw, int t) {
   const float2 w1 = tw.get<DIR>(t);
   v[1] = cmul(v[1], w1);
   if constexpr (R >= 4) {
@@ -181,8 +191,8 @@ __device__ __forceinline__ void twiddle_powers(float2* v, const Tw& tw, int t) {
 // One out-of-place Stockham pass of radix R from X to Y (padded indexing): butterfly j reads
 // X[j + r F/R], applies omega_{Ns R}^{r k} (k = j mod Ns), and writes Y[(j - k) R + k + r Ns].
 // One barrier per pass; a thread keeps one butterfly live at a time.
-template <int R, int DIR>
-__device__ __forceinline__ void fft_pass(const float2* X, float2* Y, int F, int Ns, const Tw& tw, int four_n) {
+template <int R, int DIR, class TW>
+__device__ __forceinline__ void fft_pass(const float2* X, float2* Y, int F, int Ns, const TW& tw, int four_n) {
   const int nb = F / R;
   for (int j = threadIdx.x; j < nb; j += NT) {
     float2 v[R];
@@ -203,8 +213,8 @@ __device__ __forceinline__ void fft_pass(const float2* X, float2* Y, int F, int 
 // allocation): a radix-2/4/8 pass first when log2 F is not a multiple of 4, then radix 16,
 // and when the pass count is odd the first pass runs in place through registers so that the
 // result always lands back in X.
-template <int R, int DIR>
-__device__ __forceinline__ void fft_pass_inplace(float2* X, int F, const Tw& tw, int four_n) {
+template <int R, int DIR, class TW>
+__device__ __forceinline__ void fft_pass_inplace(float2* X, int F, const TW& tw, int four_n) {
   constexpr int BPT = (F_MAX / NT) / R;
   const int nb = F / R;
   float2 v[BPT][R];
@@ -229,8 +239,8 @@ __device__ __forceinline__ void fft_pass_inplace(float2* X, int F, const Tw& tw,
   __syncthreads();
 }
 
-template <int LOGF, int DIR, int LOGNS, bool TO_Y>
-__device__ __forceinline__ void fft_rest(float2* X, float2* Y, const Tw& tw, int four_n) {
+template <int LOGF, int DIR, int LOGNS, bool TO_Y, class TW>
+__device__ __forceinline__ void fft_rest(float2* X, float2* Y, const TW& tw, int four_n) {
   // remaining passes are all radix 16; TO_Y: the next pass writes Y
   if constexpr (LOGNS < LOGF) {
     if constexpr (TO_Y) fft_pass<16, DIR>(X, Y, 1 << LOGF, 1 << LOGNS, tw, four_n);
@@ -239,8 +249,8 @@ __device__ __forceinline__ void fft_rest(float2* X, float2* Y, const Tw& tw, int
   }
 }
 
-template <int LOGF, int DIR>
-__device__ __forceinline__ void fft_plan(float2* X, float2* Y, const Tw& tw, int four_n) {
+template <int LOGF, int DIR, class TW>
+__device__ __forceinline__ void fft_plan(float2* X, float2* Y, const TW& tw, int four_n) {
   constexpr int HEAD = LOGF % 4;                       // bits of the leading small-radix pass
   constexpr int NPASS = LOGF / 4 + (HEAD ? 1 : 0);
   constexpr int R0 = HEAD == 0 ? 16 : (1 << HEAD);
@@ -255,8 +265,8 @@ __device__ __forceinline__ void fft_plan(float2* X, float2* Y, const Tw& tw, int
 }
 
 // One function per plan, so that each plan's register allocation is its own.
-template <int LOGF, int DIR>
-__device__ __noinline__ void fft_plan_call(float2* X, float2* Y, Tw tw, int four_n) {
+template <int LOGF, int DIR, class TW>
+__device__ __noinline__ void fft_plan_call(float2* X, float2* Y, TW tw, int four_n) {
   X = shp(X);
   Y = shp(Y);
   tw.lo = shp(tw.lo);
@@ -264,8 +274,8 @@ __device__ __noinline__ void fft_plan_call(float2* X, float2* Y, Tw tw, int four
   fft_plan<LOGF, DIR>(X, Y, tw, four_n);
 }
 
-template <int DIR>
-__device__ __noinline__ void local_fft(float2* X, float2* Y, int F, Tw tw, int four_n) {
+template <int DIR, class TW>
+__device__ __noinline__ void local_fft(float2* X, float2* Y, int F, TW tw, int four_n) {
   switch (__ffs(F) - 1) {
     case 1: fft_plan_call<1, DIR>(X, Y, tw, four_n); break;
     case 2: fft_plan_call<2, DIR>(X, Y, tw, four_n); break;
@@ -495,7 +505,7 @@ struct Geo {
 // barrier that every later reader passes.
 struct Ctx {
   Smem sm;
-  Tw tw;
+  TwQ tw;
   Geo g;
   int M, nwords, cap;
   const uint32_t* omask;
@@ -544,14 +554,32 @@ struct Ctx {
   const float2* czt_hat;
   Tw tw2;             // twiddles of the chirp-z FFT (omega_{4 czt_n})
   SmemPlan plan;      // the launch's shared-memory plan
+  float cg_beta;      // CG: beta of the last step, applied by the next scatter of p (cluster path)
+  int cg_fuse;        // 1 while cg_solve runs with the direction update in the scatter
 };
 __shared__ Ctx C;
 
-// The twiddle tables of the current task, addressed in shared memory.
-__device__ __forceinline__ Tw smem_tw() {
-  Tw t = C.tw;
+// The twiddle tables of the current task, addressed in shared memory: the plain table of the
+// on-chip paths (ctx_tw: generic pointers, for the FFT entry points) and the streamed path's.
+__device__ __forceinline__ Tw ctx_tw() { return static_cast<const Tw&>(C.tw); }
+__device__ __forceinline__ void smem_tw_into(Tw& t) {
+  t = static_cast<const Tw&>(C.tw);
   t.lo = shp(C.sm.twlo);
   t.hi = shp(C.sm.twhi);
+}
+__device__ __forceinline__ void smem_tw_into(TwQ& t) {
+  t = C.tw;
+  t.lo = shp(C.sm.twlo);
+  t.hi = shp(C.sm.twhi);
+}
+__device__ __forceinline__ Tw smem_tw() {
+  Tw t;
+  smem_tw_into(t);
+  return t;
+}
+__device__ __forceinline__ TwQ smem_twq() {
+  TwQ t;
+  smem_tw_into(t);
   return t;
 }
 
@@ -628,12 +656,12 @@ __device__ __forceinline__ float& slot_ref(float2* A, int sigma) {
 }
 // Signal index of local real slot sigma of CTA c: complex point m = q P + c of z, real index
 // v = 2 m + b of Makhoul's reordered sequence, v < N/2 -> n = 2 v, else n = 2 (N - 1 - v) + 1.
-__device__ __forceinline__ int n_of_slot(const Geo& g, int sigma) {
-  if (g.nat) return sigma;
+__device__ __forceinline__ int n_of_slot_pow2(const Geo& g, int sigma) {
   const int m = (sigma >> 1) * g.P + g.c;
   const int v = 2 * m + (sigma & 1);
   return v < (g.N >> 1) ? 2 * v : 2 * (g.N - 1 - v) + 1;
 }
+__device__ __forceinline__ int n_of_slot(const Geo& g, int sigma) { return g.nat ? sigma : n_of_slot_pow2(g, sigma); }
 __device__ __forceinline__ void slot_of_n(const Geo& g, int n, int& owner, int& sigma) {
   if (g.nat) {
     owner = 0;
@@ -1033,12 +1061,20 @@ __device__ __noinline__ void scatter_fwd(int src, int nloc, const float* dense, 
     for (int q = threadIdx.x; q < apad(F) / 2; q += NT) D4[q] = z4;
     __syncthreads();
     const int* list = C.list;
-    const float* vals = C.cgp;
+    float* vals = C.cgp;
+    const float* rv = C.cgr;
+    const bool upd = src == SRC_CG && C.cg_fuse;
+    const float beta = C.cg_beta;
     float* Df = reinterpret_cast<float*>(D);
     const int half = F >> 1;
     for (int i = threadIdx.x; i < nloc; i += NT) {
       const int sg = list[i];
-      const float v = (src == SRC_CG ? vals[i] : dense[sg]) * sgn_bits(signw, sg);
+      float pv = src == SRC_CG ? vals[i] : dense[sg];
+      if (upd) {   // the CG direction p = r + beta p, stored back for the step's updates
+        pv = fmaf(beta, pv, rv[i]);
+        vals[i] = pv;
+      }
+      const float v = pv * sgn_bits(signw, sg);
       if (pre2) {
         const int q = sg >> 1, b = sg & 1, j = q & (half - 1);
         atomicAdd(Df + 2 * aidx(2 * j) + b, v);
@@ -1078,7 +1114,8 @@ struct PairTw {
   float2 wkL;   // omega_{4N}^{k+L} = omega_{4N}^k e^{-i pi/4}
   float2 w4k;   // omega_{4N}^{4k} = omega_N^k
 };
-__device__ __forceinline__ PairTw pair_tw(const Tw& tw, int k) {
+template <class TW>
+__device__ __forceinline__ PairTw pair_tw(const TW& tw, int k) {
   PairTw p;
   p.wk1 = tw.get<-1>(k);
   p.wkL = cmul(p.wk1, make_float2(0.70710678118654752f, -0.70710678118654752f));
@@ -1120,10 +1157,11 @@ __device__ __forceinline__ void dct3_pair(const float* X, int k, bool self, cons
 // pre-processing back into the pair.  Returns this thread's sum of squares of the MID_RESID
 // residual y - A x on Omega, or for MID_MASK of the kept outputs A d on Omega.
 // MASK: the kind is MID_MASK (the H d step), compiled without the y-side state.
-template <bool MASK>
+template <bool MASK, class TW>
 __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, const int4* rank4, int kind,
                                            bool fwd_done, bool inv, const float* vin, float* vout) {
-  const Tw tw = smem_tw();
+  TW tw;
+  smem_tw_into(tw);
   const uint32_t* omask = C.omask;
   const int32_t* orank = C.orank;
   const int F = g.F, S2 = g.S2;
@@ -1215,7 +1253,7 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
 template <bool MASK>
 __device__ __noinline__ float freq_half_k(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
   const Geo g = C.g;
-  return freq_core<MASK>(g, shp(C.sm.B), shp(C.sm.fbits), C.rank4, kind, fwd_done, inv, vin, vout);
+  return freq_core<MASK, Tw>(g, shp(C.sm.B), shp(C.sm.fbits), C.rank4, kind, fwd_done, inv, vin, vout);
 }
 __device__ __forceinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
   return kind == MID_MASK ? freq_half_k<true>(kind, fwd_done, inv, vin, vout)
@@ -1265,7 +1303,7 @@ __device__ __noinline__ void exchange_inv() {
 
 // One out-of-place Stockham pass over the first index of a [Lc][W] array (W contiguous).
 template <int R, int DIR>
-__device__ __forceinline__ void col_pass(const float2* X, float2* Y, int Lc, int lw, int Ns, const Tw& tw, int four_n) {
+__device__ __forceinline__ void col_pass(const float2* X, float2* Y, int Lc, int lw, int Ns, const TwQ& tw, int four_n) {
   const int W = 1 << lw;
   const int nb = Lc / R;
   const int total = nb << lw;
@@ -1285,7 +1323,7 @@ __device__ __forceinline__ void col_pass(const float2* X, float2* Y, int Lc, int
 }
 
 template <int LOGL, int DIR, int LOGNS, bool TO_Y>
-__device__ __forceinline__ void col_rest(float2* X, float2* Y, int lw, const Tw& tw, int four_n) {
+__device__ __forceinline__ void col_rest(float2* X, float2* Y, int lw, const TwQ& tw, int four_n) {
   if constexpr (LOGNS < LOGL) {
     if constexpr (TO_Y) col_pass<16, DIR>(X, Y, 1 << LOGL, lw, 1 << LOGNS, tw, four_n);
     else col_pass<16, DIR>(Y, X, 1 << LOGL, lw, 1 << LOGNS, tw, four_n);
@@ -1300,7 +1338,7 @@ __device__ __forceinline__ void col_rest(float2* X, float2* Y, int lw, const Tw&
 
 // Batched FFT of length Lc = 2^LOGL along the first index of X [Lc][W]; Y is scratch.
 template <int LOGL, int DIR>
-__device__ __forceinline__ void col_plan(float2* X, float2* Y, int lw, const Tw& tw, int four_n) {
+__device__ __forceinline__ void col_plan(float2* X, float2* Y, int lw, const TwQ& tw, int four_n) {
   constexpr int HEAD = LOGL % 4;
   constexpr int R0 = HEAD == 0 ? 16 : (1 << HEAD);
   col_pass<R0, DIR>(X, Y, 1 << LOGL, lw, 1, tw, four_n);
@@ -1308,7 +1346,7 @@ __device__ __forceinline__ void col_plan(float2* X, float2* Y, int lw, const Tw&
 }
 
 template <int DIR>
-__device__ __noinline__ void col_fft(float2* X, float2* Y, int Lc, int lw, Tw tw, int four_n) {
+__device__ __noinline__ void col_fft(float2* X, float2* Y, int Lc, int lw, TwQ tw, int four_n) {
   X = shp(X);
   Y = shp(Y);
   tw.lo = shp(tw.lo);
@@ -1355,9 +1393,9 @@ __device__ __noinline__ void grid_row_forward(int lr, int src, int nloc, const f
     }
   }
   __syncthreads();
-  local_fft<-1>(C.sm.A, C.sm.B, S1, C.tw, g.four_n);
+  fft_plan_call<GRID_LOG_S1, -1>(C.sm.A, C.sm.B, C.tw, g.four_n);   // S1 = GRID_S1
   {
-    const Tw tw = smem_tw();
+    const TwQ tw = smem_twq();
     float2* row = C.op.gY + (size_t)n2 * S1;
     float2 w = tw.get<-1>(8 * n2 * (int)threadIdx.x);
     const float2 step = tw.get<-1>(8 * n2 * NT);
@@ -1393,8 +1431,8 @@ __device__ __noinline__ float grid_col_block(int j, int kind, bool fwd_done, boo
   }
   const int fbstride = (W / 2) * S2 + S2 + 1;
   const uint8_t* fbj = grid_fbits() + j * fbstride;
-  const float acc = kind == MID_MASK ? freq_core<true>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout)
-                                     : freq_core<false>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout);
+  const float acc = kind == MID_MASK ? freq_core<true, TwQ>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout)
+                                     : freq_core<false, TwQ>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout);
   __syncthreads();
   if (inv) {
     col_fft<1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);
@@ -1414,7 +1452,7 @@ __device__ __noinline__ void grid_row_inverse(int lr) {
   const int S1 = C.op.S1, n2 = g.c + lr * C.op.G;
   float2* X = shp(C.sm.A);
   {
-    const Tw tw = smem_tw();
+    const TwQ tw = smem_twq();
     const float2* row = C.op.gY + (size_t)n2 * S1;
     float2 w = tw.get<1>(8 * n2 * (int)threadIdx.x);
     const float2 step = tw.get<1>(8 * n2 * NT);
@@ -1429,7 +1467,7 @@ __device__ __noinline__ void grid_row_inverse(int lr) {
     }
   }
   __syncthreads();
-  local_fft<1>(C.sm.A, C.sm.B, S1, C.tw, g.four_n);
+  fft_plan_call<GRID_LOG_S1, 1>(C.sm.A, C.sm.B, C.tw, g.four_n);
   float2* sig = C.sig + (size_t)lr * C.rowstride;
   for (int n1 = threadIdx.x; n1 < S1; n1 += NT) sig[aidx(n1)] = X[aidx(n1)];
   __syncthreads();
@@ -1521,11 +1559,42 @@ __device__ __noinline__ void psi_signs() {
   __syncthreads();
 }
 
-// x -> C d x (no basis) or C d Psi x (basis Psi = C^T): the forward operator before the rows are
-// picked, on the real parts of A.
+// The separable 2-D basis on the real parts of A, read as an n1 x n2 row-major array S:
+// TO_TIME applies Psi, S -> C_{n1}^T S C_{n2} (a DCT-III along every row, then every column);
+// TO_FREQ applies Psi^T, x -> C_{n1} x C_{n2}^T.  Dense products with the two small DCT-II
+// matrices (n1 n2 (n1 + n2) multiply-adds), the real parts of B as the intermediate.
+__device__ __noinline__ void psi2d_stage(int dir) {
+  const int n1 = C.op.n1, n2 = C.op.n2, N = C.g.N;
+  const float* c1 = C.op.c1;
+  const float* c2 = C.op.c2;
+  float2* A = shp(C.sm.A);
+  float2* B = shp(C.sm.B);
+  // rows: T[a][j] = sum_b S[a][b] C2[b][j] (DCT-III) or sum_b S[a][b] C2[j][b] (DCT-II)
+  for (int e = threadIdx.x; e < N; e += NT) {
+    const int a = e / n2, j = e - a * n2;
+    float t = 0.f;
+    for (int b = 0; b < n2; ++b)
+      t = fmaf(A[aidx(a * n2 + b)].x, __ldg(c2 + (dir == TO_TIME ? b * n2 + j : j * n2 + b)), t);
+    B[aidx(e)].x = t;
+  }
+  __syncthreads();
+  // columns: x[i][j] = sum_a C1[a][i] T[a][j] (DCT-III) or sum_a C1[i][a] T[a][j] (DCT-II)
+  for (int e = threadIdx.x; e < N; e += NT) {
+    const int i = e / n2, j = e - i * n2;
+    float t = 0.f;
+    for (int a = 0; a < n1; ++a)
+      t = fmaf(__ldg(c1 + (dir == TO_TIME ? a * n1 + i : i * n1 + a)), B[aidx(a * n2 + j)].x, t);
+    A[aidx(e)] = make_float2(t, 0.f);
+  }
+  __syncthreads();
+}
+
+// x -> C d x (no basis) or C d Psi x (basis Psi = C^T, or the 2-D basis): the forward operator
+// before the rows are picked, on the real parts of A.
 __device__ __forceinline__ void generic_forward() {
   if (C.op.psi) {
-    czt_stage(TO_TIME);
+    if (C.op.psi == 2) psi2d_stage(TO_TIME);
+    else czt_stage(TO_TIME);
     psi_signs();
   }
   czt_stage(TO_FREQ);
@@ -1535,7 +1604,8 @@ __device__ __forceinline__ void generic_inverse() {
   czt_stage(TO_TIME);
   if (C.op.psi) {
     psi_signs();
-    czt_stage(TO_FREQ);
+    if (C.op.psi == 2) psi2d_stage(TO_FREQ);
+    else czt_stage(TO_FREQ);
   }
 }
 
@@ -1628,8 +1698,8 @@ __device__ __noinline__ float transform(int src, int nloc, const float* dense, c
   if (src != SRC_NONE) {
     const bool pre2 = src != SRC_GLOBAL_N && C.g.F == F_MAX;
     scatter_fwd(src, nloc, dense, gin, pre2);
-    if (pre2) fft_after_radix2<-1>(C.sm.A, C.sm.B, C.tw, C.g.four_n);
-    else local_fft<-1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
+    if (pre2) fft_after_radix2<-1>(C.sm.A, C.sm.B, ctx_tw(), C.g.four_n);
+    else local_fft<-1>(C.sm.A, C.sm.B, C.g.F, ctx_tw(), C.g.four_n);
     exchange_fwd();
   } else {
     cl_sync();                                    // every CTA is done with its A before any push
@@ -1641,10 +1711,10 @@ __device__ __noinline__ float transform(int src, int nloc, const float* dense, c
     cl_sync();                                    // every push into A has landed; B is scratch again
     if (fuse) {
       const float tot = reduce_collect(slot);     // the partials were published before the barrier
-      local_fft<1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
+      local_fft<1>(C.sm.A, C.sm.B, C.g.F, ctx_tw(), C.g.four_n);
       return tot;
     }
-    local_fft<1>(C.sm.A, C.sm.B, C.g.F, C.tw, C.g.four_n);
+    local_fft<1>(C.sm.A, C.sm.B, C.g.F, ctx_tw(), C.g.four_n);
   } else {
     cl_sync();                                    // nobody still reads this CTA's A
     if (fuse) return reduce_collect(slot);
@@ -1887,33 +1957,43 @@ __device__ __noinline__ void cg_solve(int wi, int nloc, bool warm, int r0src, fl
   const float stop2 = C.cg_abs ? fmaxf(tol * tol, CG_FP32_FLOOR * CG_FP32_FLOOR * v[1]) : tol * tol * v[1];
   if (maxit == 0) maxit = (int)v[2];
   int it = 0;
+  // the cluster path folds the direction update into the next scatter (one pass over the list
+  // fewer per step); the streamed and any-N paths update p here
+  const bool fuse_p = !C.grid && !C.gen;
+  if (threadIdx.x == 0) C.cg_beta = 0.f;   // every thread passed cluster_sum's barriers above
+  if (threadIdx.x == 0) C.cg_fuse = fuse_p ? 1 : 0;
   while (it < maxit && rr > stop2) {
     // H d, with d^T H d = ||P_Omega A W d||^2 summed in the frequency step and reduced through
     // the transform's last cluster barrier (one reduction per step fewer than a dot with H d)
+    // (on the cluster path the scatter first forms this step's direction p = r + beta p, with
+    // the previous step's beta, 0 on the first step where p = r0 already)
     const float pq = transform(SRC_CG, nloc, nullptr, nullptr, MID_MASK, true, nullptr, nullptr, true);
-    // pointers are re-read from the context after the call (nothing held live across it)
+    if (!(pq > 0.f)) break;   // H d = 0 in FP32: the residual is at rounding level (uniform: pq is cluster-wide)
+    const float alpha = rr / pq;
+    // pointers are re-read from the context after the call (nothing held live across it);
+    // one pass gathers q = H d and updates x and r
     const SigView Ax = sigview();
     const uint32_t* sw = shp(C.sm.signw);
     const int* li = C.list;
     float* px = C.cgx;
     float* pr = C.cgr;
     float* pp = C.cgp;
-    float* pq_ = C.cgq;
-    for (int i = threadIdx.x; i < nloc; i += NT) pq_[i] = corr_at(Ax, sw, li[i]);
-    __syncthreads();
-    if (!(pq > 0.f)) break;   // H d = 0 in FP32: the residual is at rounding level (uniform: pq is cluster-wide)
-    const float alpha = rr / pq;
     float rn = 0.f;
     for (int i = threadIdx.x; i < nloc; i += NT) {
+      const float q = corr_at(Ax, sw, li[i]);
       px[i] = fmaf(alpha, pp[i], px[i]);
-      const float r = fmaf(-alpha, pq_[i], pr[i]);
+      const float r = fmaf(-alpha, q, pr[i]);
       pr[i] = r;
       rn = fmaf(r, r, rn);
     }
     cluster_sum(&rn, 1);
     const float beta = rn / rr;
     rr = rn;
-    for (int i = threadIdx.x; i < nloc; i += NT) pp[i] = fmaf(beta, pp[i], pr[i]);
+    if (fuse_p) {
+      if (threadIdx.x == 0) C.cg_beta = beta;   // read by the next scatter, past its first barrier
+    } else {
+      for (int i = threadIdx.x; i < nloc; i += NT) pp[i] = fmaf(beta, pp[i], pr[i]);
+    }
     ++it;
   }
   if (threadIdx.x == 0) {
@@ -2062,28 +2142,34 @@ __device__ __noinline__ void topk_corr(int K, const uint32_t* excl, uint32_t* ds
 // OMP argmax step: t = argmax_{j not in S} |c_j| (lowest index on ties); returns the winner's
 // signal index or -1 when no candidate is left.  Adds it to the support mask (owner CTA) and
 // zeroes its slot of the warm-start vector.
-__device__ __noinline__ int omp_select(uint32_t* mA) {
+// This thread's largest packed key (|c| key, then the complement of the signal index, so that
+// ties go to the lowest index) over its slots outside mA, skipping the key `skip` (0: none).
+// NAT: the any-N path's natural slot order (the slot is the signal index).
+template <bool NAT>
+__device__ __forceinline__ unsigned long long argmax_key(const uint32_t* mA, unsigned long long skip) {
   const Geo g = C.g;
   const SigView A = sigview();
+  const int ns = C.nslots;
+  const int32_t* perm = C.op.perm;
   unsigned long long key = 0;
-  for (int sg = threadIdx.x; sg < C.nslots; sg += NT) {
+  for (int sg = threadIdx.x; sg < ns; sg += NT) {
     if (mask_bit(mA, sg)) continue;
-    const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) |
-                                  (0xffffffffu - (uint32_t)sig_of_slot(g, sg));
-    key = kk > key ? kk : key;
+    const int n0 = NAT ? sg : n_of_slot_pow2(g, sg);
+    const uint32_t n = (uint32_t)(perm ? __ldg(perm + n0) : n0);   // as sig_of_slot
+    const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) | (0xffffffffu - n);
+    if (kk != skip && kk > key) key = kk;
   }
+  return key;
+}
+
+__device__ __noinline__ int omp_select(uint32_t* mA) {
+  unsigned long long key = C.gen ? argmax_key<true>(mA, 0ull) : argmax_key<false>(mA, 0ull);
   cluster_max64(&key, 1);
   if (key == 0ull) return -1;   // no candidate left (uniform: key is cluster-reduced)
   const int n = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffu));
   if (C.want_margins) {
     // runner-up over the same candidates: margin (a_(1) - a_(2)) / a_(1)
-    unsigned long long k2 = 0;
-    for (int sg = threadIdx.x; sg < C.nslots; sg += NT) {
-      if (mask_bit(mA, sg)) continue;
-      const unsigned long long kk = ((unsigned long long)abs_key(A.at(sg)) << 32) |
-                                    (0xffffffffu - (uint32_t)sig_of_slot(g, sg));
-      if (kk != key && kk > k2) k2 = kk;
-    }
+    unsigned long long k2 = C.gen ? argmax_key<true>(mA, key) : argmax_key<false>(mA, key);
     cluster_max64(&k2, 1);
     const float a1 = key_value((uint32_t)(key >> 32)), a2 = key_value((uint32_t)(k2 >> 32));
     note_selection(TR_ARGMAX, a1 > 0.f ? (a1 - a2) / a1 : 0.f, n, RESERVE_HERE, 0);
@@ -2482,7 +2568,6 @@ __device__ __noinline__ void run_task(const Task* tp, int P, int c, int F_alloc)
     if (op.generic) {   // the chirp-z FFT's own table, omega_{4 czt_n}
       C.tw2.lo = C.sm.tw2lo; C.tw2.hi = C.sm.tw2hi; C.tw2.lo_bits = op.tw2_lo_bits;
       C.tw2.lo_mask = (1 << op.tw2_lo_bits) - 1; C.tw2.mask4n = 4 * op.czt_n - 1;
-      C.tw2.qbits = 31; C.tw2.qmask = 0x7fffffff;
     }
   }
   __syncthreads();
@@ -2932,7 +3017,7 @@ __device__ __noinline__ void stream_unit(const StreamArgs& a, int b, float2* T, 
   float2* TB = R1 + apad(F);
   const OpDev& op = a.op;
   const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1,
-                 31, 0x7fffffff};
+};
   Geo g;
   g.N = op.N; g.L = op.N >> 1; g.P = op.P; g.F = F; g.c = 0; g.h = 0; g.lh = 0; g.S2 = 0; g.four_n = 4 * op.N;
   const int rs = apad(F);
@@ -2985,7 +3070,7 @@ __device__ __noinline__ void stream_cols(const StreamArgs& a, int b, float2* T, 
   const OpDev& op = a.op;
   float2* TB = reinterpret_cast<float2*>(smem_raw) + 2 * apad(F);
   const Tw tw = {TB + apad(F), TB + apad(F) + apad(1 << op.lo_bits), op.lo_bits, (1 << op.lo_bits) - 1, 4 * op.N - 1,
-                 31, 0x7fffffff};
+};
   if (a.mode == MODE_APPLY)
     stream_cols_fwd<PT>(reinterpret_cast<const float4*>(a.in + (size_t)b * op.N), a.dbits, T, tw, rot, c, nc);
   else

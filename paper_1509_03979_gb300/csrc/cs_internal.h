@@ -19,6 +19,8 @@ constexpr int SCRATCH_ARRAYS = 8;   // per-CTA global arrays of 2F words (see Sc
 // S1 = GRID_S1 points; G = min(GRID_G_MAX, S2) CTAs of one cooperative launch own R = S2/G
 // rows each, and a second pass runs S2-point column FFTs over blocks of W columns.
 constexpr int GRID_S1 = 4096;
+constexpr int GRID_LOG_S1 = 12;
+static_assert((1 << GRID_LOG_S1) == GRID_S1, "GRID_LOG_S1 = log2 GRID_S1");
 constexpr int GRID_G_MAX = 128;
 constexpr int GRID_BLOCK = 4096;    // complex points per column block (W = GRID_BLOCK / S2)
 constexpr int N_MAX_GRID = 1 << 24;   // 2^24: with the quarter-period twiddle table and global Omega task bits
@@ -75,7 +77,11 @@ struct OpDev {
   const float2* czt_hat;     // [czt_n] FFT of the chirp kernel, scaled by 1 / czt_n
   const float2* tw2;         // [2^tw2_lo_bits] then [2^tw2_hi_bits]: omega_{4 czt_n}^j, two levels
   int tw2_lo_bits, tw2_hi_bits;
-  int psi;                   // sparsifying basis (any-N path): 0 identity, 1 Psi = C_N^T (Sec. III-A)
+  int psi;                   // sparsifying basis (any-N path): 0 identity, 1 Psi = C_N^T, 2 the separable
+                             // 2-D basis C_{n1}^T (.) C_{n2} of an n1 x n2 array (Sec. III-A, IV-A)
+  int n1, n2;                // 2-D basis: array shape, row-major (n1 n2 = N)
+  const float* c1;           // 2-D basis: the orthonormal DCT-II matrices C_{n1} [n1][n1] and
+  const float* c2;           //   C_{n2} [n2][n2], row k = frequency k
 };
 constexpr int N_MAX_ANY = 4096;   // largest N (not a power of two) of the any-N path: czt_n <= F_MAX
 

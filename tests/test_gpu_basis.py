@@ -71,3 +71,33 @@ def test_basis_limits(B):
         B.Operator(8192, 1000, 1, psi="dct")          # the basis runs on the any-N path, N <= 4096
     with pytest.raises(ValueError):
         B.Operator(1024, 256, 1, randomizer="perm", psi="dct")
+
+
+@pytest.mark.parametrize("n1,n2,M", [(32, 64, 600), (64, 64, 1200), (30, 33, 330)])
+def test_basis_2d_apply_and_transpose(B, n1, n2, M):
+    N = n1 * n2
+    op = B.Operator(N, M, 300 + N, psi=("dct2d", n1, n2))
+    ref = oracle.Operator(N, M, 300 + N, psi=("dct2d", n1, n2))
+    g = np.random.default_rng(n1 + n2)
+    x = g.standard_normal(N).astype(np.float32)
+    u = g.standard_normal(M).astype(np.float32)
+    assert rel(op.apply(to_dev(x)).cpu().numpy(), ref.apply(x.astype(np.float64))) <= APPLY_TOL
+    assert rel(op.apply_t(to_dev(u)).cpu().numpy(), ref.apply_t(u.astype(np.float64))) <= APPLY_TOL
+    assert rel(op.apply(op.apply_t(to_dev(u))).cpu().numpy(), u) <= 2 * APPLY_TOL
+
+
+@pytest.mark.parametrize("algo", ["omp", "sp", "cosamp"])
+def test_basis_2d_recovers_a_dct_sparse_image(B, algo):
+    """A 64 x 64 image that is K-sparse in the separable 2-D DCT basis (the image model of the
+    paper's Sec. IV-A experiment, at the size this path holds), recovered exactly from M = N/4
+    measurements, selection by selection against the oracle."""
+    n1 = n2 = 64
+    N, M, K = n1 * n2, 1024, 40
+    ref = oracle.Operator(N, M, 4242, psi=("dct2d", n1, n2))
+    S = synth.sparse_gaussian(N, K, 4243)
+    y = ref.apply(S).astype(np.float32)
+    op = B.Operator(N, M, 4242, psi=("dct2d", n1, n2))
+    rep, s_hat, supp, st, want = replay_parity(op, ref, y, K, algo, 1e-6, 200)
+    assert rel(s_hat, S) <= SHAT_TOL
+    image = ref._psi(s_hat.astype(np.float64))            # back to pixels
+    assert rel(image, ref._psi(S)) <= SHAT_TOL
