@@ -8,6 +8,7 @@ N(0,1) nonzeros, noise 1e-3 ||y|| / sqrt(M) -- in one persistent launch per clus
 replayed from a CUDA graph.  The same line carries the other parts of the metric:
   * batched_over_plain: the same batch as a loop of single-signal cs_recover calls;
   * apply_roofline:     batched A / A^T GB/s at N = 2^18 against the measured HBM peak;
+  * select_roofline:    batched top-K selection GB/s (N = 2^22 and 2^18 rows in HBM) against it;
   * workloads:          SP at N = 2^18 (56 signals per step), OMPR at N = 2^22, OMP at N = 4096,
                         the differentiable LS step (32 x solve + adjoint at N = 2^16);
   * parity:             a stated sample of the batch replayed selection by selection by the FP64
@@ -15,7 +16,7 @@ replayed from a CUDA graph.  The same line carries the other parts of the metric
   * cpu_baseline:       the FP64 oracle on the host cores (all, and one), on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload headline|sp18|batched|ompr22|ls16|omp4k|paper]
+                    [--workload headline|sp18|batched|ompr22|ls16|omp4k|select|paper]
 """
 import argparse
 import hashlib
@@ -54,14 +55,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "sp18", "batched", "ompr22", "ls16", "paper", "omp4k"])
+                    choices=["headline", "sp18", "batched", "ompr22", "ls16", "paper", "omp4k", "select"])
     ap.add_argument("--batched-count", type=int, default=256)
     ap.add_argument("--apply-batch", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the loop of single-signal calls")
     ap.add_argument("--paper-max-log2n", type=int, default=24, help="largest log2 N of the paper sweep")
-    ap.add_argument("--profile-case", default=None, choices=["apply", "apply_t", "sp", "omp", "ompr", "mixed"],
+    ap.add_argument("--profile-case", default=None, choices=["apply", "apply_t", "sp", "omp", "ompr", "mixed", "select"],
                     help="run one small fixed case for a profiler and exit (no timing, no JSON)")
     ap.add_argument("--case-N", type=int, default=1 << 18)
     ap.add_argument("--case-batch", type=int, default=16)
@@ -130,20 +131,23 @@ def peaks():
 
 
 ENGINE_SRC = os.path.join(ROOT, "paper_1509_03979_gb300", "csrc", "cs_engine.cu")
+SELECT_SRC = os.path.join(ROOT, "paper_1509_03979_gb300", "csrc", "cs_select.cu")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def engine_sha():
-    return hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
+def engine_sha(src=None):
+    return hashlib.sha256(open(src or ENGINE_SRC, "rb").read()).hexdigest()[:16]
 
 
 def traffic_per_unit(key):
     """DRAM bytes (read + write) per unit of work of a profiled kernel launch, from the data file
-    the profiling step records (null when the engine source changed since the capture)."""
+    the profiling step records (null when the kernel's source file changed since the capture:
+    cs_select.cu for select_kernel, cs_engine.cu for the others)."""
     if not os.path.exists(TRAFFIC):
         return None
     rec = json.load(open(TRAFFIC)).get(key)
-    if not rec or rec.get("engine_sha") != engine_sha():
+    src = SELECT_SRC if key.startswith("select_kernel") else ENGINE_SRC
+    if not rec or rec.get("engine_sha") != engine_sha(src):
         return None
     return rec["dram_bytes"] / rec["units"]
 
@@ -509,6 +513,36 @@ def leg_apply(args, torch, binding, devc):
             "traffic_per_vector": tpu, "cluster_engine": {"A_GBs": ca, "AT_GBs": ct}}
 
 
+def leg_select(args, torch, binding, devc):
+    """Batched top-K selection (cs_select_topk_batched) on rows resident in HBM: 304 rows of
+    N = 2^22 with K = 83 886 (the OMPR initial support at N = 2^22) and 1216 rows of N = 2^18
+    with K = 6554 (SP's at N = 2^18); both batches exceed L2.  Algorithmic bytes per row: 4N read
+    + 4K written."""
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    out = {"bound": "hbm", "peak": hbm_peak, "peak_kind": peak_kind, "kernel": "select_kernel", "cases": []}
+    for N, K, Bn in ((1 << 22, 83886, 304), (1 << 18, 6554, 1216)):
+        gen = torch.Generator(device=devc).manual_seed(N + K)
+        c = torch.randn((Bn, N), generator=gen, device=devc, dtype=torch.float32)
+        idx = torch.empty((Bn, K), dtype=torch.int32, device=devc)
+        for _ in range(2):
+            binding.select_topk_batched(c, K, out=idx)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(5):
+            e0, e1 = _events(torch)
+            e0.record(stream); binding.select_topk_batched(c, K, out=idx); e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms) / 1e3
+        gbs = Bn * 4.0 * (N + K) / t / 1e9
+        out["cases"].append({"N": N, "K": K, "rows": Bn, "ms": 1e3 * t, "GBs": gbs, "frac": gbs / hbm_peak,
+                             "bytes_per_row": 4 * (N + K), "traffic_per_row": traffic_per_unit(f"select_kernel/n{N}")})
+        del c, idx
+    torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------------- oracle legs (CPU)
 def oracle_sample_run(budget_s, batched_count):
     """The FP64 oracle as it stands on a bounded sample of the mixed batch: the signals in
@@ -610,6 +644,14 @@ def run_profile_case(args):
         _, _, st = binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs], CG_TOL, CG_MAXIT,
                                            want_stats=True)   # after the profiled launches: their work
         print("transforms per launch", sum(x["transforms"] for x in st), "engine", engine_sha())
+    else:
+        if args.profile_case == "select":   # --case-batch rows of N = --case-N, K = N / 50
+            c = torch.randn((args.case_batch, args.case_N), device=dev, generator=g)
+            for _ in range(args.case_reps):
+                binding.select_topk_batched(c, max(1, args.case_N // 50))
+            torch.cuda.synchronize()
+            print("ok", args.profile_case, args.case_N, args.case_batch)
+            return
         N, M = args.case_N, args.case_N // 4
         op = binding.Operator(N, M, 0x0C5002)
         op.set_batched_impl(args.case_impl)
@@ -683,6 +725,7 @@ def run_gb300(args, rank, world, local_rank):
         extra["omp4k"] = leg_omp4k(args, torch, binding, devc, 10)
         extra["ls16"] = leg_ls16(args, torch, binding, devc, 10)
         apply = leg_apply(args, torch, binding, devc)
+        select = leg_select(args, torch, binding, devc)
         parity = parity_leg(h["parity_jobs"]) if h["parity_jobs"] else None
         cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
         plain = h["plain"]
@@ -698,7 +741,7 @@ def run_gb300(args, rank, world, local_rank):
             "gpu_launches_note": f"{h['per_replay']} launches captured once into the graph, replayed every step",
             "roofline": h["roofline"],
             "batched_over_plain": (h["value"] / plain["value"]) if plain else None, "plain_loop": plain,
-            "apply_roofline": apply, "workloads": extra, "parity": parity, "cpu_baseline": cpu,
+            "apply_roofline": apply, "select_roofline": select, "workloads": extra, "parity": parity, "cpu_baseline": cpu,
             "quality": h["quality"], "wall_s_timed": h["wall"],
         }
         print(json.dumps(line), flush=True)
@@ -713,6 +756,8 @@ def run_single_workload(args, rank, world, local_rank):
     fn = {"sp18": leg_sp18, "ompr22": leg_ompr22, "omp4k": leg_omp4k, "ls16": leg_ls16}.get(args.workload)
     if fn is not None:
         res = fn(args, torch, binding, devc, args.steps)
+    elif args.workload == "select":
+        res = leg_select(args, torch, binding, devc)
     else:
         args.no_parity = True
         h = run_headline(args, rank, world, local_rank, torch, binding, devc, lambda v: v)

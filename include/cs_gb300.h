@@ -308,6 +308,23 @@ cs_status cs_ls_solve_batched(cs_op_t op, int32_t B, const int32_t* support, int
 cs_status cs_ls_backward_batched(cs_op_t op, int32_t B, const int32_t* support, int32_t k,
                                  const float* g, float cg_tol, int32_t cg_maxit, float* dy_out);
 
+/* Batched top-K support selection over |c| (Sec. II step 2: the K largest correlations, as in
+ * SP's merge and the SP / OMPR initial support), independent of any operator.
+ *   c        [B][N] device, row-major; c[b * N + n].
+ *   exclude  [B][ceil(N/32)] device or NULL: bit n % 32 of word n / 32 of row b set means entry
+ *            n of row b is not eligible (e.g. the current support, for top-K over j not in S).
+ *   idx_out  [B][K] device: for every row the K eligible indices with the largest |c[b][n]|,
+ *            ties broken towards the lowest index, sorted ascending; a row with fewer than K
+ *            eligible entries gets all of them followed by -1.
+ *   stream   the CUDA stream (a cudaStream_t; NULL: the legacy default stream).
+ * 1 <= N <= 2^30, 0 <= K <= N, B >= 0 (B = 0 or K = 0: nothing to do).  NaN entries order
+ * above +inf.  Asynchronous; allocates its workspace stream-ordered (cudaMallocAsync), so it
+ * can be captured into a CUDA graph.  The result is exact for every input; one pass over c in
+ * HBM suffices unless the row's values defeat the kernel's strided sample, in which case that
+ * row is re-read (slower, still exact). */
+cs_status cs_select_topk_batched(int32_t B, int64_t N, int32_t K, const float* c,
+                                 const uint32_t* exclude, int32_t* idx_out, void* stream);
+
 /* Statistics of the last single-signal call on this op (synchronises the op's stream). */
 cs_status cs_get_stats(cs_op_t op, cs_stats* out);
 

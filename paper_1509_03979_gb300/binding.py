@@ -63,6 +63,7 @@ SIGNATURES = {
     "cs_ls_backward_batched": (_I32, [_P, _I32, _P, _I32, _P, _F32, _I32, _P]),
     "cs_get_stats": (_I32, [_P, _P]),
     "cs_op_sync": (_I32, [_P]),
+    "cs_select_topk_batched": (_I32, [_I32, _I64, _I32, _P, _P, _P, _P]),
     "cs_probe_bounded_wait": (_I32, [_U64, _I32]),
     "cs_last_error": (ctypes.c_char_p, []),
     "cs_launch_count": (ctypes.c_int64, []),
@@ -319,6 +320,26 @@ class Operator:
     def sync(self):
         """Wait for this operator's stream; raises if its last launch failed or timed out."""
         _check(lib().cs_op_sync(self._h))
+
+
+def select_topk_batched(c, K, exclude=None, out=None):
+    """cs_select_topk_batched: for every row of c ([B, N] float32, CUDA) the K indices with the
+    largest |c| outside `exclude` (int32 [B, ceil(N/32)] bit words, or None), ties to the lowest
+    index, ascending; -1 past a row's eligible count.  Returns int32 [B, K] on the current stream."""
+    if c.dim() != 2:
+        raise ValueError("c must be [B, N]")
+    B, N = c.shape
+    _dev(c, torch.float32, name="c")
+    W = (N + 31) // 32
+    ex = ctypes.c_void_p(0)
+    if exclude is not None:
+        ex = _dev(exclude, torch.int32, B * W, name="exclude")
+    out = out if out is not None else torch.empty((B, K), dtype=torch.int32, device=c.device)
+    _dev(out, torch.int32, B * K, name="out")
+    stream = ctypes.c_void_p(torch.cuda.current_stream(c.device).cuda_stream)
+    _check(lib().cs_select_topk_batched(B, N, K, ctypes.c_void_p(c.data_ptr()), ex,
+                                        ctypes.c_void_p(out.data_ptr()), stream))
+    return out
 
 
 def recover_batched(ops, ys, Ks, algos, cg_tol=1e-6, cg_maxit=100, s_outs=None, supports=None, want_stats=False):

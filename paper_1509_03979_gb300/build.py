@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcs_gb300.so")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
-SOURCES = ["cs_engine.cu", "cs_api.cu"]
+SOURCES = ["cs_engine.cu", "cs_api.cu", "cs_select.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

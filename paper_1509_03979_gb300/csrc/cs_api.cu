@@ -831,6 +831,54 @@ cs_status cs_op_tune_batched(cs_op_t op, int32_t B, float* ms_out) {
   return st;
 }
 
+cs_status cs_select_topk_batched(int32_t B, int64_t N, int32_t K, const float* c, const uint32_t* exclude,
+                                 int32_t* idx_out, void* stream) {
+  if (B < 0) return fail(CS_ERR_INVALID_ARG, "B must be >= 0");
+  if (N < 1 || N > (int64_t(1) << 30)) return fail(CS_ERR_INVALID_ARG, "N must be in [1, 2^30]");
+  if (K < 0 || K > N) return fail(CS_ERR_INVALID_ARG, "K must satisfy 0 <= K <= N");
+  if (B == 0 || K == 0) return CS_OK;
+  if (!c || !idx_out) return fail(CS_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SelectArgs a = {};
+  a.c = c;
+  a.excl = exclude;
+  a.out = idx_out;
+  a.N = N;
+  a.B = B;
+  a.K = K;
+  a.W = (int)((N + 31) / 32);
+  const int64_t groups = (N + 3) / 4;
+  a.S = 4 * (int)std::min<int64_t>(groups, SELECT_SAMPLE_MAX / 4);
+  // sample rank of the threshold: the K-th largest of the row sits near rank mu = K S / N of
+  // the sample (standard deviation about sqrt(mu)); r = 1.15 mu + 4 sqrt(mu) + 8 keeps at least
+  // K entries at or above the threshold except with negligible probability, and about
+  // N r / S of them (+- N sqrt(r) / S) are candidates
+  const double mu = (double)K * a.S / (double)N;
+  a.r = (int)std::min<double>(a.S, std::ceil(1.15 * mu + 4.0 * std::sqrt(mu) + 8.0));
+  // each warp keeps the candidates of its sixteenth of the row: the expected count plus six
+  // standard deviations of the threshold's and of the warp's own fluctuation, at most the range
+  const double ew = (double)N * (a.r + 6.0 * std::sqrt((double)a.r) + 6.0) / a.S / SELECT_WARPS;
+  const int64_t range = 4 * ((groups + SELECT_WARPS - 1) / SELECT_WARPS);
+  a.capw = (int)std::min<double>((double)range, std::ceil(ew + 6.0 * std::sqrt(ew) + 64.0));
+  a.vec = (N % 4 == 0 && (reinterpret_cast<uintptr_t>(c) & 15u) == 0) ? 1 : 0;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
+  const int per_sm = select_ctas_per_sm();
+  if (per_sm < 1) return fail(CS_ERR_CUDA, "the selection kernel cannot be launched on this device");
+  const int grid = (int)std::min<int64_t>(B, (int64_t)per_sm * sms);
+  const size_t cand_bytes = sizeof(uint2) * (size_t)a.capw * SELECT_WARPS;
+  void* ws = nullptr;
+  if ((e = cudaMallocAsync(&ws, (size_t)grid * cand_bytes, s)) != cudaSuccess)
+    return cuda_fail(e, "alloc selection workspace");
+  a.cand = static_cast<uint2*>(ws);
+  e = counted(launch_select(a, grid, s));
+  cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) return cuda_fail(e, "selection launch");
+  return CS_OK;
+}
+
 cs_status cs_probe_bounded_wait(uint64_t polls, int32_t set_flag) {
   if (polls < 1 || polls > (1ull << 24)) return fail(CS_ERR_INVALID_ARG, "polls must be in [1, 2^24]");
   unsigned* buf = nullptr;

@@ -157,6 +157,23 @@ cudaError_t launch_stream(const StreamArgs& a, int nc, int clusters, cudaStream_
 
 cudaError_t launch_wait_probe(unsigned* flag, unsigned long long limit, int* status, cudaStream_t stream);
 
+// Batched top-K selection (cs_select.cu): one CTA per row at a time, workspace per CTA.
+struct SelectArgs {
+  const float* c;            // [B][N] rows
+  const uint32_t* excl;      // [B][W] exclusion bits (bit n of row b set: entry n is not eligible), or null
+  int32_t* out;              // [B][K] selected indices, ascending (-1 past the eligible count)
+  uint2* cand;               // per CTA and warp: [capw] (key, index) candidates of the warp's range
+  long long N;
+  int B, K, W;               // rows, selected per row, 32-bit words per row of excl
+  int capw;                  // candidate capacity per warp
+  int S, r;                  // sample keys (a multiple of 4) and the sample rank of the threshold
+  int vec;                   // 1: N % 4 == 0 and c 16-byte aligned (16-byte loads)
+};
+constexpr int SELECT_SAMPLE_MAX = 4096;   // sample keys of cs_select.cu
+constexpr int SELECT_WARPS = 16;          // warps per CTA of cs_select.cu
+int select_ctas_per_sm();
+cudaError_t launch_select(const SelectArgs& a, int grid, cudaStream_t stream);
+
 SmemPlan cluster_plan(int F_alloc);
 SmemPlan generic_plan(int czt_n, int F_alloc, int tw_hi_n, int tw2_lo_n, int tw2_hi_n);
 SmemPlan op_plan(const OpDev& op);              // the plan a single task of this operator runs with

@@ -65,3 +65,15 @@ def test_permutation_draw_matches_oracle(lib, N, seed):
 def test_launch_counter_starts_at_zero_without_a_gpu(lib):
     # nothing can launch on a machine without a GPU; the counter is process-wide
     assert lib.cs_launch_count() == 0
+
+
+@pytest.mark.parametrize("Bn,N,K,null_c,code", [(-1, 16, 1, False, 1), (1, 0, 0, False, 1), (1, (1 << 30) + 1, 1, False, 1),
+                                                (1, 16, 17, False, 1), (1, 16, -1, False, 1), (2, 16, 4, True, 1),
+                                                (0, 16, 4, True, 0), (3, 16, 0, True, 0)])
+def test_select_arguments_checked_without_gpu(lib, Bn, N, K, null_c, code):
+    # argument errors come back before any device work; B = 0 or K = 0 is a no-op
+    c = None if null_c else ctypes.c_void_p(16)
+    st = lib.cs_select_topk_batched(Bn, N, K, c, None, None if null_c else ctypes.c_void_p(16), None)
+    assert st == code
+    if code:
+        assert len(lib.cs_last_error()) > 0
