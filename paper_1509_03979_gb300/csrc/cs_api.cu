@@ -92,6 +92,28 @@ int8_t draw_sign(uint64_t sign_key, int64_t n) {
   return (mix64(sign_key + (uint64_t)n + GAMMA) >> 63) ? (int8_t)-1 : (int8_t)1;
 }
 
+// The library's stream-ordered scratch comes from the device's default memory pool.  Its
+// release threshold is raised once per device (a setting of this process only, not of the
+// GPU), so memory freed at the end of one call is reused by the next instead of going back to
+// the driver at every synchronisation and being mapped again.
+void retain_pool() {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  const uint64_t bit = 1ull << dev;
+  if (done.load() & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done.fetch_or(bit);
+}
+
 cs_status check_nm(int64_t N, int64_t M) {
   if (N < N_MIN || N > N_MAX_GRID || (!is_pow2(N) && N > N_MAX_ANY))
     return fail(CS_ERR_UNSUPPORTED_N, "N must be in [16, 4096] or a power of two in [16, 2^24], got " +
@@ -330,6 +352,7 @@ static cs_op_t create_op(int64_t N, int64_t M, uint64_t seed, int32_t randomizer
     fail(CS_ERR_INVALID_ARG, "unknown randomiser");
     return nullptr;
   }
+  retain_pool();
   cs_op* op = new cs_op();
   op->N = N;
   op->M = M;
@@ -838,6 +861,7 @@ cs_status cs_select_topk_batched(int32_t B, int64_t N, int32_t K, const float* c
   if (K < 0 || K > N) return fail(CS_ERR_INVALID_ARG, "K must satisfy 0 <= K <= N");
   if (B == 0 || K == 0) return CS_OK;
   if (!c || !idx_out) return fail(CS_ERR_INVALID_ARG, "null argument");
+  retain_pool();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   SelectArgs a = {};
   a.c = c;

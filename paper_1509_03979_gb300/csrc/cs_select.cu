@@ -5,8 +5,9 @@
 //
 // One CTA owns one row at a time (a persistent grid of two CTAs per SM, no waits between CTAs),
 // and each of its 16 warps owns one contiguous sixteenth of the row:
-//   1. a strided sample of SEL_SAMPLE keys gives a low threshold T (the sample's r-th largest,
-//      r set so that at least K keys of the row are >= T with overwhelming probability);
+//   1. a strided sample of SEL_SAMPLE keys gives a low threshold T (a lower bound of the
+//      sample's r-th largest key, r set so that at least K keys of the row are >= T with
+//      overwhelming probability);
 //   2. one streaming pass over the row (cp.async 16-byte copies, several tiles in flight per
 //      thread): every warp appends the (key, index) pairs of its range with key >= T, in index
 //      order, to its own candidate segment;
@@ -98,11 +99,14 @@ __device__ void digit_search(SelShared& sh, uint32_t need) {
 // Radix select of the K largest nonzero keys over the CTA (every thread calls it with the same
 // K).  each(visit) calls visit(key) for every key this thread holds.  On return keys > *tau are
 // selected and *need more are to be taken among the *eq keys equal to *tau; *tau = 0 (take every
-// nonzero key) when fewer than K are nonzero.
+// nonzero key) when fewer than K are nonzero.  With passes < 3 only the leading digits are
+// resolved: *tau is then the threshold's prefix with the low bits zero, a lower bound of the
+// K-th largest key.
 template <class Each>
-__device__ void block_radix_select(SelShared& sh, uint32_t K, Each each, uint32_t* tau, uint32_t* need, uint32_t* eq) {
+__device__ void block_radix_select(SelShared& sh, uint32_t K, Each each, uint32_t* tau, uint32_t* need, uint32_t* eq,
+                                   int passes = 3) {
   uint32_t prefix = 0, pmask = 0, nd = K, last_eq = 0;
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     const int shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
     const uint32_t dmask = pass == 2 ? 1023u : 2047u;
     for (int i = threadIdx.x; i < SEL_BINS; i += SNT) sh.hist[i] = 0u;
@@ -226,11 +230,11 @@ __device__ void select_row(SelShared& sh, const SelectArgs& a, int b) {
       [&](auto visit) {
         for (int i = threadIdx.x; i < a.S; i += SNT) visit(sh.skey[i]);
       },
-      &tlo, &need, &eq);
+      &tlo, &need, &eq, 2);   // a lower bound of the r-th largest sample key suffices
   if (tlo == 0u) tlo = 1u;   // the sample has fewer than r eligible keys: every eligible entry
 
   // 2. stream the row once; every warp appends the keys >= tlo of its range to its segment, in
-  // index order.  Branch-free: a lane's count c <= 4 is prefix-summed over the warp from three
+  // index order.  Scalar path: a lane's count c <= 4 is prefix-summed over the warp from three
   // ballots of its bits, and the stores are predicated.
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t wc = 0;   // this warp's candidates so far (warp-uniform)
@@ -259,6 +263,60 @@ __device__ void select_row(SelShared& sh, const SelectArgs& a, int b) {
     constexpr int TS = 32 * SEL_SU;
     const int T = (gw1 - gw0 + TS - 1) / TS;
     const float4* row4 = reinterpret_cast<const float4*>(row);
+    static_assert(SEL_SU * 8 <= 32 && SEL_SU * 4 <= 32, "per-group counts (at most 32 x 4) in 8-bit fields, mask in 32 bits");
+    const uint32_t tm1 = tlo - 1u;   // key >= tlo  <=>  (|c| bits) >= tlo - 1
+    // One tile: the lane's SEL_SU groups (SEL_SU x 4 entries) as a candidate mask m (bit 4u + e),
+    // the counts of each group packed in 8-bit fields and prefix-summed over the warp by one
+    // shuffle scan, then a loop over the lane's set bits only.  Index order is (group u, lane,
+    // entry), so group u's candidates of all lanes come before group u + 1's.
+    auto append_tile = [&](const float4* slot, int t) {
+      uint32_t m = 0u;
+#pragma unroll
+      for (int u = 0; u < SEL_SU; ++u) {
+        const int g = gw0 + t * TS + u * 32 + lane;
+        if (g < gw1) {
+          const float4 v = slot[u * SNT + threadIdx.x];
+          uint32_t q = ((__float_as_uint(v.x) & 0x7fffffffu) >= tm1 ? 1u : 0u) |
+                       ((__float_as_uint(v.y) & 0x7fffffffu) >= tm1 ? 2u : 0u) |
+                       ((__float_as_uint(v.z) & 0x7fffffffu) >= tm1 ? 4u : 0u) |
+                       ((__float_as_uint(v.w) & 0x7fffffffu) >= tm1 ? 8u : 0u);
+          if (ex) q &= ~(__ldg(ex + ((4 * g) >> 5)) >> ((4 * g) & 31));
+          m |= (q & 15u) << (4 * u);
+        }
+      }
+      uint32_t packed = 0u;
+#pragma unroll
+      for (int u = 0; u < SEL_SU; ++u) packed |= (uint32_t)__popc((m >> (4 * u)) & 15u) << (8 * u);
+      uint32_t incl = packed;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t excl = incl - packed;
+      uint32_t gbase[SEL_SU];   // offset of group u's candidates in the segment
+      uint32_t acc = wc;
+#pragma unroll
+      for (int u = 0; u < SEL_SU; ++u) {
+        gbase[u] = acc + ((excl >> (8 * u)) & 255u);
+        acc += (tot >> (8 * u)) & 255u;
+      }
+      uint32_t mm = m;
+      while (mm) {
+        const int bt = __ffs(mm) - 1;
+        mm &= mm - 1u;
+        const int u = bt >> 2, e = bt & 3;
+        uint32_t gb = gbase[0];
+#pragma unroll
+        for (int uu = 1; uu < SEL_SU; ++uu) gb = u == uu ? gbase[uu] : gb;
+        const uint32_t pos = gb + __popc(m & ((1u << bt) - 1u) & (15u << (4 * u)));
+        const float val = reinterpret_cast<const float*>(slot + u * SNT + threadIdx.x)[e];
+        const int g = gw0 + t * TS + u * 32 + lane;
+        if (pos < (uint32_t)capw) seg[pos] = make_uint2(sel_key(val), (uint32_t)(4 * g + e));
+      }
+      wc = acc;
+    };
     auto issue = [&](int t) {
       if (t < T) {
         float4* slot = sel_ring + (size_t)(t % SEL_DEPTH) * SEL_SU * SNT;
@@ -275,23 +333,7 @@ __device__ void select_row(SelShared& sh, const SelectArgs& a, int b) {
     for (int t = 0; t < T; ++t) {
       issue(t + SEL_DEPTH - 1);
       cp_async_wait<SEL_DEPTH - 1>();   // this thread's copies of tile t have landed
-      const float4* slot = sel_ring + (size_t)(t % SEL_DEPTH) * SEL_SU * SNT;
-#pragma unroll
-      for (int u = 0; u < SEL_SU; ++u) {
-        const int g = gw0 + t * TS + u * 32 + lane;
-        uint32_t k[4] = {0u, 0u, 0u, 0u};
-        if (g < gw1) {
-          const float4 v = slot[u * SNT + threadIdx.x];
-          k[0] = sel_key(v.x); k[1] = sel_key(v.y); k[2] = sel_key(v.z); k[3] = sel_key(v.w);
-          if (ex) {
-            const uint32_t wd = __ldg(ex + ((4 * g) >> 5)) >> ((4 * g) & 31);
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if ((wd >> e) & 1u) k[e] = 0u;
-          }
-        }
-        append(k, 4 * g);
-      }
+      append_tile(sel_ring + (size_t)(t % SEL_DEPTH) * SEL_SU * SNT, t);
     }
     cp_async_wait<0>();
   } else {
