@@ -387,11 +387,12 @@ def leg_sp18(args, torch, binding, devc, steps):
     t = sum(ms) / 1e3
     hbm_peak, _ = peaks()
     gbs = transforms * 8.0 * p.N / (t / steps) / 1e9
+    tpu = traffic_per_unit("engine_kernel/sp18")   # DRAM bytes per SP recovery (ncu capture)
     op.close()
     return {"workload": "SP+CG-LS N=2^18 M=65536 K=6554 noise 1e-3, 8 signals per resident cluster per step",
             "value": B * steps / t, "unit": "recoveries/s", "ms_per_step": 1e3 * t / steps, "batch": B,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                         "transforms_per_step": transforms,
+                         "transforms_per_step": transforms, "traffic": None if tpu is None else tpu * B,
                          "alu_frac": transforms * flops_per_dct(p.N) / (t / steps) / 1e12 / 80.5}}
 
 
