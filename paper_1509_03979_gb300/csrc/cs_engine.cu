@@ -374,6 +374,7 @@ struct Smem {
   float2* S;          // any-N path: signal-domain values by slot (natural order)
   float2* tw2lo;      // any-N path: twiddles of the chirp-z FFT
   float2* tw2hi;
+  uint16_t* tperm;    // cluster path: this CTA's frequency tasks, those with a kept output first
 };
 
 // Bump allocator over the dynamic shared-memory window (16-byte granules).
@@ -411,8 +412,9 @@ __host__ __device__ inline void layout(const SmemPlan& pl, Bump& take, Smem* s) 
   unsigned char* sv = take(sizeof(float2) * (size_t)pl.slot_n);
   unsigned char* t2l = take(sizeof(float2) * (size_t)(pl.tw2_lo_n ? apad(pl.tw2_lo_n) : 0));
   unsigned char* t2h = take(sizeof(float2) * (size_t)pl.tw2_hi_n);
+  unsigned char* tp = take(sizeof(uint16_t) * (size_t)pl.tperm_n);
   if (s) {
-    s->S = (float2*)sv; s->tw2lo = (float2*)t2l; s->tw2hi = (float2*)t2h;
+    s->S = (float2*)sv; s->tw2lo = (float2*)t2l; s->tw2hi = (float2*)t2h; s->tperm = (uint16_t*)tp;
     s->A = (float2*)A; s->B = (float2*)B; s->twlo = (float2*)tl; s->twhi = (float2*)th;
     s->signw = (uint32_t*)sw; s->mask[0] = (uint32_t*)m0; s->mask[1] = (uint32_t*)m1;
     s->fbits = (uint8_t*)fb; s->hist = (uint32_t*)hi; s->htot = (uint32_t*)ht; s->ring = (float*)rg;
@@ -441,6 +443,7 @@ SmemPlan cluster_plan(int F_alloc) {
   p.slot_n = 0;
   p.tw2_lo_n = 0;
   p.tw2_hi_n = 0;
+  p.tperm_n = F_alloc / 2 + P_MAX + 16;   // >= ntasks of every CTA
   return p;
 }
 
@@ -458,6 +461,7 @@ SmemPlan generic_plan(int czt_n, int F_alloc, int tw_hi_n, int tw2_lo_n, int tw2
   p.slot_n = apad(F_alloc);
   p.tw2_lo_n = tw2_lo_n;
   p.tw2_hi_n = tw2_hi_n;
+  p.tperm_n = 0;
   return p;
 }
 
@@ -474,6 +478,7 @@ SmemPlan grid_plan(const OpDev& op) {
   p.slot_n = 0;
   p.tw2_lo_n = 0;
   p.tw2_hi_n = 0;
+  p.tperm_n = 0;
   return p;
 }
 
@@ -556,6 +561,7 @@ struct Ctx {
   SmemPlan plan;      // the launch's shared-memory plan
   float cg_beta;      // CG: beta of the last step, applied by the next scatter of p (cluster path)
   int cg_fuse;        // 1 while cg_solve runs with the direction update in the scatter
+  int tnz;            // cluster path: frequency tasks of this CTA with a kept output (tperm's first)
 };
 __shared__ Ctx C;
 
@@ -1006,6 +1012,22 @@ __device__ __noinline__ void build_fbits() {
     rank4[t] = make_int4(rk[0], rk[1], rk[2], rk[3]);
   }
   __syncthreads();
+  // the task order of the frequency stage: a stable partition, tasks with a kept output first
+  // (every thread takes a contiguous chunk; deterministic, so every run gets the same order)
+  uint16_t* perm = shp(C.sm.tperm);
+  const int per = (nt + NT - 1) / NT;
+  const int t0 = min(nt, (int)threadIdx.x * per), t1 = min(nt, t0 + per);
+  int cnt = 0;
+  for (int t = t0; t < t1; ++t) cnt += fb[t] != 0;
+  int total;
+  int pnz = block_scan(cnt, &total);
+  int pz = total + (t0 - pnz);
+  for (int t = t0; t < t1; ++t) {
+    if (fb[t] != 0) perm[pnz++] = (uint16_t)t;
+    else perm[pz++] = (uint16_t)t;
+  }
+  if (threadIdx.x == 0) C.tnz = total;
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------- the transform pair
@@ -1157,9 +1179,12 @@ __device__ __forceinline__ void dct3_pair(const float* X, int k, bool self, cons
 // pre-processing back into the pair.  Returns this thread's sum of squares of the MID_RESID
 // residual y - A x on Omega, or for MID_MASK of the kept outputs A d on Omega.
 // MASK: the kind is MID_MASK (the H d step), compiled without the y-side state.
-template <bool MASK, class TW>
+// PERM: tasks run in the order perm[] (the cluster path's partition); the tasks from position
+// nnz on have no output in Omega, so their only effect is zero in the pair's slots (inv).
+template <bool MASK, class TW, bool PERM>
 __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_t* fb, const int4* rank4, int kind,
-                                           bool fwd_done, bool inv, const float* vin, float* vout) {
+                                           bool fwd_done, bool inv, const float* vin, float* vout,
+                                           const uint16_t* perm, int nnz) {
   TW tw;
   smem_tw_into(tw);
   const uint32_t* omask = C.omask;
@@ -1173,15 +1198,23 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
   for (int t0 = threadIdx.x; t0 < nt; t0 += 2 * NT) {
     int rk[2][4];
     float xin[2][4];
+    int tt[2];      // task of slot u, -1 past the end
+    bool live[2];   // the task has an output in Omega
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int t = t0 + u * NT;
+      const int i = t0 + u * NT;
+      tt[u] = i < nt ? (PERM ? (int)perm[i] : i) : -1;
+      live[u] = !PERM || i < nnz;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int t = tt[u];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         rk[u][i] = -1;
         xin[u][i] = 0.f;
       }
-      if (MASK || t >= nt) continue;
+      if (MASK || t < 0 || !live[u]) continue;
       if (rank4) {
         const int4 r = rank4[t];
         rk[u][0] = r.x; rk[u][1] = r.y; rk[u][2] = r.z; rk[u][3] = r.w;
@@ -1208,11 +1241,18 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int t = t0 + u * NT;
-      if (t >= nt) continue;
+      const int t = tt[u];
+      if (t < 0) continue;
       int sa, kpa, sb, kpb;
       if (!task_pair(g, t, sa, kpa, sb, kpb)) continue;
       const bool self = (sa == sb) && (kpa == kpb);
+      if (!live[u]) {   // no output in Omega: the pre-processing of zeros
+        if (inv) {
+          B[kpa * S2 + sa] = make_float2(0.f, 0.f);
+          if (!self) B[kpb * S2 + sb] = make_float2(0.f, 0.f);
+        }
+        continue;
+      }
       const int k = kq_of(g, sa) + F * kpa;
       const PairTw pt = pair_tw(tw, k);
       float X[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1253,7 +1293,8 @@ __device__ __forceinline__ float freq_core(const Geo& g, float2* B, const uint8_
 template <bool MASK>
 __device__ __noinline__ float freq_half_k(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
   const Geo g = C.g;
-  return freq_core<MASK, Tw>(g, shp(C.sm.B), shp(C.sm.fbits), C.rank4, kind, fwd_done, inv, vin, vout);
+  return freq_core<MASK, Tw, true>(g, shp(C.sm.B), shp(C.sm.fbits), C.rank4, kind, fwd_done, inv, vin, vout,
+                                   shp(C.sm.tperm), C.tnz);
 }
 __device__ __forceinline__ float freq_half(int kind, bool fwd_done, bool inv, const float* vin, float* vout) {
   return kind == MID_MASK ? freq_half_k<true>(kind, fwd_done, inv, vin, vout)
@@ -1431,8 +1472,9 @@ __device__ __noinline__ float grid_col_block(int j, int kind, bool fwd_done, boo
   }
   const int fbstride = (W / 2) * S2 + S2 + 1;
   const uint8_t* fbj = grid_fbits() + j * fbstride;
-  const float acc = kind == MID_MASK ? freq_core<true, TwQ>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout)
-                                     : freq_core<false, TwQ>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout);
+  const float acc = kind == MID_MASK
+                        ? freq_core<true, TwQ, false>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout, nullptr, 0)
+                        : freq_core<false, TwQ, false>(gb, X, fbj, nullptr, kind, fwd_done, inv, vin, vout, nullptr, 0);
   __syncthreads();
   if (inv) {
     col_fft<1>(C.sm.A, C.sm.B, S2, lw, C.tw, gb.four_n);

@@ -37,6 +37,7 @@ struct SmemPlan {
   int slot_n;       // any-N path: complex entries of the slot buffer S (0 otherwise)
   int tw2_lo_n;     // any-N path: entries of the FFT twiddle tables (0 otherwise)
   int tw2_hi_n;
+  int tperm_n;      // cluster path: entries of the frequency-task order (0 otherwise)
 };
 
 enum Mode : int {
