@@ -152,6 +152,20 @@ __device__ __forceinline__ void load4(const float* row, const uint32_t* ex, int 
   }
 }
 
+// Candidate bits of four entries: bit e set when |v_e| >= tf, i.e. when |v_e| - tf has a clear
+// sign bit.  The difference is never negative for |v_e| >= tf, so no entry at or above the
+// threshold is lost (a NaN entry keeps a clear sign bit and stays a candidate, as its key orders
+// it above +inf; a NaN threshold makes every entry a candidate).  The four sign bytes are
+// gathered by byte permutes and packed into a nibble by one multiply: the shifted sign bits sit
+// at bits 0, 8, 16, 24, and x 0x01020408 moves them to bits 24 .. 27 with no carries there.
+__device__ __forceinline__ uint32_t cand_nibble(const float4& v, float tf) {
+  const uint32_t d0 = __float_as_uint(fabsf(v.x) - tf), d1 = __float_as_uint(fabsf(v.y) - tf);
+  const uint32_t d2 = __float_as_uint(fabsf(v.z) - tf), d3 = __float_as_uint(fabsf(v.w) - tf);
+  const uint32_t w = __byte_perm(__byte_perm(d0, d1, 0x0073), __byte_perm(d2, d3, 0x0073), 0x5410);
+  const uint32_t sgn = ((w >> 7) & 0x01010101u) * 0x01020408u >> 24;
+  return ~sgn & 15u;
+}
+
 __device__ __forceinline__ uint32_t key_at(const float* row, const uint32_t* ex, int n) {
   if (ex && ((__ldg(ex + (n >> 5)) >> (n & 31)) & 1u)) return 0u;
   return sel_key(__ldcg(row + n));
@@ -264,7 +278,7 @@ __device__ void select_row(SelShared& sh, const SelectArgs& a, int b) {
     const int T = (gw1 - gw0 + TS - 1) / TS;
     const float4* row4 = reinterpret_cast<const float4*>(row);
     static_assert(SEL_SU * 8 <= 32 && SEL_SU * 4 <= 32, "per-group counts (at most 32 x 4) in 8-bit fields, mask in 32 bits");
-    const uint32_t tm1 = tlo - 1u;   // key >= tlo  <=>  (|c| bits) >= tlo - 1
+    const float tf = __uint_as_float(tlo - 1u);   // key >= tlo  <=>  |c| >= tf (bit patterns)
     // One tile: the lane's SEL_SU groups (SEL_SU x 4 entries) as a candidate mask m (bit 4u + e),
     // the counts of each group packed in 8-bit fields and prefix-summed over the warp by one
     // shuffle scan, then a loop over the lane's set bits only.  Index order is (group u, lane,
@@ -276,10 +290,7 @@ __device__ void select_row(SelShared& sh, const SelectArgs& a, int b) {
         const int g = gw0 + t * TS + u * 32 + lane;
         if (g < gw1) {
           const float4 v = slot[u * SNT + threadIdx.x];
-          uint32_t q = ((__float_as_uint(v.x) & 0x7fffffffu) >= tm1 ? 1u : 0u) |
-                       ((__float_as_uint(v.y) & 0x7fffffffu) >= tm1 ? 2u : 0u) |
-                       ((__float_as_uint(v.z) & 0x7fffffffu) >= tm1 ? 4u : 0u) |
-                       ((__float_as_uint(v.w) & 0x7fffffffu) >= tm1 ? 8u : 0u);
+          uint32_t q = cand_nibble(v, tf);
           if (ex) q &= ~(__ldg(ex + ((4 * g) >> 5)) >> ((4 * g) & 31));
           m |= (q & 15u) << (4 * u);
         }
