@@ -38,11 +38,15 @@ from paper_1509_03979_gb300 import shard, synth  # noqa: E402
 METRIC = "recoveries/s at rel-err≤1e-4; A/Aᵀ apply GB/s vs HBM peak; batched vs plain"
 HEADLINE = ("mixed batch of 256 signals: N=2^12..2^18 (log2 N uniform), M/N~U[0.15,0.4], K/M~U[0.05,0.2], "
             "OMP/SP by a coin, N(0,1) nonzeros, noise 1e-3, one launch per cluster size from a CUDA graph")
-# CG tolerance of the timed recoveries: the metric counts recoveries within rel-err 1e-4 of the
-# FP64 oracle; on these noisy workloads the GPU error is set by near-ties in the support, not by
-# the CG tolerance (SP at N = 2^18: max rel-err 2.3e-5 at cg_tol 1e-6, 3.4e-5 at 5e-6, 4.4e-5 at
-# 2e-5); 5e-6 keeps a 3x margin, and the parity leg re-measures the error on every run.
+# Relative CG tolerances of the timed recoveries.  The metric counts recoveries within rel-err
+# 1e-4 of the FP64 oracle, and CG's precision trades speed for accuracy (Sec. IV-C).  The batched
+# workloads (the mixed batch and the SP batch) run at 2e-5: measured max rel-err 3.2e-5 on the
+# parity leg's replayed sample of the mixed batch (5.0e-6 at 5e-6), SP at N = 2^18 4.4e-5 over
+# 7 signals, and the full-size oracle test of both batches runs at the same setting; the parity
+# leg re-measures the error on every run.  The single-signal legs keep 5e-6, the setting their
+# own oracle tests use.
 CG_TOL, CG_MAXIT = 5e-6, 100
+BATCH_CG_TOL = 2e-5
 SIGNALS_PER_CLUSTER = 8          # SP N = 2^18 workload: signals per resident cluster and step
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 SMSPs x 32)
 ORACLE_BUDGET_S = 15.0           # CPU seconds of each oracle timing leg
@@ -68,6 +72,7 @@ def parse():
     ap.add_argument("--case-batch", type=int, default=16)
     ap.add_argument("--case-reps", type=int, default=2)
     ap.add_argument("--case-impl", default="auto", choices=["auto", "cluster", "streamed"])
+    ap.add_argument("--cg-tol", type=float, default=BATCH_CG_TOL, help="relative CG tolerance of the batched workloads")
     ap.add_argument("--oracle-sample", type=float, default=0.0, help=argparse.SUPPRESS)
     ap.add_argument("--one-core", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -221,18 +226,18 @@ def run_headline(args, rank, world, local_rank, torch, binding, devc, reduce_max
         traces[i] = torch.zeros(replay.trace_words(probs[i].N, probs[i].K, probs[i].algo), dtype=torch.int32,
                                 device=devc)
         ops[i].set_trace(traces[i])
-    _, _, stats = binding.recover_batched(ops, ys, Ks, algos, CG_TOL, CG_MAXIT, souts, supps, want_stats=True)
+    _, _, stats = binding.recover_batched(ops, ys, Ks, algos, BATCH_CG_TOL, CG_MAXIT, souts, supps, want_stats=True)
     torch.cuda.synchronize()
     for i in sample:
         ops[i].set_trace(None)
     parity_jobs = [dict(N=probs[i].N, M=probs[i].M, op_seed=probs[i].op_seed, y=ys[i].cpu().numpy().astype(np.float64),
                         K=probs[i].K, algo=probs[i].algo, trace=traces[i].cpu().numpy(), s=souts[i].cpu().numpy(),
-                        supp=supps[i].cpu().numpy(), stats=stats[i], shat_tol=1e-4, cg_tol=CG_TOL, index=int(idx[i]))
+                        supp=supps[i].cpu().numpy(), stats=stats[i], shat_tol=1e-4, cg_tol=BATCH_CG_TOL, index=int(idx[i]))
                    for i in sample]
     transforms = [s["transforms"] for s in stats]
 
     def batched():
-        binding.recover_batched(ops, ys, Ks, algos, CG_TOL, CG_MAXIT, souts, supps)
+        binding.recover_batched(ops, ys, Ks, algos, BATCH_CG_TOL, CG_MAXIT, souts, supps)
 
     batched()
     graph = torch.cuda.CUDAGraph()
@@ -316,12 +321,12 @@ def run_headline(args, rank, world, local_rank, torch, binding, devc, reduce_max
     # batched vs plain: the same signals as a loop of single-signal cs_recover calls
     plain = None
     if not args.no_plain:
-        ops[0].recover(ys[0], Ks[0], algos[0], CG_TOL, CG_MAXIT, souts[0], supps[0])
+        ops[0].recover(ys[0], Ks[0], algos[0], BATCH_CG_TOL, CG_MAXIT, souts[0], supps[0])
         torch.cuda.synchronize()
         e0, e1 = _events(torch)
         e0.record(stream)
         for op, y, k, a, so, sp in zip(ops, ys, Ks, algos, souts, supps):
-            op.recover(y, k, a, CG_TOL, CG_MAXIT, so, sp)
+            op.recover(y, k, a, BATCH_CG_TOL, CG_MAXIT, so, sp)
         e1.record(stream)
         torch.cuda.synchronize()
         tp = reduce_max(e0.elapsed_time(e1) / 1e3)
@@ -368,10 +373,10 @@ def leg_sp18(args, torch, binding, devc, steps):
     s_out = torch.empty((B, p.N), dtype=torch.float32, device=devc)
     supp = torch.empty((B, p.K), dtype=torch.int32, device=devc)
     ops, ys, so, sk = [op] * B, [Y[b] for b in range(B)], [s_out[b] for b in range(B)], [supp[b] for b in range(B)]
-    _, _, stats = binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, CG_TOL, CG_MAXIT, so, sk, want_stats=True)
+    _, _, stats = binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, BATCH_CG_TOL, CG_MAXIT, so, sk, want_stats=True)
     transforms = sum(s["transforms"] for s in stats)
     for _ in range(3):
-        binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, CG_TOL, CG_MAXIT, so, sk)
+        binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, BATCH_CG_TOL, CG_MAXIT, so, sk)
     torch.cuda.synchronize()
     l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=devc)
     stream = torch.cuda.current_stream()
@@ -380,7 +385,7 @@ def leg_sp18(args, torch, binding, devc, steps):
         l2_flush.zero_()
         e0, e1 = _events(torch)
         e0.record(stream)
-        binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, CG_TOL, CG_MAXIT, so, sk)
+        binding.recover_batched(ops, ys, [p.K] * B, ["sp"] * B, BATCH_CG_TOL, CG_MAXIT, so, sk)
         e1.record(stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -641,8 +646,8 @@ def run_profile_case(args):
         ys = [op.apply(torch.from_numpy(p.signal().astype(np.float32)).to(dev)).contiguous()
               for op, p in zip(ops, probs)]
         for _ in range(args.case_reps):
-            binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs], CG_TOL, CG_MAXIT)
-        _, _, st = binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs], CG_TOL, CG_MAXIT,
+            binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs], BATCH_CG_TOL, CG_MAXIT)
+        _, _, st = binding.recover_batched(ops, ys, [p.K for p in probs], [p.algo for p in probs], BATCH_CG_TOL, CG_MAXIT,
                                            want_stats=True)   # after the profiled launches: their work
         print("transforms per launch", sum(x["transforms"] for x in st), "engine", engine_sha())
     else:
@@ -734,7 +739,7 @@ def run_gb300(args, rank, world, local_rank):
             "metric": METRIC, "value": h["value"], "unit": "recoveries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": HEADLINE, "signals": h["n_all"], "cg_tol": CG_TOL, "cg_maxit": CG_MAXIT,
+            "config": {"workload": HEADLINE, "signals": h["n_all"], "cg_tol": BATCH_CG_TOL, "cg_maxit": CG_MAXIT,
                        "l2": "256 MiB buffer written between timed steps",
                        "parallelism": (f"the batch cut into {world} contiguous blocks of equal estimated work, "
                                        "no collective") if world > 1 else "one GPU"},
@@ -854,7 +859,9 @@ def run_paper_sweep(args, rank, local_rank):
 
 
 def main():
+    global BATCH_CG_TOL
     args = parse()
+    BATCH_CG_TOL = args.cg_tol
     if args.oracle_sample > 0:
         oracle_child(args)
         return

@@ -22,7 +22,7 @@ from tests.gpu_common import SHAT_TOL
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-CG_TOL, CG_MAXIT = 5e-6, 100   # the benchmark's settings for these workloads
+CG_TOL, CG_MAXIT = 2e-5, 100   # the benchmark's settings for these batched workloads
 
 
 def _trace(op, K, algo):
