@@ -41,6 +41,11 @@
  *     precision, Sec. IV-C) or xi = 1e-10 yields the LS solution to FP32 precision.
  *     cg_maxit = 0 means at most |S| steps, the bound of Theorem 5.  A step whose H d
  *     vanishes in FP32 ends the solve (the residual is at rounding level).
+ *   - Per-call scratch is stream-ordered (cudaMallocAsync / cudaFreeAsync on the call's
+ *     stream).  The first operator creation or selection call on a device raises the release
+ *     threshold of that device's default memory pool to its maximum, so freed scratch stays
+ *     pooled for the next call instead of returning to the driver at every synchronisation
+ *     (a setting of this process; it also applies to the host program's own cudaMallocAsync).
  *   - cs_last_error() returns a thread-local message describing the last failure.
  *   - Operators are not thread-safe: one host thread at a time per cs_op_t.
  *   - CUDA graphs: cs_op_apply(_t)(_batched), cs_recover, cs_recover_batched (stats_host
