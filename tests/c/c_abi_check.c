@@ -25,6 +25,9 @@ int main(int argc, char** argv) {
   if (cs_operator_perm(N, 7u, perm) != CS_OK) return 1;
   /* an unsupported size is refused with a message */
   if (cs_operator_draws(4097, 8, 1u, omega, NULL) != CS_ERR_UNSUPPORTED_N || strlen(cs_last_error()) == 0) return 1;
+  /* the batched selection checks its arguments on the host; an empty batch is a no-op */
+  if (cs_select_topk_batched(1, 16, 17, (const float*)16, NULL, (int32_t*)16, NULL) != CS_ERR_INVALID_ARG) return 1;
+  if (cs_select_topk_batched(0, 16, 4, NULL, NULL, NULL, NULL) != CS_OK) return 1;
   if (cs_launch_count() < 0) return 1;
   printf("omega[0]=%d omega[M-1]=%d d[0]=%d perm[0]=%d launches=%lld\n", (int)omega[0], (int)omega[M - 1], (int)d[0],
          (int)perm[0], (long long)cs_launch_count());
