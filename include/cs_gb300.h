@@ -44,7 +44,7 @@
  *   - Per-call scratch is stream-ordered (cudaMallocAsync / cudaFreeAsync on the call's
  *     stream).  The first operator creation or selection call on a device raises the release
  *     threshold of that device's default memory pool to its maximum, so freed scratch stays
- *     pooled for the next call instead of returning to the driver at every synchronisation
+ *     pooled for the next call instead of returning to the CUDA driver at every synchronisation
  *     (a setting of this process; it also applies to the host program's own cudaMallocAsync).
  *   - cs_last_error() returns a thread-local message describing the last failure.
  *   - Operators are not thread-safe: one host thread at a time per cs_op_t.

@@ -95,7 +95,7 @@ int8_t draw_sign(uint64_t sign_key, int64_t n) {
 // The library's stream-ordered scratch comes from the device's default memory pool.  Its
 // release threshold is raised once per device (a setting of this process only, not of the
 // GPU), so memory freed at the end of one call is reused by the next instead of going back to
-// the driver at every synchronisation and being mapped again.
+// the CUDA driver at every synchronisation and being mapped again.
 void retain_pool() {
   static std::atomic<uint64_t> done{0};
   int dev = 0;
